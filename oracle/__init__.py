@@ -1,0 +1,200 @@
+"""CPU FP64 oracle for the short-range nonbonded path (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` may import this package. The CUDA library never loads it and
+shares no code with it. The arithmetic lives in ``oracle.c`` (plain C,
+FP64, OpenMP); this module compiles it with gcc on first use and marshals
+numpy arrays.
+
+Functions:
+
+* ``energy_forces`` - E_LJ, E_C and F for every atom (O(N^2) or cell list).
+* ``forces_subset`` - F on chosen atoms only, each summed over all partners.
+* ``pairs_f64`` - brute-force set of pairs with r < r_cut in FP64.
+* ``pairs_f32`` - the set of pairs within rc under the FP32 contract that the
+  GPU pair list must reproduce bit for bit.
+* ``image_f32`` - the FP32 positions that contract uses.
+* ``loss_grad`` - force-matching loss and its analytic gradients.
+
+Parity: pinned by the CPU tests in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.environ.get("NB_ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+COULOMB_F = 138.935458
+
+
+def build(force: bool = False, src: str = _SRC, out: str | None = None) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, OpenMP, no FP contraction).
+
+    ``src``/``out`` let the mutation tests compile a deliberately broken copy
+    elsewhere; ``NB_ORACLE_LIB`` then points the loader at it.
+    """
+    out = out or _LIB_PATH
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", tmp, src, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.environ.get("NB_ORACLE_LIB"):
+                build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            F = ctypes.c_float
+            LL = ctypes.c_longlong
+            lib.oracle_threads.restype = I
+            lib.oracle_energy_forces.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, P, P, P]
+            lib.oracle_energy_forces.restype = I
+            lib.oracle_forces_subset.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, P, P]
+            lib.oracle_forces_subset.restype = I
+            lib.oracle_pairs_f64.argtypes = [I, P, P, D, P, P, P, P, LL, P]
+            lib.oracle_pairs_f64.restype = I
+            lib.oracle_pairs_f32.argtypes = [I, P, P, P, F, P, P, P, P, LL, P]
+            lib.oracle_pairs_f32.restype = I
+            lib.oracle_image_f32.argtypes = [I, P, P, P, P]
+            lib.oracle_image_f32.restype = None
+            if hasattr(lib, "oracle_loss_grad"):
+                lib.oracle_loss_grad.argtypes = [I, P, P, P, I, P, P, D, D, P, P, P, P, P, P, P, P]
+                lib.oracle_loss_grad.restype = I
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _i32(a) -> np.ndarray | None:
+    return None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().oracle_threads())
+
+
+def energy_forces(x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None, method="auto"):
+    """FP64 energies and forces.
+
+    Returns ``(F [N,3], E_lj, E_coul, npairs)``. ``lj`` is [ntype, ntype, 2]
+    holding (C6, C12). ``method`` is "auto", "n2" or "cell".
+    """
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    n = x.shape[0]
+    lj = _f64(lj)
+    ntype = lj.shape[0]
+    F = np.zeros((n, 3), dtype=np.float64)
+    E = np.zeros(2, dtype=np.float64)
+    npairs = ctypes.c_longlong(0)
+    m = {"auto": 0, "n2": 1, "cell": 2}[method]
+    rcode = lib.oracle_energy_forces(n, _p(x), _p(_f64(q)), _p(_i32(type_)), ntype, _p(lj),
+                                     _p(_f64(box)), float(rc), float(beta), _p(_i32(excl_off)),
+                                     _p(_i32(excl_idx)), m, _p(F), _p(E), ctypes.byref(npairs))
+    if rcode != 0:
+        raise ValueError(f"oracle_energy_forces failed with code {rcode}")
+    return F, float(E[0]), float(E[1]), int(npairs.value)
+
+
+def forces_subset(x, q, type_, lj, box, rc, beta, atoms, excl_off=None, excl_idx=None):
+    """FP64 forces on the atoms listed in ``atoms`` ([m, 3])."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    lj = _f64(lj)
+    atoms = _i32(atoms)
+    out = np.zeros((atoms.size, 3), dtype=np.float64)
+    rcode = lib.oracle_forces_subset(x.shape[0], _p(x), _p(_f64(q)), _p(_i32(type_)), lj.shape[0],
+                                     _p(lj), _p(_f64(box)), float(rc), float(beta),
+                                     _p(_i32(excl_off)), _p(_i32(excl_idx)), atoms.size, _p(atoms),
+                                     _p(out))
+    if rcode != 0:
+        raise ValueError(f"oracle_forces_subset failed with code {rcode}")
+    return out
+
+
+def pairs_f64(x, box, r_cut, excl_off=None, excl_idx=None):
+    """Brute-force FP64 set of pairs (i < j) within r_cut, as an int64 array [P, 2]."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    n = x.shape[0]
+    cap = max(16, n * 512)
+    while True:
+        pi = np.empty(cap, dtype=np.int32)
+        pj = np.empty(cap, dtype=np.int32)
+        cnt = ctypes.c_longlong(0)
+        lib.oracle_pairs_f64(n, _p(x), _p(_f64(box)), float(r_cut), _p(_i32(excl_off)),
+                             _p(_i32(excl_idx)), _p(pi), _p(pj), cap, ctypes.byref(cnt))
+        if cnt.value <= cap:
+            return np.stack([pi[:cnt.value], pj[:cnt.value]], axis=1).astype(np.int64)
+        cap = int(cnt.value)
+
+
+def pairs_f32(x0, x, box, rc, excl_off=None, excl_idx=None, count_only=False):
+    """Pairs within rc under the FP32 contract (see ``oracle.c``).
+
+    ``x0`` is the frame the list was searched on, ``x`` the current frame
+    (pass the same array twice for the search frame). Returns an int64 array
+    [P, 2] with i < j, or the count if ``count_only``.
+    """
+    lib = _load()
+    x0 = _f32(x0).reshape(-1, 3)
+    x = _f32(x).reshape(-1, 3)
+    n = x.shape[0]
+    box = _f32(box)
+    cnt = ctypes.c_longlong(0)
+    if count_only:
+        rc_ = lib.oracle_pairs_f32(n, _p(x0), _p(x), _p(box), float(rc), _p(_i32(excl_off)),
+                                   _p(_i32(excl_idx)), None, None, 0, ctypes.byref(cnt))
+        if rc_ < 0:
+            raise ValueError(f"oracle_pairs_f32 failed with code {rc_}")
+        return int(cnt.value)
+    cap = max(16, n * 400)
+    while True:
+        pi = np.empty(cap, dtype=np.int32)
+        pj = np.empty(cap, dtype=np.int32)
+        rc_ = lib.oracle_pairs_f32(n, _p(x0), _p(x), _p(box), float(rc), _p(_i32(excl_off)),
+                                   _p(_i32(excl_idx)), _p(pi), _p(pj), cap, ctypes.byref(cnt))
+        if rc_ < 0:
+            raise ValueError(f"oracle_pairs_f32 failed with code {rc_}")
+        if cnt.value <= cap:
+            return np.stack([pi[:cnt.value], pj[:cnt.value]], axis=1).astype(np.int64)
+        cap = int(cnt.value)
+
+
+def image_f32(x0, x, box):
+    """FP32 positions of the contract: image of ``x`` nearest wrap(``x0``)."""
+    lib = _load()
+    x0 = _f32(x0).reshape(-1, 3)
+    x = _f32(x).reshape(-1, 3)
+    y = np.empty_like(x)
+    lib.oracle_image_f32(x.shape[0], _p(x0), _p(x), _p(_f32(box)), _p(y))
+    return y

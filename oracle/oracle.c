@@ -1,0 +1,455 @@
+/*
+ * Plain CPU oracle for the short-range nonbonded path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load this library. The product path never links,
+ * loads or calls it, and it shares no code, header or constant with the
+ * CUDA library.
+ *
+ * What it computes (the plain definition that the cluster-pair method of
+ * §III-A, "NBNXM", reaches exactly up to rounding):
+ *
+ *   E_LJ = sum_{i<j, (i,j) not excluded, r_ij < rc}
+ *            C12_ij / r^12 - C6_ij / r^6 - (C12_ij / rc^12 - C6_ij / rc^6)
+ *   E_C  = f * sum_{i<j, not excluded, r_ij < rc} q_i q_j erfc(beta r) / r
+ *   F_i  = -dE/dx_i
+ *
+ * with f = 138.935458 kJ mol^-1 nm e^-2, r_ij the minimum-image distance in
+ * an orthorhombic box, and the cutoff test r < rc (strict). Everything is
+ * FP64 with libm erfc/exp. The paper gives no formulas for the kernel
+ * (§III-A names it "short-range non-bonded forces" with Ewald-type and
+ * Lennard-Jones flavours); this is textbook LJ + Ewald real-space physics.
+ *
+ * Pins (tests, CPU only): Coulomb's law at beta = 0, tabulated erfc values,
+ * the LJ force zero at 2^(1/6) sigma and energy zero at sigma, continuity at
+ * rc, sum of forces = 0, translation and permutation invariance, length
+ * scaling laws, F = -dE/dx by central differences, O(N^2) == cell list, and
+ * brute-force pair sets on tiny inputs.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_COULOMB_F 138.935458
+
+static int oracle_nthreads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int oracle_tid(void) {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+int oracle_threads(void) { return oracle_nthreads(); }
+
+/* Is j in the exclusion list of i? Self is always excluded. */
+static int is_excluded(int i, int j, const int *excl_off, const int *excl_idx) {
+    if (i == j) return 1;
+    if (!excl_off) return 0;
+    for (int k = excl_off[i]; k < excl_off[i + 1]; ++k)
+        if (excl_idx[k] == j) return 1;
+    return 0;
+}
+
+/* Minimum-image displacement x_i - x_j in FP64: d -= L * rint(d / L). */
+static void min_image(const double *xi, const double *xj, const double *box, double *d) {
+    for (int k = 0; k < 3; ++k) {
+        double v = xi[k] - xj[k];
+        v -= box[k] * rint(v / box[k]);
+        d[k] = v;
+    }
+}
+
+/*
+ * One pair's contribution. Returns the pair energies and the scalar s such
+ * that F_i += s * d and F_j -= s * d, with
+ *   s = f q_i q_j [erfc(beta r)/r + 2 beta/sqrt(pi) exp(-beta^2 r^2)] / r^2
+ *       + 12 C12 / r^14 - 6 C6 / r^8,
+ * which is -(1/r) dE/dr for the pair energy above.
+ */
+static void pair_terms(double r2, double qi, double qj, double c6, double c12, double rc,
+                       double beta, double *elj, double *ec, double *s) {
+    double r = sqrt(r2);
+    double rinv2 = 1.0 / r2;
+    double rinv6 = rinv2 * rinv2 * rinv2;
+    double rc6 = pow(rc, -6.0), rc12 = rc6 * rc6;
+    *elj = c12 * rinv6 * rinv6 - c6 * rinv6 - (c12 * rc12 - c6 * rc6);
+    double qq = ORACLE_COULOMB_F * qi * qj;
+    double erfc_r = erfc(beta * r) / r;
+    *ec = qq * erfc_r;
+    double sc = qq * (erfc_r + 2.0 * beta / sqrt(M_PI) * exp(-beta * beta * r2)) * rinv2;
+    double slj = (12.0 * c12 * rinv6 * rinv6 - 6.0 * c6 * rinv6) * rinv2;
+    *s = sc + slj;
+}
+
+/* Cell grid for the cell-list path: nc[k] = floor(L_k / rc) cells per axis. */
+static int cell_grid(const double *box, double rc, int *nc) {
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(box[k] / rc);
+        if (nc[k] < 3) return 0; /* too few cells for a 27-cell stencil without repeats */
+    }
+    return 1;
+}
+
+static int cell_of(const double *x, const double *box, const int *nc) {
+    int c[3];
+    for (int k = 0; k < 3; ++k) {
+        double w = x[k] - box[k] * floor(x[k] / box[k]);
+        int ck = (int)floor(w / box[k] * nc[k]);
+        if (ck < 0) ck = 0;
+        if (ck >= nc[k]) ck = nc[k] - 1;
+        c[k] = ck;
+    }
+    return (c[0] * nc[1] + c[1]) * nc[2] + c[2];
+}
+
+/* Counting sort of atoms by cell: cell_start[ncell + 1], cell_atoms[n]. */
+static void build_cells(int n, const double *x, const double *box, const int *nc,
+                        int *cell_start, int *cell_atoms, int *atom_cell) {
+    int ncell = nc[0] * nc[1] * nc[2];
+    memset(cell_start, 0, sizeof(int) * (size_t)(ncell + 1));
+    for (int i = 0; i < n; ++i) {
+        atom_cell[i] = cell_of(x + 3 * i, box, nc);
+        cell_start[atom_cell[i] + 1]++;
+    }
+    for (int c = 0; c < ncell; ++c) cell_start[c + 1] += cell_start[c];
+    int *fill = (int *)malloc(sizeof(int) * (size_t)ncell);
+    memcpy(fill, cell_start, sizeof(int) * (size_t)ncell);
+    for (int i = 0; i < n; ++i) cell_atoms[fill[atom_cell[i]]++] = i;
+    free(fill);
+}
+
+/* The 27 neighbour cells of cell c (with periodic wrap). */
+static void neighbour_cells(int c, const int *nc, int *out) {
+    int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+    int m = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1],
+                    z = (cz + dz + nc[2]) % nc[2];
+                out[m++] = (x * nc[1] + y) * nc[2] + z;
+            }
+}
+
+/*
+ * Energies and forces in FP64.
+ *   x[3n], q[n], type[n], lj[ntype*ntype*2] = (C6, C12) per type pair,
+ *   box[3], excl CSR (may be NULL), method 0 = auto, 1 = O(N^2), 2 = cell list.
+ * Outputs: F[3n] (overwritten), E[2] = {E_LJ, E_C}, *npairs = pairs counted.
+ * Returns 0, or -1 if rc >= L/2 on some axis, -2 if the cell list was asked
+ * for but the box has fewer than 3 cells per axis.
+ */
+int oracle_energy_forces(int n, const double *x, const double *q, const int *type, int ntype,
+                         const double *lj, const double *box, double rc, double beta,
+                         const int *excl_off, const int *excl_idx, int method, double *F,
+                         double *E, long long *npairs) {
+    for (int k = 0; k < 3; ++k)
+        if (!(rc < 0.5 * box[k])) return -1;
+    int nc[3];
+    int have_cells = cell_grid(box, rc, nc);
+    if (method == 2 && !have_cells) return -2;
+    int use_cells = (method == 2) || (method == 0 && have_cells && n > 4096);
+
+    int nt = oracle_nthreads();
+    double *Ft = (double *)calloc((size_t)nt * 3 * (size_t)n, sizeof(double));
+    double *Elj = (double *)calloc((size_t)nt, sizeof(double));
+    double *Ec = (double *)calloc((size_t)nt, sizeof(double));
+    long long *Np = (long long *)calloc((size_t)nt, sizeof(long long));
+    double rc2 = rc * rc;
+
+    int *cell_start = NULL, *cell_atoms = NULL, *atom_cell = NULL;
+    if (use_cells) {
+        int ncell = nc[0] * nc[1] * nc[2];
+        cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
+        cell_atoms = (int *)malloc(sizeof(int) * (size_t)n);
+        atom_cell = (int *)malloc(sizeof(int) * (size_t)n);
+        build_cells(n, x, box, nc, cell_start, cell_atoms, atom_cell);
+    }
+
+#pragma omp parallel
+    {
+        int tid = oracle_tid();
+        double *Fl = Ft + (size_t)tid * 3 * (size_t)n;
+        double elj_sum = 0.0, ec_sum = 0.0;
+        long long np = 0;
+        int nb[27];
+#pragma omp for schedule(static)
+        for (int i = 0; i < n; ++i) {
+            int ncand_cells = use_cells ? 27 : 1;
+            if (use_cells) neighbour_cells(atom_cell[i], nc, nb);
+            for (int cc = 0; cc < ncand_cells; ++cc) {
+                int j0, j1;
+                if (use_cells) {
+                    j0 = cell_start[nb[cc]];
+                    j1 = cell_start[nb[cc] + 1];
+                } else {
+                    j0 = i + 1;
+                    j1 = n;
+                }
+                for (int jj = j0; jj < j1; ++jj) {
+                    int j = use_cells ? cell_atoms[jj] : jj;
+                    if (j <= i) continue;
+                    double d[3];
+                    min_image(x + 3 * i, x + 3 * j, box, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!(r2 < rc2)) continue;
+                    if (is_excluded(i, j, excl_off, excl_idx)) continue;
+                    const double *p = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+                    double elj, ec, s;
+                    pair_terms(r2, q[i], q[j], p[0], p[1], rc, beta, &elj, &ec, &s);
+                    elj_sum += elj;
+                    ec_sum += ec;
+                    np++;
+                    for (int k = 0; k < 3; ++k) {
+                        Fl[3 * i + k] += s * d[k];
+                        Fl[3 * j + k] -= s * d[k];
+                    }
+                }
+            }
+        }
+        Elj[tid] = elj_sum;
+        Ec[tid] = ec_sum;
+        Np[tid] = np;
+    }
+    /* fixed-order reduction: deterministic for a given thread count */
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += Ft[(size_t)t * 3 * (size_t)n + k];
+        F[k] = s;
+    }
+    double el = 0.0, ecs = 0.0;
+    long long npt = 0;
+    for (int t = 0; t < nt; ++t) {
+        el += Elj[t];
+        ecs += Ec[t];
+        npt += Np[t];
+    }
+    E[0] = el;
+    E[1] = ecs;
+    if (npairs) *npairs = npt;
+    free(Ft);
+    free(Elj);
+    free(Ec);
+    free(Np);
+    free(cell_start);
+    free(cell_atoms);
+    free(atom_cell);
+    return 0;
+}
+
+/*
+ * Forces on a subset of atoms, each summed over all its partners (no Newton's
+ * third law), FP64. Used to check sampled atoms of systems too large to
+ * compare in full. F_sub[3m]. Same return codes as oracle_energy_forces.
+ */
+int oracle_forces_subset(int n, const double *x, const double *q, const int *type, int ntype,
+                         const double *lj, const double *box, double rc, double beta,
+                         const int *excl_off, const int *excl_idx, int m, const int *atoms,
+                         double *F_sub) {
+    for (int k = 0; k < 3; ++k)
+        if (!(rc < 0.5 * box[k])) return -1;
+    int nc[3];
+    int use_cells = cell_grid(box, rc, nc);
+    int *cell_start = NULL, *cell_atoms = NULL, *atom_cell = NULL;
+    if (use_cells) {
+        int ncell = nc[0] * nc[1] * nc[2];
+        cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
+        cell_atoms = (int *)malloc(sizeof(int) * (size_t)n);
+        atom_cell = (int *)malloc(sizeof(int) * (size_t)n);
+        build_cells(n, x, box, nc, cell_start, cell_atoms, atom_cell);
+    }
+    double rc2 = rc * rc;
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < m; ++t) {
+        int i = atoms[t];
+        double f[3] = {0.0, 0.0, 0.0};
+        int nb[27];
+        int ncc = use_cells ? 27 : 1;
+        if (use_cells) neighbour_cells(atom_cell[i], nc, nb);
+        for (int cc = 0; cc < ncc; ++cc) {
+            int j0 = use_cells ? cell_start[nb[cc]] : 0;
+            int j1 = use_cells ? cell_start[nb[cc] + 1] : n;
+            for (int jj = j0; jj < j1; ++jj) {
+                int j = use_cells ? cell_atoms[jj] : jj;
+                if (j == i) continue;
+                double d[3];
+                min_image(x + 3 * i, x + 3 * j, box, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(r2 < rc2)) continue;
+                if (is_excluded(i, j, excl_off, excl_idx)) continue;
+                const double *p = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+                double elj, ec, s;
+                pair_terms(r2, q[i], q[j], p[0], p[1], rc, beta, &elj, &ec, &s);
+                for (int k = 0; k < 3; ++k) f[k] += s * d[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) F_sub[3 * t + k] = f[k];
+    }
+    free(cell_start);
+    free(cell_atoms);
+    free(atom_cell);
+    return 0;
+}
+
+/*
+ * Brute-force FP64 set of non-excluded pairs (i < j) with minimum-image
+ * r < r_cut. O(N^2). Writes up to cap pairs to pi/pj and the total count to
+ * *count. Returns 0, or 1 if cap was too small.
+ */
+int oracle_pairs_f64(int n, const double *x, const double *box, double r_cut,
+                     const int *excl_off, const int *excl_idx, int *pi, int *pj, long long cap,
+                     long long *count) {
+    long long c = 0;
+    double r2c = r_cut * r_cut;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            double d[3];
+            min_image(x + 3 * i, x + 3 * j, box, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < r2c) || is_excluded(i, j, excl_off, excl_idx)) continue;
+            if (c < cap) {
+                pi[c] = i;
+                pj[c] = j;
+            }
+            c++;
+        }
+    *count = c;
+    return c > cap ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------
+ * FP32 pair-set contract.
+ *
+ * The cluster-pair list is exact if the set of atom pairs the force kernel
+ * counts equals the set of pairs within rc, where "within rc" is decided in
+ * FP32 on the same FP32 coordinates. These functions state that decision as
+ * plain C (compile with -ffp-contract=off):
+ *
+ *   wrap:   w = x - L*floor(x/L); if (w < 0) w += L; if (w >= L) w -= L;
+ *           if (!(w >= 0 && w < L)) w = 0                (search frame x0)
+ *   image:  k = rint((x - w0)/L); y = x - k*L            (current frame x)
+ *   d:      d = (y_a - y_b) + S, S = s*L with s in {-1, 0, 1} per axis
+ *   r2:     r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx))
+ *   test:   r2 < rc*rc  (both FP32, rc*rc rounded once)
+ *
+ * d is antisymmetric in (a, b) with S -> -S, so the decision does not depend
+ * on which atom sits in the i-cluster.
+ * ------------------------------------------------------------------------ */
+static float wrap32(float x, float L) {
+    float w = x - L * floorf(x / L);
+    if (w < 0.0f) w += L;
+    if (w >= L) w -= L;
+    if (!(w >= 0.0f && w < L)) w = 0.0f;
+    return w;
+}
+
+static float image32(float x, float w0, float L) {
+    float k = rintf((x - w0) / L);
+    return x - k * L;
+}
+
+static float r2_32(float dx, float dy, float dz) {
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+/* FP32 positions used by the contract: y = image(x, wrap(x0)). y[3n] out. */
+void oracle_image_f32(int n, const float *x0, const float *x, const float *box, float *y) {
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) y[3 * i + k] = image32(x[3 * i + k], wrap32(x0[3 * i + k], box[k]), box[k]);
+}
+
+/*
+ * Set of non-excluded pairs (i < j) that are within rc under the FP32
+ * contract above. Candidates come from an FP64 cell search with a 1e-3 nm
+ * margin, far above FP32 rounding, so the margin never decides membership.
+ * pi/pj may be NULL (count only). Returns 0; 1 if cap was too small; -1 if
+ * rc >= L/2 (images would not be unique); -3 if some pair is within rc
+ * for two different shifts.
+ */
+int oracle_pairs_f32(int n, const float *x0, const float *x, const float *box, float rc,
+                     const int *excl_off, const int *excl_idx, int *pi, int *pj, long long cap,
+                     long long *count) {
+    for (int k = 0; k < 3; ++k)
+        if (!(rc < 0.5f * box[k])) return -1;
+    float *y = (float *)malloc(sizeof(float) * 3 * (size_t)n);
+    oracle_image_f32(n, x0, x, box, y);
+    double *yd = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) yd[k] = (double)y[k];
+    double bd[3] = {box[0], box[1], box[2]};
+    double rsearch = (double)rc + 1e-3;
+    int nc[3];
+    int use_cells = 1;
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int)floor(bd[k] / rsearch);
+        if (nc[k] < 3) use_cells = 0;
+    }
+    int *cell_start = NULL, *cell_atoms = NULL, *atom_cell = NULL;
+    if (use_cells) {
+        int ncell = nc[0] * nc[1] * nc[2];
+        cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
+        cell_atoms = (int *)malloc(sizeof(int) * (size_t)n);
+        atom_cell = (int *)malloc(sizeof(int) * (size_t)n);
+        build_cells(n, yd, bd, nc, cell_start, cell_atoms, atom_cell);
+    }
+    float rc2 = rc * rc;
+    double rs2 = rsearch * rsearch;
+    long long c = 0;
+    int status = 0;
+    int nb[27];
+    for (int i = 0; i < n; ++i) {
+        int ncc = use_cells ? 27 : 1;
+        if (use_cells) neighbour_cells(atom_cell[i], nc, nb);
+        for (int cc = 0; cc < ncc; ++cc) {
+            int j0 = use_cells ? cell_start[nb[cc]] : i + 1;
+            int j1 = use_cells ? cell_start[nb[cc] + 1] : n;
+            for (int jj = j0; jj < j1; ++jj) {
+                int j = use_cells ? cell_atoms[jj] : jj;
+                if (j <= i) continue;
+                double dd[3];
+                min_image(yd + 3 * i, yd + 3 * j, bd, dd);
+                if (!(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2] < rs2)) continue;
+                if (is_excluded(i, j, excl_off, excl_idx)) continue;
+                int hits = 0;
+                float u[3];
+                for (int k = 0; k < 3; ++k) u[k] = y[3 * i + k] - y[3 * j + k];
+                for (int sx = -1; sx <= 1; ++sx)
+                    for (int sy = -1; sy <= 1; ++sy)
+                        for (int sz = -1; sz <= 1; ++sz) {
+                            float dx = u[0] + (float)sx * box[0];
+                            float dy = u[1] + (float)sy * box[1];
+                            float dz = u[2] + (float)sz * box[2];
+                            if (r2_32(dx, dy, dz) < rc2) hits++;
+                        }
+                if (hits > 1) status = -3;
+                if (hits >= 1) {
+                    if (pi && c < cap) {
+                        pi[c] = i;
+                        pj[c] = j;
+                    }
+                    c++;
+                }
+            }
+        }
+    }
+    *count = c;
+    free(y);
+    free(yd);
+    free(cell_start);
+    free(cell_atoms);
+    free(atom_cell);
+    if (status) return status;
+    return (pi && c > cap) ? 1 : 0;
+}

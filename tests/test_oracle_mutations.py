@@ -1,0 +1,43 @@
+"""Plant plausible mistakes in a copy of the oracle and check that the pins catch each.
+
+The mutated C source is compiled to a temporary library and the pin module
+runs against it in a subprocess (``NB_ORACLE_LIB``). Every mutation must make
+at least one pin fail; the unmodified oracle passes them all (see
+``test_oracle_pins.py``).
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTATIONS = {
+    "drop_exp_term_of_coulomb_force": ("2.0 * beta / sqrt(M_PI) * exp(-beta * beta * r2)", "0.0"),
+    "reaction_force_wrong_sign": ("Fl[3 * j + k] -= s * d[k];", "Fl[3 * j + k] += s * d[k];"),
+    "lj_force_wrong_prefactor": ("12.0 * c12 * rinv6 * rinv6", "6.0 * c12 * rinv6 * rinv6"),
+    "missing_lj_potential_shift": (" - (c12 * rc12 - c6 * rc6)", ""),
+    "erfc_argument_squared": ("erfc(beta * r) / r", "erfc(beta * r2) / r"),
+    "exclusions_ignored": ("if (is_excluded(i, j, excl_off, excl_idx)) continue;\n                    const", "const"),
+    "min_image_uses_floor": ("v -= box[k] * rint(v / box[k]);", "v -= box[k] * floor(v / box[k]);"),
+    "coulomb_constant_dropped": ("double qq = ORACLE_COULOMB_F * qi * qj;", "double qq = qi * qj;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.build(force=True, src=str(mutated), out=str(tmp_path / "liboracle_mut.so"))
+    env = dict(os.environ, NB_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -1,0 +1,313 @@
+"""Pins for the CPU oracle: closed forms, tabulated values, invariants, brute force.
+
+None of these re-types the oracle's own pair formula. Each checks the oracle
+against a fact the mathematics or a textbook fixes (Coulomb's law, the LJ
+well depth and zero crossing, tabulated erfc, Newton's third law,
+translation / permutation invariance, scaling laws, F = -dE/dx), or against
+an independent brute force on tiny inputs.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+F_COUL = 138.935458
+SIGMA, EPS = 0.3166, 0.650
+C6_O, C12_O = 4 * EPS * SIGMA ** 6, 4 * EPS * SIGMA ** 12
+
+
+def two_atoms(r, q1=0.0, q2=0.0, lj=True, L=10.0, direction=(1.0, 2.0, -0.5)):
+    u = np.asarray(direction, dtype=np.float64)
+    u /= np.linalg.norm(u)
+    c = np.array([L / 2, L / 2, L / 2])
+    x = np.stack([c + 0.5 * r * u, c - 0.5 * r * u])
+    q = np.array([q1, q2])
+    typ = np.zeros(2, dtype=np.int32)
+    ljp = np.zeros((1, 1, 2))
+    if lj:
+        ljp[0, 0] = (C6_O, C12_O)
+    return x, q, typ, ljp, np.array([L, L, L]), u
+
+
+def lj_textbook(r):
+    """Lennard-Jones in sigma-epsilon form: 4 eps [(s/r)^12 - (s/r)^6]."""
+    return 4 * EPS * ((SIGMA / r) ** 12 - (SIGMA / r) ** 6)
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("r", [0.15, 0.31, 0.5, 0.89])
+@pytest.mark.parametrize("q1,q2", [(1.0, 1.0), (-0.8476, 0.4238), (0.5, -2.0)])
+def test_coulomb_law_at_beta_zero(r, q1, q2):
+    """beta = 0 turns erfc(beta r) into 1: plain Coulomb's law."""
+    x, q, t, lj, box, u = two_atoms(r, q1, q2, lj=False)
+    F, elj, ec, npairs = oracle.energy_forces(x, q, t, lj, box, 0.9, 0.0, method="n2")
+    assert npairs == 1
+    assert elj == 0.0
+    assert ec == pytest.approx(F_COUL * q1 * q2 / r, rel=1e-14)
+    # like charges repel: the force on atom 0 points away from atom 1 (along +u)
+    mag = F_COUL * q1 * q2 / r ** 2
+    np.testing.assert_allclose(F[0], mag * u, rtol=1e-13, atol=1e-12 * abs(mag))
+    np.testing.assert_allclose(F[1], -mag * u, rtol=1e-13, atol=1e-12 * abs(mag))
+
+
+def test_erfc_against_table(golden_dir):
+    """E_C for two unit charges with beta r = x equals f erfc(x) / r (A&S Table 7.1)."""
+    rows = np.loadtxt(os.path.join(golden_dir, "erfc_table.txt"))
+    r = 0.4
+    for xval, erfc_tab in rows:
+        beta = xval / r
+        x, q, t, lj, box, _ = two_atoms(r, 1.0, 1.0, lj=False)
+        _, _, ec, _ = oracle.energy_forces(x, q, t, lj, box, 0.9, beta, method="n2")
+        assert ec == pytest.approx(F_COUL * erfc_tab / r, rel=2e-14), xval
+
+
+def test_lj_well_depth_and_zero_crossing():
+    """LJ: force zero and depth -eps at r = 2^(1/6) sigma; zero crossing at sigma."""
+    rc = 0.9
+    shift = lj_textbook(rc)  # potential-shifted: E(r) = V(r) - V(rc)
+    rmin = 2 ** (1 / 6) * SIGMA
+    x, q, t, lj, box, _ = two_atoms(rmin)
+    F, elj, ec, _ = oracle.energy_forces(x, q, t, lj, box, rc, 3.0, method="n2")
+    assert ec == 0.0
+    assert elj == pytest.approx(-EPS - shift, rel=1e-12)
+    assert np.abs(F).max() < 1e-10
+    x, q, t, lj, box, _ = two_atoms(SIGMA)
+    F, elj, _, _ = oracle.energy_forces(x, q, t, lj, box, rc, 3.0, method="n2")
+    assert elj == pytest.approx(-shift, rel=1e-12)
+    # repulsive inside sigma: the force on atom 0 points away from atom 1
+    x, q, t, lj, box, u = two_atoms(0.3)
+    F, _, _, _ = oracle.energy_forces(x, q, t, lj, box, rc, 3.0, method="n2")
+    assert np.dot(F[0], u) > 0
+
+
+def test_cutoff_continuity_and_strictness():
+    """Potential-shifted LJ vanishes at rc; the Coulomb term there is f q q 1e-5 / rc."""
+    rc = 0.9
+    beta = synth.ewald_beta(rc)
+    x, q, t, lj, box, _ = two_atoms(rc * (1 - 1e-12), 1.0, -1.0)
+    _, elj, ec, n = oracle.energy_forces(x, q, t, lj, box, rc, beta, method="n2")
+    assert n == 1
+    assert abs(elj) < 1e-12
+    assert ec == pytest.approx(-F_COUL * 1e-5 / rc, rel=1e-9)
+    x, q, t, lj, box, _ = two_atoms(rc * (1 + 1e-12), 1.0, -1.0)
+    _, elj, ec, n = oracle.energy_forces(x, q, t, lj, box, rc, beta, method="n2")
+    assert n == 0 and elj == 0.0 and ec == 0.0
+
+
+# ------------------------------------------------------------------- invariants
+
+@pytest.fixture(scope="module")
+def box512():
+    return synth.water_box(512, 1)
+
+
+def run(b, x=None, rc=0.9, beta=None, method="auto", q=None, lj=None):
+    beta = synth.ewald_beta(rc) if beta is None else beta
+    return oracle.energy_forces(b.coords if x is None else x, b.q if q is None else q, b.type,
+                                b.ljparams if lj is None else lj, b.box, rc, beta,
+                                b.excl_off, b.excl_idx, method)
+
+
+def test_newton_third_law(box512):
+    F, elj, ec, _ = run(box512)
+    rms = np.sqrt((F ** 2).sum(1).mean())
+    assert np.abs(F.sum(0)).max() <= 1e-10 * len(F) * rms
+
+
+def test_translation_invariance(box512):
+    F, elj, ec, n = run(box512)
+    rng = np.random.default_rng(7)
+    t = rng.uniform(-3, 3, size=3)
+    L = box512.box.astype(np.float64)
+    x2 = box512.coords.astype(np.float64) + t
+    x2 -= L * np.floor(x2 / L)
+    F2, elj2, ec2, n2 = run(box512, x=x2)
+    assert n2 == n
+    assert elj2 == pytest.approx(elj, rel=1e-12)
+    assert ec2 == pytest.approx(ec, rel=1e-11)
+    np.testing.assert_allclose(F2, F, atol=1e-9 * np.abs(F).max())
+
+
+def test_permutation_invariance(box512):
+    b = box512
+    F, elj, ec, n = run(b)
+    rng = np.random.default_rng(3)
+    p = rng.permutation(b.n_atoms)  # new atom k is old atom p[k]
+    inv = np.empty_like(p)
+    inv[p] = np.arange(len(p))
+    offs = [0]
+    idx = []
+    for k in range(len(p)):
+        old = p[k]
+        partners = b.excl_idx[b.excl_off[old]:b.excl_off[old + 1]]
+        idx.extend(inv[partners])
+        offs.append(len(idx))
+    F2, elj2, ec2, n2 = oracle.energy_forces(b.coords[p], b.q[p], b.type[p], b.ljparams, b.box, 0.9,
+                                             synth.ewald_beta(0.9), np.array(offs), np.array(idx), "n2")
+    assert n2 == n
+    assert elj2 == pytest.approx(elj, rel=1e-12)
+    assert ec2 == pytest.approx(ec, rel=1e-11)
+    np.testing.assert_allclose(F2, F[p], atol=1e-9 * np.abs(F).max())
+
+
+def test_scaling_laws(box512):
+    """x, L, rc -> lam x, lam L, lam rc; beta -> beta/lam; C6 -> lam^6 C6; C12 -> lam^12 C12.
+
+    Then E_LJ is unchanged, E_C scales by 1/lam, and the LJ and Coulomb forces
+    by 1/lam (LJ) and 1/lam^2 (Coulomb). Catches a wrong power anywhere.
+    """
+    b = box512
+    lam = 1.7
+    beta = synth.ewald_beta(0.9)
+    q0 = np.zeros(b.n_atoms)
+    F_lj, elj, _, _ = oracle.energy_forces(b.coords, q0, b.type, b.ljparams, b.box, 0.9, beta,
+                                           b.excl_off, b.excl_idx, "n2")
+    F_c, _, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, 0 * b.ljparams, b.box, 0.9, beta,
+                                         b.excl_off, b.excl_idx, "n2")
+    lj2 = b.ljparams.astype(np.float64).copy()
+    lj2[..., 0] *= lam ** 6
+    lj2[..., 1] *= lam ** 12
+    x2 = b.coords.astype(np.float64) * lam
+    box2 = b.box.astype(np.float64) * lam
+    F_lj2, elj2, _, _ = oracle.energy_forces(x2, q0, b.type, lj2, box2, 0.9 * lam, beta / lam,
+                                             b.excl_off, b.excl_idx, "n2")
+    F_c2, _, ec2, _ = oracle.energy_forces(x2, b.q, b.type, 0 * lj2, box2, 0.9 * lam, beta / lam,
+                                           b.excl_off, b.excl_idx, "n2")
+    assert elj2 == pytest.approx(elj, rel=1e-11)
+    assert ec2 == pytest.approx(ec / lam, rel=1e-10)
+    np.testing.assert_allclose(F_lj2, F_lj / lam, atol=1e-9 * np.abs(F_lj).max())
+    np.testing.assert_allclose(F_c2, F_c / lam ** 2, atol=1e-9 * np.abs(F_c).max())
+
+
+def test_charge_scaling(box512):
+    """E_C is quadratic in the charges: q -> 2q multiplies E_C and F_C by 4."""
+    b = box512
+    F, _, ec, _ = run(b, lj=0 * b.ljparams)
+    F2, _, ec2, _ = run(b, lj=0 * b.ljparams, q=2 * b.q.astype(np.float64))
+    assert ec2 == pytest.approx(4 * ec, rel=1e-13)
+    np.testing.assert_allclose(F2, 4 * F, rtol=1e-12, atol=1e-10)
+
+
+def test_force_is_minus_energy_gradient(box512):
+    """Central finite differences of E (pair set frozen) equal -F."""
+    b = box512
+    rc = 0.9
+    beta = synth.ewald_beta(rc)
+    x = b.coords.astype(np.float64)
+    F, _, _, n = run(b, x=x)
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    checked = 0
+    for atom in rng.choice(b.n_atoms, 12, replace=False):
+        for k in range(3):
+            xp = x.copy()
+            xm = x.copy()
+            xp[atom, k] += h
+            xm[atom, k] -= h
+            _, elp, ecp, np_ = run(b, x=xp)
+            _, elm, ecm, nm = run(b, x=xm)
+            if np_ != n or nm != n:
+                continue  # a pair crossed rc; the energy is discontinuous there
+            fd = -((elp + ecp) - (elm + ecm)) / (2 * h)
+            assert fd == pytest.approx(F[atom, k], rel=1e-6, abs=1e-4), (atom, k)
+            checked += 1
+    assert checked >= 30
+
+
+def test_n2_equals_cell_list():
+    b = synth.water_box(4096, 5)  # L = 4.97 nm: 5 cells of >= 0.9 nm per axis
+    F1, elj1, ec1, n1 = run(b, method="n2")
+    F2, elj2, ec2, n2 = run(b, method="cell")
+    assert n1 == n2
+    assert elj2 == pytest.approx(elj1, rel=1e-12)
+    assert ec2 == pytest.approx(ec1, rel=1e-12)
+    np.testing.assert_allclose(F2, F1, atol=1e-10 * np.abs(F1).max())
+
+
+def test_forces_subset_matches_full():
+    b = synth.water_box(4096, 5)
+    beta = synth.ewald_beta(0.9)
+    F, _, _, _ = run(b)
+    atoms = np.array([0, 1, 2, 100, 5000, b.n_atoms - 1])
+    Fs = oracle.forces_subset(b.coords, b.q, b.type, b.ljparams, b.box, 0.9, beta, atoms,
+                              b.excl_off, b.excl_idx)
+    np.testing.assert_allclose(Fs, F[atoms], atol=1e-10 * np.abs(F).max())
+
+
+# --------------------------------------------------------------- special cases
+
+def test_single_water_is_fully_excluded():
+    b = synth.water_box(1, 1)
+    F, elj, ec, n = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, 10 * b.box, 0.9,
+                                         3.0, b.excl_off, b.excl_idx)
+    assert n == 0 and elj == 0.0 and ec == 0.0 and np.all(F == 0)
+
+
+def test_superposition_of_separated_groups():
+    """Two groups more than rc apart: E(A u B) = E(A) + E(B)."""
+    a = synth.water_box(27, 1)
+    L = 8.0
+    xa = a.coords.astype(np.float64) + 0.5
+    xb = a.coords.astype(np.float64) + 4.5  # gap > 0.9 nm in every direction
+    x = np.concatenate([xa, xb])
+    q = np.concatenate([a.q, a.q]).astype(np.float64)
+    t = np.concatenate([a.type, a.type])
+    off = np.concatenate([a.excl_off, a.excl_off[1:] + a.excl_off[-1]])
+    idx = np.concatenate([a.excl_idx, a.excl_idx + a.n_atoms])
+    box = np.array([L, L, L])
+    beta = synth.ewald_beta(0.9)
+    _, elj, ec, n = oracle.energy_forces(x, q, t, a.ljparams, box, 0.9, beta, off, idx, "n2")
+    _, elj1, ec1, n1 = oracle.energy_forces(xa, a.q, a.type, a.ljparams, box, 0.9, beta,
+                                            a.excl_off, a.excl_idx, "n2")
+    assert n == 2 * n1
+    assert elj == pytest.approx(2 * elj1, rel=1e-13)
+    assert ec == pytest.approx(2 * ec1, rel=1e-13)
+
+
+def test_pairs_f64_against_numpy_brute_force():
+    b = synth.water_box(8, 4)
+    L = b.box.astype(np.float64)
+    x = b.coords.astype(np.float64)
+    n = b.n_atoms
+    rc = 0.3
+    want = set()
+    for i in range(n):
+        for j in range(i + 1, n):
+            if i // 3 == j // 3:
+                continue
+            d = x[i] - x[j]
+            d -= L * np.round(d / L)
+            if math.sqrt((d * d).sum()) < rc:
+                want.add((i, j))
+    got = oracle.pairs_f64(x, b.box, rc, b.excl_off, b.excl_idx)
+    assert set(map(tuple, got.tolist())) == want
+    assert len(want) > 0
+
+
+def test_pairs_f32_differs_from_f64_only_at_the_cutoff(box512):
+    b = box512
+    rc = 0.9
+    p32 = set(map(tuple, oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx).tolist()))
+    p64 = set(map(tuple, oracle.pairs_f64(b.coords, b.box, rc, b.excl_off, b.excl_idx).tolist()))
+    x = b.coords.astype(np.float64)
+    L = b.box.astype(np.float64)
+    for (i, j) in p32 ^ p64:
+        d = x[i] - x[j]
+        d -= L * np.round(d / L)
+        assert abs(math.sqrt((d * d).sum()) - rc) < 1e-5
+    assert len(p32 ^ p64) <= 5
+
+
+def test_pair_count_matches_density(box512):
+    """Half-pairs per atom within rc ~ rho (2/3) pi rc^3, minus one excluded pair per atom."""
+    b = synth.water_box(32000, 2)
+    _, _, _, n = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, 1.0, 3.1234,
+                                      b.excl_off, b.excl_idx)
+    rho = b.n_atoms / float(b.box[0]) ** 3
+    expect = rho * (2.0 / 3.0) * math.pi * 1.0 ** 3 - 1.0
+    assert n / b.n_atoms == pytest.approx(expect, rel=0.02)
