@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the short-range nonbonded path on one GB300 (or N replicas).
+
+Workload (the production-size configuration): a 96,000-atom rigid 3-site
+water box (32,000 waters, L = 9.858 nm), rc = 1.0 nm, rlist = 1.1 nm,
+r_inner = 1.04 nm, rolling prune every 10 evaluations. One step = one
+trajectory of 100 force + energy evaluations on a Gaussian random walk
+(sigma = 0.001 nm per component per frame), with the pair search and the
+prunes the schedule calls for. All frames are resident in HBM before the
+timed region; L2 is flushed (256 MiB write) between steps.
+
+Metric: in-range pairs per second (pairs within rc counted by the force
+kernel, summed over the 100 evaluations, divided by the step time) and
+microseconds per force evaluation.
+
+``--impl reference`` times the CPU FP64 oracle (all host cores) on the same
+workload instead: each step is one full force + energy evaluation of one
+frame.
+
+Under torchrun each rank runs an independent replica (its own box seed);
+there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "nonbonded pairs/s & µs/force-eval at 96k atoms; batched & backward vs plain"
+UNIT = "pairs/s"
+N_WATERS = 32000
+RC, RLIST, R_INNER = 1.0, 1.1, 1.04
+PRUNE_INTERVAL = 10
+SIGMA = 0.001
+# FP32 operations per in-range pair in the force + energy formula as the
+# kernel evaluates it (FMA = 2): see DESIGN.md, "Roofline".
+FLOPS_PER_PAIR = 66
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_desc(evals: int) -> dict:
+    L = synth.box_edge(N_WATERS)
+    return {
+        "workload": (f"water96k: 96,000-atom rigid 3-site water box ({N_WATERS} waters, L={L:.3f} nm), "
+                     f"rc {RC} / rlist {RLIST} / r_inner {R_INNER} nm, prune every {PRUNE_INTERVAL} evals, "
+                     f"{evals} force+energy evals per step on a sigma={SIGMA} nm random walk"),
+        "n_atoms": 3 * N_WATERS,
+        "evals_per_step": evals,
+        "cache": "L2 flushed (256 MiB write) between timed steps",
+    }
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--evals", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- distributed
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- oracle timing
+
+def time_oracle(box, frames, evals_budget_s: float = 15.0, max_evals: int = 20):
+    """Oracle (FP64, all host cores) pairs/s on whole frames of the workload."""
+    import oracle
+    beta = synth.ewald_beta(RC)
+    oracle.energy_forces(frames[0], box.q, box.type, box.ljparams, box.box, RC, beta, box.excl_off,
+                         box.excl_idx)  # warm: builds/loads the library
+    pairs = 0
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_evals and (time.perf_counter() - t0) < evals_budget_s:
+        _, _, _, p = oracle.energy_forces(frames[n % len(frames)], box.q, box.type, box.ljparams, box.box, RC,
+                                          beta, box.excl_off, box.excl_idx)
+        pairs += p
+        n += 1
+    dt = time.perf_counter() - t0
+    return pairs / dt, n, dt, oracle.threads()
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores (rank 0 only), same metric and config."""
+    if rank != 0:
+        return
+    import oracle
+    box = synth.water_box(N_WATERS, 2)
+    frames = synth.random_walk_frames(box, max(args.steps + args.warmup, 1), SIGMA, seed=2)
+    beta = synth.ewald_beta(RC)
+    times, pairs = [], []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, _, p = oracle.energy_forces(frames[s % len(frames)], box.q, box.type, box.ljparams, box.box, RC,
+                                          beta, box.excl_off, box.excl_idx)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            pairs.append(p)
+    value = sum(pairs) / sum(times)
+    cores = oracle.threads()
+    sample = "one full force+energy evaluation of one 96,000-atom frame per step (cell list, FP64)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+
+def load_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, if it matches the kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in ("nb_force.cu", "nb_pair.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2405_01420_gb300", "csrc", f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec.get("bytes_per_launch_96k")
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2405_01420_gb300 import nb
+    from paper_2405_01420_gb300.engine import NonbondedEngine
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nb.load_library()
+    box = synth.water_box(N_WATERS, 2 + rank)
+    frames = synth.random_walk_frames(box, args.evals, SIGMA, seed=2 + rank)
+    N = box.n_atoms
+    beta = synth.ewald_beta(RC)
+    frames_d = torch.from_numpy(frames).to(dev)
+    q = torch.from_numpy(box.q).to(dev)
+    typ = torch.from_numpy(box.type).to(dev)
+    lj = torch.from_numpy(box.ljparams).to(dev)
+    eo = torch.from_numpy(box.excl_off).to(dev)
+    ei = torch.from_numpy(box.excl_idx).to(dev)
+    forces = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    energies = torch.zeros((args.evals, 2), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    eng = NonbondedEngine(N, box.box, RC, beta, RLIST, R_INNER, PRUNE_INTERVAL, eo, ei)
+
+    def restart():
+        eng.evals_since_search = None
+        eng.interval = PRUNE_INTERVAL
+        eng.n_search = eng.n_prune = 0
+
+    def one_step(frame_src, kernel_events=None, out_forces=None):
+        restart()
+        for i in range(args.evals):
+            if kernel_events is not None:
+                nb.nb_set_timing_events(eng.pl.handle, *kernel_events[i])
+            x = frame_src(i)
+            eng.compute(x, q, typ, lj, forces, energies[i])
+            if out_forces is not None:
+                out_forces(i)
+        if kernel_events is not None:
+            nb.nb_set_timing_events(eng.pl.handle, None, None)
+
+    # untimed pass: in-range pairs of each evaluation (synchronises every eval)
+    restart()
+    pairs = []
+    for i in range(args.evals):
+        eng.compute(frames_d[i], q, typ, lj, forces, energies[i])
+        pairs.append(eng.pl.stats()["pairs_last"])
+    assert eng.check() == 0, "device error word set in the counting pass"
+    pairs_per_step = float(sum(pairs))
+
+    for _ in range(args.warmup):
+        one_step(lambda i: frames_d[i])
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.evals)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    step_ms, kern_ms = [], []
+    searches = prunes = 0
+    if sampler:
+        sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        one_step(lambda i: frames_d[i], kernel_events=ev)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(t0.elapsed_time(t1))
+        kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        searches, prunes = eng.n_search, eng.n_prune
+    clocks = sampler.stop() if sampler else None
+    err = eng.check()
+    assert err == 0, f"device error word 0x{err:x} in the timed steps"
+
+    ms_step = dist_max(statistics.mean(step_ms), world)
+    total_pairs = dist_sum(pairs_per_step * args.steps, world)
+    value = total_pairs / (dist_max(sum(step_ms), world) / 1e3)
+    kern_ms_per_launch = statistics.mean(kern_ms) / args.evals
+    pairs_per_eval = pairs_per_step / args.evals
+
+    # end to end through the public API: frames from pinned host memory each
+    # eval, forces and energies back to pinned host memory each eval
+    e2e = None
+    if not args.no_e2e:
+        frames_h = torch.from_numpy(frames).pin_memory()
+        f_out = torch.empty((args.evals, N, 3), dtype=torch.float32).pin_memory()
+        e_out = torch.empty((args.evals, 2), dtype=torch.float64).pin_memory()
+        x_dev = torch.empty((N, 3), dtype=torch.float32, device=dev)
+
+        def src(i):
+            x_dev.copy_(frames_h[i], non_blocking=True)
+            return x_dev
+
+        def sink(i):
+            f_out[i].copy_(forces, non_blocking=True)
+            e_out[i].copy_(energies[i], non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            one_step(src, out_forces=sink)
+        e2e_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier(world)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one_step(src, out_forces=sink)
+            b.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        e2e_value = total_pairs / (dist_max(sum(e2e_ms), world) / 1e3)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": args.evals * N * 12,
+               "d2h_bytes_per_step": args.evals * (N * 12 + 16)}
+        assert eng.check() == 0
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n_ev, dt, cores = time_oracle(box, frames)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_ev} full force+energy evaluations of frames of the same 96,000-atom trajectory "
+                         f"(cell list, FP64), {dt:.1f} s"}
+
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak_max = sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs_per_eval / (kern_ms_per_launch / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
+            "traffic": load_traffic(),
+            "kernel": "k_force (LJ + Ewald real-space, energies on)",
+            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x 2070 MHz (max SM clock)",
+            "kernel_us_per_launch": 1e3 * kern_ms_per_launch}
+    if clocks and clocks.get("sm_mhz"):
+        peak_clk = sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12
+        roof["frac_at_measured_clock"] = achieved / peak_clk
+    n_launch_search, n_launch_prune, n_launch_force = 5, 2, 3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_desc(args.evals), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "us_per_eval": 1e3 * ms_step / args.evals,
+        "pairs_per_eval": pairs_per_eval,
+        "searches_per_step": searches, "prunes_per_step": prunes,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": n_launch_search * searches + n_launch_prune * prunes + n_launch_force * args.evals,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

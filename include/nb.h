@@ -1,0 +1,212 @@
+/*
+ * nb.h - C ABI of the GB300 short-range nonbonded library (libnb.so).
+ *
+ * The library computes short-range nonbonded forces and energies of a
+ * periodic particle system: Lennard-Jones plus Ewald real-space Coulomb
+ * (erfc) with intra-molecular exclusions, over a cluster-pair (8x8) Verlet
+ * list with a rolling prune. This is the "NBNXM" short-range non-bonded
+ * kernel that the paper identifies as the rate limiter of a GPU MD step
+ * (§III-A, Fig. 2 and the text after it; §IV-A, §IV-B), together with the
+ * pair search that feeds it and the prune-only kernel that re-prunes the
+ * buffered list ("pair list buffer", "list range", "Prune-only kernel",
+ * §III-A). The paper gives no formulas; the arithmetic follows textbook LJ
+ * and Ewald real-space physics:
+ *
+ *   E_LJ = sum_{i<j, not excluded, r < rc} C12_ij/r^12 - C6_ij/r^6
+ *                                          - (C12_ij/rc^12 - C6_ij/rc^6)
+ *   E_C  = f sum_{i<j, not excluded, r < rc} q_i q_j erfc(beta r)/r
+ *   F_i  = -dE/dx_i,   f = 138.935458 kJ mol^-1 nm e^-2
+ *
+ * Units: nm, e, kJ/mol; forces in kJ mol^-1 nm^-1. Box: orthorhombic,
+ * periodic in x, y and z, edges given on the host.
+ *
+ * Conventions for every function:
+ *   - Device pointers are CUDA device addresses owned by the caller; the
+ *     library never frees them and keeps no reference after the call
+ *     returns, except that launched work reads them until it completes on
+ *     the stream. Host pointers are read before the call returns.
+ *   - "stream" is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream. Work is stream-ordered; no call synchronises unless
+ *     its comment says it does.
+ *   - Every function returns NB_OK (0) or an NB_ERR_* code; nb_last_error()
+ *     then gives a message (thread-local). Nothing aborts or traps the GPU.
+ *     Errors found on the device (list overflow, non-finite coordinates,
+ *     a stale list) set bits in a sticky device error word that nb_status()
+ *     reads; the forces of a call that set an error bit are not valid.
+ *   - A pair list belongs to one device (the current device at creation)
+ *     and must be used from one stream at a time.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define NB_OK 0
+#define NB_ERR_ARG 1       /* invalid argument (sizes, NULL, box, radii) */
+#define NB_ERR_CUDA 2      /* a CUDA runtime call or launch failed */
+#define NB_ERR_CAPACITY 3  /* a size exceeds what the pair list was created for */
+#define NB_ERR_NONFINITE 4 /* reserved for host-side checks of non-finite input */
+#define NB_ERR_TIMEOUT 5   /* a bounded device wait gave up */
+#define NB_ERR_STATE 6     /* call out of order (e.g. nb_forces before nb_search) */
+#define NB_ERR_NOMEM 7     /* device allocation failed */
+
+/* Bits of the device error word returned by nb_status(). */
+#define NB_DEV_LIST_OVERFLOW 0x01u   /* list entries exceeded capacity_entries */
+#define NB_DEV_COLUMN_OVERFLOW 0x02u /* a grid column held more than 4096 atoms */
+#define NB_DEV_NONFINITE 0x04u       /* a coordinate was NaN or infinite */
+#define NB_DEV_STALE_SEARCH 0x08u    /* atoms moved more than (rlist - r)/2 since the search */
+#define NB_DEV_STALE_PRUNE 0x10u     /* atoms moved more than (r_inner - rc)/2 since the prune */
+#define NB_DEV_EXCL_OVERFLOW 0x20u   /* >256 exclusions in one 8-atom cluster, or an index outside [0, n) */
+#define NB_DEV_CLUSTER_OVERFLOW 0x40u /* more than 512 list entries for one i-cluster */
+#define NB_DEV_BAD_TYPE 0x80u         /* an LJ type outside [0, ntype) (treated as type 0) */
+
+/* Which list nb_pairlist_export() copies. */
+#define NB_LIST_OUTER 0 /* built by nb_search at rlist */
+#define NB_LIST_INNER 1 /* built by nb_prune at r_inner */
+
+typedef struct nb_pairlist nb_pairlist;
+
+/* Creation options. Zero-initialise and set what you need. */
+typedef struct {
+    size_t capacity_entries; /* list entries (8x8 cluster pairs) to reserve; 0 = automatic:
+                                200 per 8-atom cluster + 65536, enough for rlist <= ~1.3 nm
+                                at water density */
+    unsigned flags;          /* reserved, must be 0 */
+} nb_config;
+
+/* Host-side snapshot of a pair list (filled by nb_pairlist_stats). */
+typedef struct {
+    int n_atoms;
+    int n_clusters;          /* 8-atom clusters after the last search (incl. padding slots) */
+    int n_columns;           /* xy grid columns of the last search */
+    int has_inner;           /* 1 if nb_prune ran since the last search */
+    long long outer_entries; /* cluster pairs in the outer (rlist) list */
+    long long inner_entries; /* cluster pairs in the inner (r_inner) list */
+    long long capacity_entries;
+    long long pairs_last;    /* in-range atom pairs counted by the last nb_forces */
+    float rlist;             /* radius of the last search */
+    float r_inner;           /* radius of the last prune (0 if none) */
+    float max_disp_search;   /* largest atom displacement since the search, as seen by the last call */
+    float max_disp_prune;    /* largest atom displacement since the last prune, as seen by the last call */
+    unsigned error_word;     /* sticky device error bits (not cleared by this call) */
+} nb_stats;
+
+/* Library version string, e.g. "nb 0.1.0 sm_103a". */
+const char *nb_version(void);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *nb_last_error(void);
+
+/*
+ * Create a pair list for systems of exactly n_atoms atoms on the current
+ * device. Allocates all device buffers up front (cudaMalloc), so later calls
+ * allocate nothing and can be captured in a CUDA graph. cfg may be NULL.
+ * Errors: NB_ERR_ARG (n_atoms < 1), NB_ERR_NOMEM, NB_ERR_CUDA.
+ */
+int nb_pairlist_create(nb_pairlist **pl, int n_atoms, const nb_config *cfg);
+
+/* Free a pair list and its device buffers. Synchronises the device. NULL is a no-op. */
+int nb_pairlist_destroy(nb_pairlist *pl);
+
+/*
+ * Pair search (§III-A, "pair list buffer" / "list range"): grid-sort atoms
+ * into 8-atom clusters and build the outer cluster-pair list at radius
+ * rlist.
+ *   coords   device float[3*n_atoms], x,y,z per atom in original order;
+ *            any real values (wrapped into the box here).
+ *   box      HOST float[3], orthorhombic box edges; each > 2*rlist.
+ *   rlist    list radius (nm), > 0.
+ *   excl_off device int[n_atoms+1], excl_idx device int[excl_off[n]]:
+ *            symmetric exclusion lists in original atom indices (both
+ *            directions listed; self need not be). Both NULL = none.
+ * The list keeps each cluster pair (ci <= cj) once, with a periodic shift
+ * and a 64-bit mask of atom pairs that are real, not excluded and not
+ * duplicated. Mask bit a*8+b is atom a of ci with atom b of cj.
+ * After the search the forces use the outer list until nb_prune runs.
+ * Device errors: NB_DEV_LIST_OVERFLOW, NB_DEV_COLUMN_OVERFLOW,
+ * NB_DEV_NONFINITE, NB_DEV_EXCL_OVERFLOW, NB_DEV_CLUSTER_OVERFLOW.
+ */
+int nb_search(nb_pairlist *pl, const float *coords, const float *box, float rlist,
+              const int *excl_off, const int *excl_idx, void *stream);
+
+/*
+ * Rolling prune (§III-A, "Prune-only kernel"): from the outer list keep the
+ * cluster pairs with at least one masked-in atom pair closer than r_inner
+ * at the given coordinates, and store per-atom-pair in-range masks. The
+ * forces then use this inner list until the next nb_prune or nb_search.
+ *   coords device float[3*n_atoms] (current frame), r_inner in (0, rlist].
+ * Errors: NB_ERR_STATE before any search, NB_ERR_ARG for r_inner > rlist.
+ * Device errors: NB_DEV_STALE_SEARCH if atoms moved more than
+ * (rlist - r_inner)/2 since the search, NB_DEV_NONFINITE.
+ */
+int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, void *stream);
+
+/*
+ * Forces and energies (§III-A, "NBNXM (short-range non-bonded forces)"),
+ * FP32 arithmetic, FP64 energy reduction.
+ *   coords   device float[3*n_atoms], current frame, original order.
+ *   q        device float[n_atoms] charges (e).
+ *   type     device int[n_atoms] LJ type in [0, ntype).
+ *   ntype    1..32.
+ *   ljparams device float[ntype*ntype*2] = (C6, C12) for type pair
+ *            (ti, tj) at index 2*(ti*ntype + tj); symmetric.
+ *   rc       cutoff (nm); <= r_inner if pruned, else <= rlist.
+ *   beta     Ewald splitting parameter (nm^-1), 0 <= beta*rc <= 3.2.
+ *   forces   device float[3*n_atoms], overwritten, original order.
+ *   energies device double[2] = {E_LJ, E_C}, overwritten; may be NULL
+ *            (forces only).
+ * A pair counts iff its mask bit is set and r2 < fl(rc*rc) in FP32, with
+ * d = (y_a - y_b) + S and r2 = fma(dz,dz,fma(dy,dy,dx*dx)); y is the image
+ * of the current position nearest to the search-time wrapped position.
+ * Errors: NB_ERR_STATE before any search; NB_ERR_ARG for bad ntype, rc, beta.
+ * Device errors: NB_DEV_STALE_SEARCH / NB_DEV_STALE_PRUNE when the
+ * displacement since the search / prune exceeds (rlist-rc)/2 / (r_inner-rc)/2
+ * (minus 1e-5 nm), NB_DEV_NONFINITE, NB_DEV_BAD_TYPE.
+ */
+int nb_forces(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
+              const float *ljparams, float rc, float beta, float *forces, double *energies,
+              void *stream);
+
+/*
+ * Read the sticky device error word into *error_word (NB_DEV_* bits).
+ * Synchronises the stream. clear != 0 resets the word after reading.
+ */
+int nb_status(nb_pairlist *pl, unsigned *error_word, int clear, void *stream);
+
+/* Fill *out with list sizes, counters and radii. Synchronises the stream. */
+int nb_pairlist_stats(nb_pairlist *pl, nb_stats *out, void *stream);
+
+/*
+ * Copy a list to HOST arrays (for tests and inspection). Synchronises.
+ *   which  NB_LIST_OUTER or NB_LIST_INNER.
+ *   ci, cj, shift: int[cap]; mask: unsigned long long[cap]. shift is
+ *   (sx+1)*9 + (sy+1)*3 + (sz+1) with S = (sx*Lx, sy*Ly, sz*Lz) added to
+ *   (y_a - y_b), a in ci, b in cj.
+ *   *n_out receives the entry count (also when it exceeds cap; then only
+ *   cap entries are written and NB_ERR_CAPACITY is returned).
+ *   perm: int[perm_cap] or NULL: atom of each cluster slot (slot = 8*c + a),
+ *   -1 for padding; *n_slots receives 8*n_clusters.
+ */
+int nb_pairlist_export(nb_pairlist *pl, int which, int *ci, int *cj, int *shift,
+                       unsigned long long *mask, size_t cap, size_t *n_out, int *perm,
+                       size_t perm_cap, size_t *n_slots, void *stream);
+
+/*
+ * Timing hook (no counterpart in the paper; measurement only): every later
+ * nb_forces call records the caller's CUDA events `start` right before and
+ * `stop` right after its force kernel, on the call's stream, so that the
+ * kernel alone can be timed with cudaEventElapsedTime. Both NULL disables.
+ * The events are caller-owned (cudaEvent_t passed as void*).
+ */
+int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NB_H */

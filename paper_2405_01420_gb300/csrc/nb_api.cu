@@ -1,0 +1,321 @@
+// C ABI of the nonbonded library (declared in include/nb.h): argument
+// checks, device buffer ownership, grid sizing and the order of launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int ok() {
+    g_err.clear();
+    return NB_OK;
+}
+
+#define NB_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail(NB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Makes the pair list's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) switched = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
+void free_buffers(nb_pairlist *pl) {
+    void *bufs[] = {pl->st,     pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->atom_col,
+                    pl->atom_slot, pl->xw,     pl->keys,           pl->perm,           pl->pos,
+                    pl->xref,   pl->xprune,    pl->xq,             pl->tsort,          pl->fsort,
+                    pl->bbox,   pl->outer,     pl->inner,          pl->ci_start,       pl->ci_len_outer,
+                    pl->ci_len_inner};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+}
+
+template <class T>
+bool alloc(T **p, size_t count, size_t *total) {
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    *total += bytes;
+    return cudaMalloc((void **)p, bytes) == cudaSuccess;
+}
+
+float sq_nonneg(double x) { return x > 0.0 ? (float)(x * x) : 0.0f; }
+
+// Displacement budget: half the radius difference, less 1e-5 nm so that
+// FP32 rounding of the distances cannot use up the margin.
+float stale_bound2(double r_big, double r_small) { return sq_nonneg(0.5 * (r_big - r_small) - 1e-5); }
+
+}  // namespace
+
+extern "C" const char *nb_version(void) { return "nb 0.1.0 sm_103a"; }
+
+extern "C" const char *nb_last_error(void) { return g_err.c_str(); }
+
+extern "C" int nb_pairlist_create(nb_pairlist **out, int n_atoms, const nb_config *cfg) {
+    if (!out) return fail(NB_ERR_ARG, "nb_pairlist_create: out is NULL");
+    *out = nullptr;
+    if (n_atoms < 1) return fail(NB_ERR_ARG, "nb_pairlist_create: n_atoms = %d < 1", n_atoms);
+    if (cfg && cfg->flags != 0u) return fail(NB_ERR_ARG, "nb_pairlist_create: flags must be 0");
+    nb_pairlist *pl = new (std::nothrow) nb_pairlist;
+    if (!pl) return fail(NB_ERR_NOMEM, "nb_pairlist_create: host allocation failed");
+    std::memset(pl, 0, sizeof(*pl));
+    NB_CUDA(cudaGetDevice(&pl->device));
+    NB_CUDA(cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device));
+    const long long n = n_atoms;
+    const long long nclus = (n + NB_CLUSTER - 1) / NB_CLUSTER;
+    pl->n_atoms = n_atoms;
+    pl->ncol_max = (int)nclus;
+    pl->nc_max = (int)(nclus + pl->ncol_max);
+    size_t cap = (cfg && cfg->capacity_entries) ? cfg->capacity_entries : (size_t)nclus * 200 + 65536;
+    if (cap >= (size_t)1 << 31) {
+        delete pl;
+        return fail(NB_ERR_ARG, "nb_pairlist_create: capacity_entries %zu >= 2^31", cap);
+    }
+    pl->cap = cap;
+    const size_t nslot = (size_t)pl->nc_max * NB_CLUSTER;
+    size_t total = 0;
+    bool good = alloc(&pl->st, 1, &total) && alloc(&pl->col_count, pl->ncol_max, &total) &&
+                alloc(&pl->col_atom_start, pl->ncol_max + 1, &total) &&
+                alloc(&pl->col_clus_start, pl->ncol_max + 1, &total) && alloc(&pl->atom_col, n, &total) &&
+                alloc(&pl->atom_slot, n, &total) && alloc(&pl->xw, n, &total) && alloc(&pl->keys, n, &total) &&
+                alloc(&pl->perm, nslot, &total) && alloc(&pl->pos, n, &total) && alloc(&pl->xref, nslot, &total) &&
+                alloc(&pl->xprune, nslot, &total) && alloc(&pl->xq, nslot, &total) &&
+                alloc(&pl->tsort, nslot, &total) && alloc(&pl->fsort, nslot, &total) &&
+                alloc(&pl->bbox, 2 * (size_t)pl->nc_max, &total) && alloc(&pl->outer, cap, &total) &&
+                alloc(&pl->inner, cap, &total) && alloc(&pl->ci_start, pl->nc_max, &total) &&
+                alloc(&pl->ci_len_outer, pl->nc_max, &total) && alloc(&pl->ci_len_inner, pl->nc_max, &total);
+    if (!good) {
+        cudaGetLastError();  // clear the allocation error
+        free_buffers(pl);
+        delete pl;
+        return fail(NB_ERR_NOMEM, "nb_pairlist_create: cudaMalloc of %zu bytes failed", total);
+    }
+    // Defined contents for everything a kernel may read before the first search writes it.
+    NB_CUDA(cudaMemset(pl->st, 0, sizeof(nb_dev_state)));
+    NB_CUDA(cudaMemset(pl->pos, 0, sizeof(int) * (size_t)n));
+    NB_CUDA(cudaMemset(pl->perm, 0xff, sizeof(int) * nslot));
+    NB_CUDA(cudaMemset(pl->ci_start, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->ci_len_outer, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->ci_len_inner, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->fsort, 0, sizeof(float4) * nslot));
+    NB_CUDA(cudaDeviceSynchronize());
+    *out = pl;
+    return ok();
+}
+
+extern "C" int nb_pairlist_destroy(nb_pairlist *pl) {
+    if (!pl) return ok();
+    DeviceGuard g(pl->device);
+    cudaDeviceSynchronize();
+    free_buffers(pl);
+    delete pl;
+    return ok();
+}
+
+extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box, float rlist,
+                         const int *excl_off, const int *excl_idx, void *stream) {
+    if (!pl || !coords || !box) return fail(NB_ERR_ARG, "nb_search: NULL pair list, coords or box");
+    if ((excl_off == nullptr) != (excl_idx == nullptr))
+        return fail(NB_ERR_ARG, "nb_search: excl_off and excl_idx must both be given or both NULL");
+    if (!(rlist > 0.0f) || !std::isfinite(rlist)) return fail(NB_ERR_ARG, "nb_search: rlist = %g", rlist);
+    for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(box[k]) || !(box[k] > 2.0f * rlist))
+            return fail(NB_ERR_ARG, "nb_search: box[%d] = %g must exceed 2*rlist = %g", k, box[k], 2.0f * rlist);
+    }
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < 3; ++k) pl->box[k] = box[k];
+
+    // xy columns of ~cubic 8-atom cells at the mean density
+    const double Lx = box[0], Ly = box[1], Lz = box[2];
+    const double n = pl->n_atoms;
+    const double side = std::cbrt(NB_CLUSTER * Lx * Ly * Lz / n);
+    int ncx = std::max(1, (int)std::floor(Lx / side));
+    int ncy = std::max(1, (int)std::floor(Ly / side));
+    while (n / ((double)ncx * ncy) > NB_MAX_COL_ATOMS / 4 && (long long)(ncx + 1) * (ncy + 1) <= pl->ncol_max) {
+        ++ncx;
+        ++ncy;
+    }
+    while ((long long)ncx * ncy > pl->ncol_max) {
+        if (ncx >= ncy) --ncx; else --ncy;
+    }
+    pl->ncx = ncx;
+    pl->ncy = ncy;
+    pl->ncol = ncx * ncy;
+
+    NB_CUDA(cudaMemsetAsync(&pl->st->list_count, 0, sizeof(unsigned long long), s));
+    NB_CUDA(nb_launch_grid_sort(pl, coords, (float)(ncx / Lx), (float)(ncy / Ly), s));
+
+    // The bounding-box test uses a radius inflated by a few ulps of the box
+    // edge, so that every pair within rlist under the FP32 distance contract
+    // is in the list (the list is a buffered superset anyway).
+    const float lmax = std::max(box[0], std::max(box[1], box[2]));
+    const double ulp = (double)std::nextafter(lmax, 2.0f * lmax) - lmax;
+    const double rle = rlist + std::max(1e-5, 8.0 * ulp) + 1e-6 * rlist;
+    const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
+    const float rl_col = (float)(rle + 1e-3);
+    NB_CUDA(nb_launch_search(pl, excl_off, excl_idx, rl2, rl_col, s));
+    pl->searched = 1;
+    pl->has_inner = 0;
+    pl->rlist = rlist;
+    pl->r_inner = 0.0f;
+    return ok();
+}
+
+extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, void *stream) {
+    if (!pl || !coords) return fail(NB_ERR_ARG, "nb_prune: NULL pair list or coords");
+    if (!pl->searched) return fail(NB_ERR_STATE, "nb_prune: no search yet");
+    if (!(r_inner > 0.0f) || !(r_inner <= pl->rlist))
+        return fail(NB_ERR_ARG, "nb_prune: r_inner = %g must be in (0, rlist = %g]", r_inner, pl->rlist);
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(nb_launch_gather(pl, coords, nullptr, nullptr, 1, 1, nullptr, s));
+    const float r2cut = r_inner * r_inner;
+    NB_CUDA(nb_launch_prune(pl, r2cut, stale_bound2(pl->rlist, r_inner), s));
+    pl->has_inner = 1;
+    pl->r_inner = r_inner;
+    return ok();
+}
+
+extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
+                         const float *ljparams, float rc, float beta, float *forces, double *energies,
+                         void *stream) {
+    if (!pl || !coords || !q || !type || !ljparams || !forces)
+        return fail(NB_ERR_ARG, "nb_forces: NULL argument");
+    if (!pl->searched) return fail(NB_ERR_STATE, "nb_forces: no search yet");
+    if (ntype < 1 || ntype > NB_MAX_TYPES) return fail(NB_ERR_ARG, "nb_forces: ntype = %d not in [1, %d]", ntype, NB_MAX_TYPES);
+    const float rmax = pl->has_inner ? pl->r_inner : pl->rlist;
+    if (!(rc > 0.0f) || !(rc <= rmax))
+        return fail(NB_ERR_ARG, "nb_forces: rc = %g must be in (0, %g] (list radius)", rc, rmax);
+    if (!(beta >= 0.0f) || !((double)beta * rc <= 3.2))
+        return fail(NB_ERR_ARG, "nb_forces: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, energies, s));
+    if (pl->ev_start) NB_CUDA(cudaEventRecord(pl->ev_start, s));
+    NB_CUDA(nb_launch_force(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->rlist, rc),
+                            stale_bound2(pl->r_inner, rc), s));
+    if (pl->ev_stop) NB_CUDA(cudaEventRecord(pl->ev_stop, s));
+    NB_CUDA(nb_launch_scatter(pl, forces, s));
+    return ok();
+}
+
+extern "C" int nb_status(nb_pairlist *pl, unsigned *error_word, int clear, void *stream) {
+    if (!pl || !error_word) return fail(NB_ERR_ARG, "nb_status: NULL argument");
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned w = 0;
+    NB_CUDA(cudaMemcpyAsync(&w, &pl->st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    if (clear) NB_CUDA(cudaMemsetAsync(&pl->st->err, 0, sizeof(unsigned), s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    *error_word = w;
+    return ok();
+}
+
+extern "C" int nb_pairlist_stats(nb_pairlist *pl, nb_stats *out, void *stream) {
+    if (!pl || !out) return fail(NB_ERR_ARG, "nb_pairlist_stats: NULL argument");
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    nb_dev_state st;
+    NB_CUDA(cudaMemcpyAsync(&st, pl->st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    std::memset(out, 0, sizeof(*out));
+    out->n_atoms = pl->n_atoms;
+    out->n_clusters = pl->searched ? st.nc : 0;
+    out->n_columns = pl->searched ? pl->ncol : 0;
+    out->has_inner = pl->has_inner;
+    out->outer_entries = (long long)st.list_count;
+    out->inner_entries = pl->has_inner ? (long long)st.inner_count : 0;
+    out->capacity_entries = (long long)pl->cap;
+    out->pairs_last = (long long)st.npairs;
+    out->rlist = pl->rlist;
+    out->r_inner = pl->r_inner;
+    float ds, dp;
+    std::memcpy(&ds, &st.last_d2_search, sizeof(float));
+    std::memcpy(&dp, &st.last_d2_prune, sizeof(float));
+    out->max_disp_search = std::sqrt(ds);
+    out->max_disp_prune = std::sqrt(dp);
+    out->error_word = st.err;
+    return ok();
+}
+
+extern "C" int nb_pairlist_export(nb_pairlist *pl, int which, int *ci, int *cj, int *shift,
+                                  unsigned long long *mask, size_t cap, size_t *n_out, int *perm,
+                                  size_t perm_cap, size_t *n_slots, void *stream) {
+    if (!pl || !n_out) return fail(NB_ERR_ARG, "nb_pairlist_export: NULL argument");
+    if (cap > 0 && (!ci || !cj || !shift || !mask)) return fail(NB_ERR_ARG, "nb_pairlist_export: NULL output arrays");
+    if (which != NB_LIST_OUTER && which != NB_LIST_INNER) return fail(NB_ERR_ARG, "nb_pairlist_export: bad list id %d", which);
+    if (!pl->searched) return fail(NB_ERR_STATE, "nb_pairlist_export: no search yet");
+    if (which == NB_LIST_INNER && !pl->has_inner) return fail(NB_ERR_STATE, "nb_pairlist_export: no prune since the search");
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    nb_dev_state st;
+    NB_CUDA(cudaMemcpyAsync(&st, pl->st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    const int nc = st.nc;
+    const size_t used = std::min((size_t)st.list_count, pl->cap);
+    std::vector<int> start(nc), len(nc);
+    std::vector<int4> ent(used);
+    NB_CUDA(cudaMemcpyAsync(start.data(), pl->ci_start, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(len.data(), which == NB_LIST_OUTER ? pl->ci_len_outer : pl->ci_len_inner,
+                            sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    if (used)
+        NB_CUDA(cudaMemcpyAsync(ent.data(), which == NB_LIST_OUTER ? pl->outer : pl->inner, sizeof(int4) * used,
+                                cudaMemcpyDeviceToHost, s));
+    const size_t nslot = (size_t)nc * NB_CLUSTER;
+    if (n_slots) *n_slots = nslot;
+    if (perm && perm_cap >= nslot)
+        NB_CUDA(cudaMemcpyAsync(perm, pl->perm, sizeof(int) * nslot, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    size_t k = 0;
+    for (int c = 0; c < nc; ++c) {
+        for (int t = 0; t < len[c]; ++t, ++k) {
+            if (k >= cap) continue;
+            const size_t idx = (size_t)start[c] + t;
+            if (idx >= used) return fail(NB_ERR_STATE, "nb_pairlist_export: entry %zu beyond the list", idx);
+            const int4 e = ent[idx];
+            ci[k] = c;
+            cj[k] = e.x;
+            shift[k] = e.y;
+            mask[k] = (unsigned long long)(unsigned)e.z | ((unsigned long long)(unsigned)e.w << 32);
+        }
+    }
+    *n_out = k;
+    if (perm && perm_cap < nslot) return fail(NB_ERR_CAPACITY, "nb_pairlist_export: perm_cap %zu < %zu slots", perm_cap, nslot);
+    if (k > cap) return fail(NB_ERR_CAPACITY, "nb_pairlist_export: %zu entries > cap %zu", k, cap);
+    return ok();
+}
+
+extern "C" int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop) {
+    if (!pl) return fail(NB_ERR_ARG, "nb_set_timing_events: NULL pair list");
+    if ((start == nullptr) != (stop == nullptr))
+        return fail(NB_ERR_ARG, "nb_set_timing_events: give both events or neither");
+    pl->ev_start = (cudaEvent_t)start;
+    pl->ev_stop = (cudaEvent_t)stop;
+    return ok();
+}

@@ -1,0 +1,355 @@
+// Nonbonded forces and energies over the cluster-pair list (the NBNXM
+// kernel of §III-A), plus the gather that feeds it and the permute-back
+// that follows it.
+//
+// k_gather   coords/q/type (original order) -> xq (float4 y,q) / tsort in
+//            cluster order; y is the image nearest the search-frame
+//            position. Zeroes the force accumulators, tracks the largest
+//            displacement since the search and since the last prune.
+// k_force    persistent grid, one warp per i-cluster taken from a work
+//            counter. Lane l owns j-atom b = l & 7 and i-atoms l >> 3 and
+//            (l >> 3) + 4, i.e. exactly mask bits l (low word) and 32 + l
+//            (high word). i-forces stay in registers for the whole list of
+//            ci; j-forces are reduced across the four lanes sharing b with
+//            a reduce-scatter (3 shuffles) and added with one atomic per
+//            (atom, component) per 8x8 tile. Half-tiles (mask word 0) are
+//            skipped by a warp-uniform branch. Energies: per-lane FP32 per
+//            tile, Kahan-compensated across tiles, FP64 per
+//            i-cluster and across the grid.
+// k_scatter  forces of cluster slots -> original atom order.
+#include "nb_pair.cuh"
+
+namespace {
+
+constexpr int kForceThreads = 256;
+
+struct GatherParams {
+    const int *perm;
+    const float *coords;
+    const float *q;
+    const int *type;
+    const float4 *xref;
+    float4 *xprune;
+    float4 *xq;
+    int *tsort;
+    float4 *fsort;
+    nb_dev_state *st;
+    double *energies;
+    float Lx, Ly, Lz;
+    int snapshot;
+    int ntype;
+};
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_gather(GatherParams p) {
+    const int nslot = p.st->nc * NB_CLUSTER;
+    float d2s_max = 0.0f, d2p_max = 0.0f;
+    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nslot; slot += gridDim.x * blockDim.x) {
+        const int atom = p.perm[slot];
+        p.fsort[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (atom < 0) continue;
+        const float4 r = p.xref[slot];
+        float x = p.coords[3 * atom + 0], y = p.coords[3 * atom + 1], z = p.coords[3 * atom + 2];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            atomicOr(&p.st->err, NB_DEV_NONFINITE);
+            x = r.x;
+            y = r.y;
+            z = r.z;
+        }
+        const float yx = nb_image(x, r.x, p.Lx), yy = nb_image(y, r.y, p.Ly), yz = nb_image(z, r.z, p.Lz);
+        p.xq[slot] = make_float4(yx, yy, yz, p.q ? p.q[atom] : 0.0f);
+        if (p.type) {
+            int t = p.type[atom];
+            if (t < 0 || t >= p.ntype) {  // keep the LJ table lookup in bounds
+                atomicOr(&p.st->err, NB_DEV_BAD_TYPE);
+                t = 0;
+            }
+            p.tsort[slot] = t;
+        }
+        float ex = yx - r.x, ey = yy - r.y, ez = yz - r.z;
+        d2s_max = fmaxf(d2s_max, ex * ex + ey * ey + ez * ez);
+        if (p.snapshot) {
+            p.xprune[slot] = make_float4(yx, yy, yz, 0.0f);
+        } else {
+            const float4 pr = p.xprune[slot];
+            ex = yx - pr.x;
+            ey = yy - pr.y;
+            ez = yz - pr.z;
+            d2p_max = fmaxf(d2p_max, ex * ex + ey * ey + ez * ez);
+        }
+    }
+    d2s_max = warp_max(d2s_max);
+    d2p_max = warp_max(d2p_max);
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative floats order like their bit patterns
+        if (d2s_max > 0.0f) atomicMax(&p.st->cur_d2_search, __float_as_uint(d2s_max));
+        if (d2p_max > 0.0f) atomicMax(&p.st->cur_d2_prune, __float_as_uint(d2p_max));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.st->work = 0u;
+        p.st->npairs = 0ull;
+        if (p.snapshot) {  // a prune follows this gather
+            p.st->work_prune = 0u;
+            p.st->inner_count = 0ull;
+        }
+        if (p.energies) {
+            p.energies[0] = 0.0;
+            p.energies[1] = 0.0;
+        }
+    }
+}
+
+struct ForceParams {
+    const float4 *xq;
+    const int *tsort;
+    float *fsort;  // float4 per slot, viewed as floats
+    const int4 *list;
+    const int *ci_start;
+    const int *ci_len;
+    const float *ljparams;
+    nb_dev_state *st;
+    double *energies;
+    int ntype;
+    float rc6inv, rc12inv;  // 1/rc^6, 1/rc^12 for the LJ potential shift
+    float Lx, Ly, Lz;
+    nb_coul cc;
+    float stale_search2, stale_prune2;
+    int has_inner;
+};
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(kForceThreads) k_force(ForceParams p) {
+    __shared__ float4 s_lj[NB_MAX_TYPES * NB_MAX_TYPES];
+    __shared__ double s_red[2][kForceThreads / 32];
+    __shared__ unsigned long long s_cnt[kForceThreads / 32];
+    const int nt2 = p.ntype * p.ntype;
+    for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
+        const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
+        s_lj[k] = make_float4(c6, c12, c12 * p.rc12inv - c6 * p.rc6inv, 0.0f);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // The gather of this call has finished; record its displacements and
+        // check them against the list buffers.
+        const unsigned ds = p.st->cur_d2_search, dp = p.st->cur_d2_prune;
+        p.st->last_d2_search = ds;
+        p.st->last_d2_prune = dp;
+        p.st->cur_d2_search = 0u;
+        p.st->cur_d2_prune = 0u;
+        if (!p.has_inner && __uint_as_float(ds) > p.stale_search2) atomicOr(&p.st->err, NB_DEV_STALE_SEARCH);
+        if (p.has_inner && __uint_as_float(dp) > p.stale_prune2) atomicOr(&p.st->err, NB_DEV_STALE_PRUNE);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int b = lane & 7, a1 = lane >> 3, a2 = a1 + 4;
+    const unsigned lanebit = 1u << lane;
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    const int comp = (hi16 ? 2 : 0) + (hi8 ? 1 : 0);  // component this lane adds after the reduce-scatter
+    const int nc = p.st->nc;
+    double ecd = 0.0, eljd = 0.0;
+    unsigned cnt = 0;
+
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(&p.st->work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= (unsigned)nc) break;
+        const int ci = (int)w;
+        const int k0 = p.ci_start[ci], k1 = k0 + p.ci_len[ci];
+        const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
+        const float qi1 = xi1.w * NB_COULOMB_F, qi2 = xi2.w * NB_COULOMB_F;
+        const int tr1 = p.tsort[ci * NB_CLUSTER + a1] * p.ntype;
+        const int tr2 = p.tsort[ci * NB_CLUSTER + a2] * p.ntype;
+        float3 fi1 = make_float3(0.0f, 0.0f, 0.0f), fi2 = make_float3(0.0f, 0.0f, 0.0f);
+        float ec = 0.0f, ecomp = 0.0f, elj = 0.0f, eljcomp = 0.0f;
+
+        for (int k = k0; k < k1; ++k) {
+            const int4 e = p.list[k];
+            const int cj = e.x, sidx = e.y;
+            const unsigned mlo = (unsigned)e.z, mhi = (unsigned)e.w;
+            const int sj = cj * NB_CLUSTER + b;
+            const float4 xj = p.xq[sj];
+            const int tj = p.tsort[sj];
+            float3 fj = make_float3(0.0f, 0.0f, 0.0f);
+            float ect = 0.0f, eljt = 0.0f;
+            if (sidx == NB_SHIFT_CENTER) {
+                if (mlo) cnt += nb_pair<false, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
+                                                       (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
+                if (mhi) cnt += nb_pair<false, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
+                                                       (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
+            } else {
+                const float Sx = (float)nb_shift_x(sidx) * p.Lx;
+                const float Sy = (float)nb_shift_y(sidx) * p.Ly;
+                const float Sz = (float)nb_shift_z(sidx) * p.Lz;
+                if (mlo) cnt += nb_pair<true, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], Sx, Sy, Sz,
+                                                      (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
+                if (mhi) cnt += nb_pair<true, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], Sx, Sy, Sz,
+                                                      (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
+            }
+            // Reduce fj over the lanes l, l^8, l^16, l^24 (same b) as a
+            // reduce-scatter: afterwards lane l holds component comp.
+            float ka = hi16 ? fj.z : fj.x, sa = hi16 ? fj.x : fj.z;
+            float kb = hi16 ? 0.0f : fj.y, sb = hi16 ? fj.y : 0.0f;
+            ka += __shfl_xor_sync(0xffffffffu, sa, 16);
+            kb += __shfl_xor_sync(0xffffffffu, sb, 16);
+            float kk = hi8 ? kb : ka, ss = hi8 ? ka : kb;
+            kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+            if (comp < 3) atomicAdd(p.fsort + 4 * sj + comp, kk);
+            if (ENERGY) {  // Kahan-compensated sums across the tiles of ci
+                const float y = ect - ecomp;
+                const float t = ec + y;
+                ecomp = (t - ec) - y;
+                ec = t;
+                const float yl = eljt - eljcomp;
+                const float tl = elj + yl;
+                eljcomp = (tl - elj) - yl;
+                elj = tl;
+            }
+        }
+        // i-forces: sum over the 8 lanes sharing a1 (b varies: xor 1, 2, 4)
+        for (int o = 1; o < 8; o <<= 1) {
+            fi1.x += __shfl_xor_sync(0xffffffffu, fi1.x, o);
+            fi1.y += __shfl_xor_sync(0xffffffffu, fi1.y, o);
+            fi1.z += __shfl_xor_sync(0xffffffffu, fi1.z, o);
+            fi2.x += __shfl_xor_sync(0xffffffffu, fi2.x, o);
+            fi2.y += __shfl_xor_sync(0xffffffffu, fi2.y, o);
+            fi2.z += __shfl_xor_sync(0xffffffffu, fi2.z, o);
+        }
+        if (b < 3) {
+            const float v = b == 0 ? fi1.x : (b == 1 ? fi1.y : fi1.z);
+            atomicAdd(p.fsort + 4 * (ci * NB_CLUSTER + a1) + b, v);
+        } else if (b < 6) {
+            const float v = b == 3 ? fi2.x : (b == 4 ? fi2.y : fi2.z);
+            atomicAdd(p.fsort + 4 * (ci * NB_CLUSTER + a2) + (b - 3), v);
+        }
+        if (ENERGY) {
+            ecd += (double)ec - (double)ecomp;
+            eljd += (double)elj - (double)eljcomp;
+        }
+    }
+
+    // grid-wide reduction of energies (FP64) and of the pair count
+    unsigned long long c64 = cnt;
+    for (int o = 16; o > 0; o >>= 1) {
+        c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+        if (ENERGY) {
+            ecd += __shfl_xor_sync(0xffffffffu, ecd, o);
+            eljd += __shfl_xor_sync(0xffffffffu, eljd, o);
+        }
+    }
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_cnt[warp] = c64;
+        s_red[0][warp] = eljd;
+        s_red[1][warp] = ecd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ct = 0;
+        double el = 0.0, ecc = 0.0;
+        for (int k = 0; k < kForceThreads / 32; ++k) {
+            ct += s_cnt[k];
+            el += s_red[0][k];
+            ecc += s_red[1][k];
+        }
+        atomicAdd(&p.st->npairs, ct);
+        if (ENERGY && p.energies) {
+            atomicAdd(&p.energies[0], el);
+            atomicAdd(&p.energies[1], ecc);
+        }
+    }
+}
+
+__global__ void k_scatter(int n, const int *__restrict__ pos, const float4 *__restrict__ fsort,
+                          float *__restrict__ forces) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 f = fsort[pos[i]];
+    forces[3 * i + 0] = f.x;
+    forces[3 * i + 1] = f.y;
+    forces[3 * i + 2] = f.z;
+}
+
+int g_force_blocks_per_sm[2] = {0, 0};
+
+}  // namespace
+
+cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
+                             int ntype, int snapshot, double *energies, cudaStream_t s) {
+    GatherParams p;
+    p.ntype = ntype;
+    p.perm = pl->perm;
+    p.coords = coords;
+    p.q = q;
+    p.type = type;
+    p.xref = pl->xref;
+    p.xprune = pl->xprune;
+    p.xq = pl->xq;
+    p.tsort = pl->tsort;
+    p.fsort = pl->fsort;
+    p.st = pl->st;
+    p.energies = energies;
+    p.Lx = pl->box[0];
+    p.Ly = pl->box[1];
+    p.Lz = pl->box[2];
+    p.snapshot = snapshot;
+    int blocks = (pl->nc_max * NB_CLUSTER + 255) / 256;
+    blocks = max(1, min(blocks, pl->num_sms * 8));
+    k_gather<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
+                            double *energies, float stale_search2, float stale_prune2,
+                            cudaStream_t s) {
+    ForceParams p;
+    p.xq = pl->xq;
+    p.tsort = pl->tsort;
+    p.fsort = reinterpret_cast<float *>(pl->fsort);
+    p.list = pl->has_inner ? pl->inner : pl->outer;
+    p.ci_start = pl->ci_start;
+    p.ci_len = pl->has_inner ? pl->ci_len_inner : pl->ci_len_outer;
+    p.ljparams = ljparams;
+    p.st = pl->st;
+    p.energies = energies;
+    p.ntype = ntype;
+    const double rc6 = 1.0 / ((double)rc * rc * rc * rc * rc * rc);
+    p.rc6inv = (float)rc6;
+    p.rc12inv = (float)(rc6 * rc6);
+    p.Lx = pl->box[0];
+    p.Ly = pl->box[1];
+    p.Lz = pl->box[2];
+    p.cc.rc2 = rc * rc;
+    p.cc.beta = beta;
+    p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
+    p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    p.stale_search2 = stale_search2;
+    p.stale_prune2 = stale_prune2;
+    p.has_inner = pl->has_inner;
+    const int e = energies ? 1 : 0;
+    if (g_force_blocks_per_sm[e] == 0) {
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &g_force_blocks_per_sm[e], e ? (const void *)k_force<true> : (const void *)k_force<false>,
+            kForceThreads, 0);
+        if (err != cudaSuccess) return err;
+        if (g_force_blocks_per_sm[e] < 1) g_force_blocks_per_sm[e] = 1;
+    }
+    int blocks = pl->num_sms * g_force_blocks_per_sm[e];
+    blocks = min(blocks, (pl->nc_max + kForceThreads / 32 - 1) / (kForceThreads / 32));
+    blocks = max(blocks, 1);
+    if (e)
+        k_force<true><<<blocks, kForceThreads, 0, s>>>(p);
+    else
+        k_force<false><<<blocks, kForceThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_scatter(nb_pairlist *pl, float *forces, cudaStream_t s) {
+    const int n = pl->n_atoms;
+    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, pl->pos, pl->fsort, forces);
+    return cudaGetLastError();
+}

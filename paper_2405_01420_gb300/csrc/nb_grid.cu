@@ -1,0 +1,206 @@
+// Grid sort into 8-atom clusters (first stage of the pair search, §III-A).
+//
+// 1. k_bin: wrap each atom into the box and bin it into an xy column;
+//    count atoms per column.
+// 2. k_col_scan: exclusive scans of atoms and of 8-atom clusters per column.
+// 3. k_col_scatter: bucket (z, atom) keys by column.
+// 4. k_col_sort: one CTA per column sorts its keys by z (bitonic, shared
+//    memory), packs runs of 8 into clusters, pads the last one, and writes
+//    the slot <-> atom maps, the search-frame positions and per-cluster
+//    bounding boxes.
+//
+// Layout in HBM after the sort (slot = 8 * cluster + lane):
+//   perm[slot] (int), xref[slot] (float4), bbox[2c], bbox[2c+1] (float4).
+#include "nb_internal.cuh"
+
+namespace {
+
+__global__ void k_bin(int n, const float *__restrict__ coords, float Lx, float Ly, float Lz,
+                      float inv_sx, float inv_sy, int ncx, int ncy, int *__restrict__ col_count,
+                      int *__restrict__ atom_col, int *__restrict__ atom_slot,
+                      float4 *__restrict__ xw, nb_dev_state *st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x = coords[3 * i + 0], y = coords[3 * i + 1], z = coords[3 * i + 2];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+        atomicOr(&st->err, NB_DEV_NONFINITE);
+        x = 0.0f;
+        y = 0.0f;
+        z = 0.0f;
+    }
+    float4 w = make_float4(nb_wrap(x, Lx), nb_wrap(y, Ly), nb_wrap(z, Lz), 0.0f);
+    int cx = min(ncx - 1, max(0, (int)floorf(w.x * inv_sx)));
+    int cy = min(ncy - 1, max(0, (int)floorf(w.y * inv_sy)));
+    int col = cx * ncy + cy;
+    xw[i] = w;
+    atom_col[i] = col;
+    atom_slot[i] = atomicAdd(&col_count[col], 1);
+}
+
+// Single CTA: exclusive scans of col_count (atoms) and ceil(count/8)
+// (clusters) over ncol columns; total clusters -> st->nc.
+__global__ void __launch_bounds__(1024) k_col_scan(int ncol, const int *__restrict__ col_count,
+                                                   int *__restrict__ col_atom_start,
+                                                   int *__restrict__ col_clus_start,
+                                                   nb_dev_state *st) {
+    __shared__ int warp_a[32], warp_c[32];
+    int t = threadIdx.x, nt = blockDim.x;
+    int chunk = (ncol + nt - 1) / nt;
+    int b = t * chunk, e = min(ncol, b + chunk);
+    int sa = 0, sc = 0, over = 0;
+    // Atom offsets use the full counts (every atom gets a key slot); cluster
+    // offsets use the counts the per-column sort can hold, so that every
+    // allocated cluster slot is written even after a column overflow.
+    for (int c = b; c < e; ++c) {
+        int k = col_count[c];
+        sa += k;
+        sc += (min(k, NB_MAX_COL_ATOMS) + NB_CLUSTER - 1) / NB_CLUSTER;
+        over |= (k > NB_MAX_COL_ATOMS);
+    }
+    if (over) atomicOr(&st->err, NB_DEV_COLUMN_OVERFLOW);
+    // inclusive scan of (sa, sc) across the CTA
+    int lane = t & 31, wid = t >> 5;
+    int ia = sa, ic = sc;
+    for (int o = 1; o < 32; o <<= 1) {
+        int va = __shfl_up_sync(0xffffffffu, ia, o), vc = __shfl_up_sync(0xffffffffu, ic, o);
+        if (lane >= o) {
+            ia += va;
+            ic += vc;
+        }
+    }
+    if (lane == 31) {
+        warp_a[wid] = ia;
+        warp_c[wid] = ic;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        int nw = nt >> 5;
+        int va = lane < nw ? warp_a[lane] : 0, vc = lane < nw ? warp_c[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int ua = __shfl_up_sync(0xffffffffu, va, o), uc = __shfl_up_sync(0xffffffffu, vc, o);
+            if (lane >= o) {
+                va += ua;
+                vc += uc;
+            }
+        }
+        warp_a[lane] = va;
+        warp_c[lane] = vc;
+    }
+    __syncthreads();
+    int pa = (wid > 0 ? warp_a[wid - 1] : 0) + ia - sa;  // exclusive prefix of this thread
+    int pc = (wid > 0 ? warp_c[wid - 1] : 0) + ic - sc;
+    for (int c = b; c < e; ++c) {
+        col_atom_start[c] = pa;
+        col_clus_start[c] = pc;
+        int k = col_count[c];
+        pa += k;
+        pc += (min(k, NB_MAX_COL_ATOMS) + NB_CLUSTER - 1) / NB_CLUSTER;
+    }
+    if (t == nt - 1) {
+        col_atom_start[ncol] = pa;
+        col_clus_start[ncol] = pc;
+        st->nc = pc;
+    }
+}
+
+__global__ void k_col_scatter(int n, const float4 *__restrict__ xw, const int *__restrict__ atom_col,
+                              const int *__restrict__ atom_slot,
+                              const int *__restrict__ col_atom_start,
+                              unsigned long long *__restrict__ keys) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // z >= 0 after wrapping, so its bit pattern orders like the value
+    unsigned long long k = ((unsigned long long)__float_as_uint(xw[i].z) << 32) | (unsigned)i;
+    keys[col_atom_start[atom_col[i]] + atom_slot[i]] = k;
+}
+
+// One CTA per column. Shared memory: NB_MAX_COL_ATOMS keys.
+__global__ void __launch_bounds__(256) k_col_sort(
+    const int *__restrict__ col_count, const int *__restrict__ col_atom_start,
+    const int *__restrict__ col_clus_start, const unsigned long long *__restrict__ keys,
+    const float4 *__restrict__ xw, int *__restrict__ perm, int *__restrict__ pos,
+    float4 *__restrict__ xref, float4 *__restrict__ xprune, float4 *__restrict__ xq,
+    int *__restrict__ tsort, float4 *__restrict__ bbox) {
+    __shared__ unsigned long long sk[NB_MAX_COL_ATOMS];
+    int col = blockIdx.x;
+    int cnt = min(col_count[col], NB_MAX_COL_ATOMS);  // overflow already flagged by the scan
+    int a0 = col_atom_start[col];
+    int p2 = 1;
+    while (p2 < cnt) p2 <<= 1;
+    for (int k = threadIdx.x; k < p2; k += blockDim.x) sk[k] = (k < cnt) ? keys[a0 + k] : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = threadIdx.x; k < p2; k += blockDim.x) {
+                int partner = k ^ stride;
+                if (partner > k) {
+                    bool up = ((k & size) == 0);
+                    unsigned long long u = sk[k], v = sk[partner];
+                    if ((u > v) == up) {
+                        sk[k] = v;
+                        sk[partner] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    int c0 = col_clus_start[col];
+    int ncl = (cnt + NB_CLUSTER - 1) / NB_CLUSTER;
+    int s0 = c0 * NB_CLUSTER;
+    const float4 pad = make_float4(NB_PAD_COORD, NB_PAD_COORD, NB_PAD_COORD, 0.0f);
+    for (int k = threadIdx.x; k < ncl * NB_CLUSTER; k += blockDim.x) {
+        int slot = s0 + k;
+        if (k < cnt) {
+            int atom = (int)(sk[k] & 0xffffffffu);
+            float4 w = xw[atom];
+            perm[slot] = atom;
+            pos[atom] = slot;
+            xref[slot] = w;
+            xprune[slot] = w;
+        } else {
+            perm[slot] = -1;
+            xref[slot] = pad;
+            xprune[slot] = pad;
+            xq[slot] = pad;
+            tsort[slot] = 0;
+        }
+    }
+    // bounding boxes: one thread per cluster, real atoms only
+    for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
+        int nreal = min(NB_CLUSTER, cnt - c * NB_CLUSTER);
+        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, __int_as_float(nreal));
+        float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, __int_as_float(col));
+        for (int a = 0; a < nreal; ++a) {
+            float4 w = xw[(int)(sk[c * NB_CLUSTER + a] & 0xffffffffu)];
+            lo.x = fminf(lo.x, w.x);
+            lo.y = fminf(lo.y, w.y);
+            lo.z = fminf(lo.z, w.z);
+            hi.x = fmaxf(hi.x, w.x);
+            hi.y = fmaxf(hi.y, w.y);
+            hi.z = fmaxf(hi.z, w.z);
+        }
+        bbox[2 * (c0 + c)] = lo;
+        bbox[2 * (c0 + c) + 1] = hi;
+    }
+}
+
+}  // namespace
+
+cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, float inv_sx, float inv_sy,
+                                cudaStream_t s) {
+    int n = pl->n_atoms;
+    cudaError_t e = cudaMemsetAsync(pl->col_count, 0, sizeof(int) * (size_t)pl->ncol, s);
+    if (e != cudaSuccess) return e;
+    int bs = 256, gb = (n + bs - 1) / bs;
+    k_bin<<<gb, bs, 0, s>>>(n, coords, pl->box[0], pl->box[1], pl->box[2], inv_sx, inv_sy, pl->ncx,
+                            pl->ncy, pl->col_count, pl->atom_col, pl->atom_slot, pl->xw, pl->st);
+    k_col_scan<<<1, 1024, 0, s>>>(pl->ncol, pl->col_count, pl->col_atom_start, pl->col_clus_start,
+                                  pl->st);
+    k_col_scatter<<<gb, bs, 0, s>>>(n, pl->xw, pl->atom_col, pl->atom_slot, pl->col_atom_start,
+                                    pl->keys);
+    k_col_sort<<<pl->ncol, 256, 0, s>>>(pl->col_count, pl->col_atom_start, pl->col_clus_start,
+                                        pl->keys, pl->xw, pl->perm, pl->pos, pl->xref, pl->xprune,
+                                        pl->xq, pl->tsort, pl->bbox);
+    return cudaGetLastError();
+}

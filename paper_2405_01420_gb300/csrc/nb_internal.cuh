@@ -1,0 +1,123 @@
+// Internal declarations of the nonbonded library: pair-list layout in HBM,
+// device state, FP32 position contract and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nb.h"
+
+#define NB_CLUSTER 8            // atoms per cluster (i and j)
+#define NB_MAX_COL_ATOMS 4096   // atoms per grid column the per-column sort can hold
+#define NB_MAX_TYPES 32         // LJ types (table of ntype^2 float4 in shared memory)
+#define NB_CI_ENTRY_BUF 512     // list entries one i-cluster may own
+#define NB_CI_EXCL_BUF 256      // exclusions within one i-cluster
+#define NB_SHIFT_CENTER 13      // shift index of S = (0, 0, 0)
+#define NB_COULOMB_F 138.935458f
+
+// Device-side state of one pair list (one allocation, zeroed at creation).
+struct nb_dev_state {
+    unsigned err;                  // sticky NB_DEV_* bits
+    int nc;                        // clusters produced by the last search
+    unsigned long long list_count; // outer entries allocated by the last search
+    unsigned long long inner_count;// entries kept by the last prune
+    unsigned work;                 // work counter of the force kernel
+    unsigned work_prune;           // work counter of the prune kernel
+    unsigned cur_d2_search;        // max |y - y_search|^2 (float bits) of the running call
+    unsigned cur_d2_prune;         // max |y - y_prune|^2 (float bits) of the running call
+    unsigned last_d2_search;       // the same values of the last completed call
+    unsigned last_d2_prune;
+    unsigned long long npairs;     // in-range pairs counted by the last force call
+};
+
+// Host handle. Device buffers are sized at creation for n_atoms.
+struct nb_pairlist {
+    int device;
+    int num_sms;
+    int n_atoms;
+    int nc_max;     // upper bound on clusters: ceil(N/8) + ncol_max
+    int ncol_max;   // upper bound on grid columns
+    size_t cap;     // list entries per list
+
+    // host copy of what the last search / prune set up
+    int searched;
+    int has_inner;
+    float box[3];
+    float rlist;
+    float r_inner;
+    int ncx, ncy, ncol;
+    cudaEvent_t ev_start, ev_stop;  // optional timing events around the force kernel
+
+    // device buffers
+    nb_dev_state *st;
+    int *col_count;       // [ncol_max]
+    int *col_atom_start;  // [ncol_max + 1]
+    int *col_clus_start;  // [ncol_max + 1]
+    int *atom_col;        // [N]
+    int *atom_slot;       // [N] arrival rank within the column
+    float4 *xw;           // [N] wrapped search-frame positions, original order
+    unsigned long long *keys;  // [N] (z bits << 32 | atom), column-bucketed
+    int *perm;            // [8 nc_max] slot -> atom, -1 = padding
+    int *pos;             // [N] atom -> slot
+    float4 *xref;         // [8 nc_max] wrapped position at the search
+    float4 *xprune;       // [8 nc_max] position at the last prune
+    float4 *xq;           // [8 nc_max] (y, q) of the current call
+    int *tsort;           // [8 nc_max] LJ type of the current call
+    float4 *fsort;        // [8 nc_max] force accumulators, sorted order
+    float4 *bbox;         // [2 nc_max] lo (w = real atom count), hi (w = column)
+    int4 *outer;          // [cap] (cj, shift, mask lo, mask hi)
+    int4 *inner;          // [cap]
+    int *ci_start;        // [nc_max] first entry of i-cluster ci (both lists)
+    int *ci_len_outer;    // [nc_max]
+    int *ci_len_inner;    // [nc_max]
+};
+
+// ---------------------------------------------------------------------------
+// FP32 position contract. Every operation is written with explicit
+// round-to-nearest intrinsics so that the compiler cannot contract or
+// reorder it; the same sequence defines which pairs are within a radius.
+// ---------------------------------------------------------------------------
+
+// Wrap a coordinate into [0, L).
+__device__ __forceinline__ float nb_wrap(float x, float L) {
+    float w = __fsub_rn(x, __fmul_rn(L, floorf(__fdiv_rn(x, L))));
+    if (w < 0.0f) w = __fadd_rn(w, L);
+    if (w >= L) w = __fsub_rn(w, L);
+    if (!(w >= 0.0f && w < L)) w = 0.0f;
+    return w;
+}
+
+// Image of x nearest to the search-time wrapped position w0.
+__device__ __forceinline__ float nb_image(float x, float w0, float L) {
+    float k = rintf(__fdiv_rn(__fsub_rn(x, w0), L));
+    return __fsub_rn(x, __fmul_rn(k, L));
+}
+
+// Squared distance of a displacement, fixed FMA order.
+__device__ __forceinline__ float nb_r2(float dx, float dy, float dz) {
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Shift index s = (sx+1)*9 + (sy+1)*3 + (sz+1) -> integer components.
+__device__ __forceinline__ int nb_shift_x(int s) { return s / 9 - 1; }
+__device__ __forceinline__ int nb_shift_y(int s) { return (s / 3) % 3 - 1; }
+__device__ __forceinline__ int nb_shift_z(int s) { return s % 3 - 1; }
+
+// Padding slots sit far from every real atom so that no distance test
+// near them passes even before the mask removes them.
+#define NB_PAD_COORD (-1.0e6f)
+
+// ---------------------------------------------------------------------------
+// Launchers (return cudaError_t of the launch).
+// ---------------------------------------------------------------------------
+cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, float inv_sx, float inv_sy,
+                                cudaStream_t s);
+cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *excl_idx, float rl2,
+                             float rl_col, cudaStream_t s);
+cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
+                             int ntype, int snapshot, double *energies, cudaStream_t s);
+cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2, cudaStream_t s);
+cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
+                            double *energies, float stale_search2, float stale_prune2,
+                            cudaStream_t s);
+cudaError_t nb_launch_scatter(nb_pairlist *pl, float *forces, cudaStream_t s);

@@ -1,0 +1,108 @@
+// One atom pair of the LJ + Ewald real-space interaction, FP32.
+//
+//   E_LJ  = C12/r^12 - C6/r^6 - (C12/rc^12 - C6/rc^6)
+//   E_C   = f q_i q_j erfc(beta r)/r
+//   s     = -(1/r) dE/dr
+//         = f q_i q_j [erfc(beta r)/r + (2 beta/sqrt(pi)) exp(-beta^2 r^2)] / r^2
+//           + (12 C12/r^12 - 6 C6/r^6) / r^2
+//   F_i  += s d,  F_j -= s d
+//
+// erfc(x) = exp(-x^2) R(x) with R(x) = P(x)/Q(x) a degree-4/4 rational fit
+// of erfcx on [0, 3.2] (relative error 1.6e-8 in FP64, 2.9e-7 evaluated in
+// FP32; coefficients from fit_erfcx.py). exp, 1/sqrt and the division use
+// the hardware approximations (ex2.approx, rsqrt.approx, rcp.approx).
+#pragma once
+
+#include "nb_internal.cuh"
+
+#define NB_ERFCX_P1 8.430113792e-01f
+#define NB_ERFCX_P2 3.496225476e-01f
+#define NB_ERFCX_P3 5.748734251e-02f
+#define NB_ERFCX_P4 1.737346247e-05f
+#define NB_ERFCX_Q1 1.971389651e+00f
+#define NB_ERFCX_Q2 1.574109197e+00f
+#define NB_ERFCX_Q3 6.144732237e-01f
+#define NB_ERFCX_Q4 1.024811342e-01f
+
+__device__ __forceinline__ float nb_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float nb_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float nb_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// R(x) = erfc(x) exp(x^2) for x in [0, 3.2].
+__device__ __forceinline__ float nb_erfcx(float x) {
+    float p = fmaf(fmaf(fmaf(fmaf(NB_ERFCX_P4, x, NB_ERFCX_P3), x, NB_ERFCX_P2), x, NB_ERFCX_P1), x, 1.0f);
+    float q = fmaf(fmaf(fmaf(fmaf(NB_ERFCX_Q4, x, NB_ERFCX_Q3), x, NB_ERFCX_Q2), x, NB_ERFCX_Q1), x, 1.0f);
+    return p * nb_rcp(q);
+}
+
+// Constants of one force call, shared by all pairs.
+struct nb_coul {
+    float rc2;   // fl(rc * rc): a pair counts iff r2 < rc2
+    float beta;  // Ewald splitting parameter
+    float kexp;  // -beta^2 log2(e): exp(-beta^2 r^2) = 2^(kexp r^2)
+    float c2b;   // 2 beta / sqrt(pi)
+};
+
+// Accumulates one pair into fi (+) and fj (-). in_mask: the list mask bit.
+// SHIFT: add the periodic shift S to (y_a - y_b). ENERGY: also accumulate
+// the pair energies. Returns 1 if the pair was within rc and counted.
+template <bool SHIFT, bool ENERGY>
+__device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const float4 xj,
+                                       const float4 lj, const float Sx, const float Sy,
+                                       const float Sz, const bool in_mask, const nb_coul &cc,
+                                       float3 &fi, float3 &fj, float &ec, float &elj) {
+    float dx = __fsub_rn(xi.x, xj.x);
+    float dy = __fsub_rn(xi.y, xj.y);
+    float dz = __fsub_rn(xi.z, xj.z);
+    if (SHIFT) {
+        dx = __fadd_rn(dx, Sx);
+        dy = __fadd_rn(dy, Sy);
+        dz = __fadd_rn(dz, Sz);
+    }
+    const float r2 = nb_r2(dx, dy, dz);
+    const bool in = in_mask && (r2 < cc.rc2);
+    // 1/sqrt(r2): hardware estimate plus one Newton step on the residual
+    // e = 1 - r2 y^2, so that the LJ terms (which carry 1/r to the 12th
+    // power) see no systematic bias from the estimate.
+    const float y0 = nb_rsqrt(r2);
+    const float res = fmaf(-(r2 * y0), y0, 1.0f);
+    const float rinv = fmaf(0.5f * y0, res, y0);
+    const float rinv2 = rinv * rinv;
+    const float rinv6 = rinv2 * rinv2 * rinv2;
+    const float v6 = lj.x * rinv6;           // C6 / r^6
+    const float v12 = lj.y * rinv6 * rinv6;  // C12 / r^12
+    const float slj = fmaf(12.0f, v12, -6.0f * v6) * rinv2;
+    const float r = r2 * rinv;
+    const float ex = nb_ex2(cc.kexp * r2);           // exp(-beta^2 r^2)
+    const float a = ex * nb_erfcx(cc.beta * r) * rinv;  // erfc(beta r) / r
+    const float qq = qi_f * xj.w;                    // f q_i q_j
+    float s = fmaf(qq * fmaf(cc.c2b, ex, a), rinv2, slj);
+    s = in ? s : 0.0f;
+    fi.x = fmaf(s, dx, fi.x);
+    fi.y = fmaf(s, dy, fi.y);
+    fi.z = fmaf(s, dz, fi.z);
+    fj.x = fmaf(-s, dx, fj.x);
+    fj.y = fmaf(-s, dy, fj.y);
+    fj.z = fmaf(-s, dz, fj.z);
+    if (ENERGY) {
+        const float e_c = qq * a;
+        const float e_lj = v12 - v6 - lj.z;
+        ec += in ? e_c : 0.0f;
+        elj += in ? e_lj : 0.0f;
+    }
+    return in ? 1 : 0;
+}

@@ -1,0 +1,266 @@
+"""Python binding of libnb.so (include/nb.h).
+
+Argument marshalling only: each function checks tensor dtype, device and
+size, passes raw device pointers and a CUDA stream to the C entry point of
+the same name, and raises ``NBError`` on a non-zero status. Every step of
+the computation runs in the CUDA kernels of libnb.so; there is no CPU or
+PyTorch fallback, and using the binding without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libnb.so")
+
+NB_OK = 0
+NB_ERR_ARG = 1
+NB_ERR_CUDA = 2
+NB_ERR_CAPACITY = 3
+NB_ERR_NONFINITE = 4
+NB_ERR_TIMEOUT = 5
+NB_ERR_STATE = 6
+NB_ERR_NOMEM = 7
+
+NB_DEV_LIST_OVERFLOW = 0x01
+NB_DEV_COLUMN_OVERFLOW = 0x02
+NB_DEV_NONFINITE = 0x04
+NB_DEV_STALE_SEARCH = 0x08
+NB_DEV_STALE_PRUNE = 0x10
+NB_DEV_EXCL_OVERFLOW = 0x20
+NB_DEV_CLUSTER_OVERFLOW = 0x40
+NB_DEV_BAD_TYPE = 0x80
+
+NB_LIST_OUTER = 0
+NB_LIST_INNER = 1
+
+
+class NBError(RuntimeError):
+    """A libnb call returned a non-zero status."""
+
+    def __init__(self, code: int, message: str):
+        super().__init__(f"libnb error {code}: {message}")
+        self.code = code
+
+
+class nb_config(ctypes.Structure):
+    _fields_ = [("capacity_entries", ctypes.c_size_t), ("flags", ctypes.c_uint)]
+
+
+class nb_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int),
+        ("n_clusters", ctypes.c_int),
+        ("n_columns", ctypes.c_int),
+        ("has_inner", ctypes.c_int),
+        ("outer_entries", ctypes.c_longlong),
+        ("inner_entries", ctypes.c_longlong),
+        ("capacity_entries", ctypes.c_longlong),
+        ("pairs_last", ctypes.c_longlong),
+        ("rlist", ctypes.c_float),
+        ("r_inner", ctypes.c_float),
+        ("max_disp_search", ctypes.c_float),
+        ("max_disp_prune", ctypes.c_float),
+        ("error_word", ctypes.c_uint),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes); mirrors include/nb.h
+SIGNATURES = {
+    "nb_version": (ctypes.c_char_p, []),
+    "nb_last_error": (ctypes.c_char_p, []),
+    "nb_pairlist_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(nb_config)]),
+    "nb_pairlist_destroy": (_I, [_P]),
+    "nb_search": (_I, [_P, _P, _P, _F, _P, _P, _P]),
+    "nb_prune": (_I, [_P, _P, _F, _P]),
+    "nb_forces": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P]),
+    "nb_status": (_I, [_P, ctypes.POINTER(ctypes.c_uint), _I, _P]),
+    "nb_pairlist_stats": (_I, [_P, ctypes.POINTER(nb_stats), _P]),
+    "nb_pairlist_export": (_I, [_P, _I, _P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P, _SZ,
+                                ctypes.POINTER(_SZ), _P]),
+    "nb_set_timing_events": (_I, [_P, _P, _P]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnb.so and declare its signatures. Raises if it is not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`. "
+                    "The nonbonded path runs only in its CUDA kernels; there is no fallback.")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(code: int):
+    if code != NB_OK:
+        raise NBError(code, load_library().nb_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t, dtype, numel=None, name="tensor", allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def nb_version() -> str:
+    return load_library().nb_version().decode()
+
+
+def nb_last_error() -> str:
+    return load_library().nb_last_error().decode()
+
+
+def nb_pairlist_create(n_atoms: int, capacity_entries: int = 0) -> ctypes.c_void_p:
+    handle = ctypes.c_void_p()
+    cfg = nb_config(capacity_entries, 0)
+    _check(load_library().nb_pairlist_create(ctypes.byref(handle), int(n_atoms), ctypes.byref(cfg)))
+    return handle
+
+
+def nb_pairlist_destroy(pl) -> None:
+    if pl is not None:
+        _check(load_library().nb_pairlist_destroy(pl))
+
+
+def nb_search(pl, coords, box, rlist, excl_off=None, excl_idx=None, stream=None) -> None:
+    n = coords.numel() // 3
+    box_h = (ctypes.c_float * 3)(*[float(v) for v in box])
+    _check(load_library().nb_search(pl, _dev(coords, torch.float32, 3 * n, "coords"), box_h, float(rlist),
+                                    _dev(excl_off, torch.int32, n + 1, "excl_off", True),
+                                    _dev(excl_idx, torch.int32, None, "excl_idx", True), _stream(stream)))
+
+
+def nb_prune(pl, coords, r_inner, stream=None) -> None:
+    _check(load_library().nb_prune(pl, _dev(coords, torch.float32, None, "coords"), float(r_inner),
+                                   _stream(stream)))
+
+
+def nb_forces(pl, coords, q, type_, ljparams, rc, beta, forces, energies=None, stream=None) -> None:
+    n = coords.numel() // 3
+    ntype = int(ljparams.shape[0])
+    _check(load_library().nb_forces(pl, _dev(coords, torch.float32, 3 * n, "coords"),
+                                    _dev(q, torch.float32, n, "q"), _dev(type_, torch.int32, n, "type"), ntype,
+                                    _dev(ljparams, torch.float32, 2 * ntype * ntype, "ljparams"), float(rc),
+                                    float(beta), _dev(forces, torch.float32, 3 * n, "forces"),
+                                    _dev(energies, torch.float64, 2, "energies", True), _stream(stream)))
+
+
+def nb_status(pl, clear: bool = False, stream=None) -> int:
+    w = ctypes.c_uint(0)
+    _check(load_library().nb_status(pl, ctypes.byref(w), 1 if clear else 0, _stream(stream)))
+    return int(w.value)
+
+
+def nb_pairlist_stats(pl, stream=None) -> dict:
+    s = nb_stats()
+    _check(load_library().nb_pairlist_stats(pl, ctypes.byref(s), _stream(stream)))
+    return {name: getattr(s, name) for name, _ in nb_stats._fields_}
+
+
+def nb_pairlist_export(pl, which: int = NB_LIST_OUTER, stream=None) -> dict:
+    """Copy a list to host numpy arrays: ci, cj, shift, mask (uint64), perm."""
+    st = nb_pairlist_stats(pl, stream)
+    cap = int(st["outer_entries"]) + 1
+    nslot = 8 * int(st["n_clusters"])
+    ci = np.empty(cap, np.int32)
+    cj = np.empty(cap, np.int32)
+    sh = np.empty(cap, np.int32)
+    mk = np.empty(cap, np.uint64)
+    perm = np.empty(max(nslot, 1), np.int32)
+    n_out = ctypes.c_size_t(0)
+    n_slots = ctypes.c_size_t(0)
+    _check(load_library().nb_pairlist_export(
+        pl, int(which), ci.ctypes.data_as(_P), cj.ctypes.data_as(_P), sh.ctypes.data_as(_P),
+        mk.ctypes.data_as(_P), cap, ctypes.byref(n_out), perm.ctypes.data_as(_P), perm.size,
+        ctypes.byref(n_slots), _stream(stream)))
+    k = n_out.value
+    return {"ci": ci[:k], "cj": cj[:k], "shift": sh[:k], "mask": mk[:k], "perm": perm[:n_slots.value]}
+
+
+def nb_set_timing_events(pl, start=None, stop=None) -> None:
+    """Record torch.cuda.Event ``start``/``stop`` around the force kernel of later nb_forces calls."""
+    sp = None if start is None else ctypes.c_void_p(start.cuda_event)
+    ep = None if stop is None else ctypes.c_void_p(stop.cuda_event)
+    _check(load_library().nb_set_timing_events(pl, sp, ep))
+
+
+class Pairlist:
+    """Owns one nb_pairlist handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, n_atoms: int, capacity_entries: int = 0):
+        self.n_atoms = int(n_atoms)
+        self.handle = nb_pairlist_create(self.n_atoms, capacity_entries)
+
+    def search(self, coords, box, rlist, excl_off=None, excl_idx=None, stream=None):
+        nb_search(self.handle, coords, box, rlist, excl_off, excl_idx, stream)
+
+    def prune(self, coords, r_inner, stream=None):
+        nb_prune(self.handle, coords, r_inner, stream)
+
+    def forces(self, coords, q, type_, ljparams, rc, beta, forces=None, energies=None, want_energy=True,
+               stream=None):
+        if forces is None:
+            forces = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=coords.device)
+        if energies is None and want_energy:
+            energies = torch.empty(2, dtype=torch.float64, device=coords.device)
+        nb_forces(self.handle, coords, q, type_, ljparams, rc, beta, forces, energies, stream)
+        return forces, energies
+
+    def status(self, clear=False, stream=None) -> int:
+        return nb_status(self.handle, clear, stream)
+
+    def stats(self, stream=None) -> dict:
+        return nb_pairlist_stats(self.handle, stream)
+
+    def export(self, which=NB_LIST_OUTER, stream=None) -> dict:
+        return nb_pairlist_export(self.handle, which, stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            nb_pairlist_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

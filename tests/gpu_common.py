@@ -1,0 +1,74 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path, expand its list."""
+import numpy as np
+import torch
+
+import oracle
+from fp32util import r2_contract
+
+F_TOL = 1e-4   # per-atom |dF| <= F_TOL * rms(F_oracle)
+E_TOL = 1e-6   # relative energy error
+
+
+def to_dev(box, dev="cuda"):
+    """Device tensors of a synth.WaterBox."""
+    return {
+        "coords": torch.from_numpy(np.ascontiguousarray(box.coords)).to(dev),
+        "q": torch.from_numpy(np.ascontiguousarray(box.q)).to(dev),
+        "type": torch.from_numpy(np.ascontiguousarray(box.type)).to(dev),
+        "lj": torch.from_numpy(np.ascontiguousarray(box.ljparams)).to(dev),
+        "excl_off": torch.from_numpy(np.ascontiguousarray(box.excl_off)).to(dev),
+        "excl_idx": torch.from_numpy(np.ascontiguousarray(box.excl_idx)).to(dev),
+    }
+
+
+def expand_counted_pairs(exp, y, box, r_cut):
+    """Atom pairs of an exported list whose mask bit is set and whose FP32
+    distance under the kernels' contract is below r_cut.
+
+    ``y`` are the contract positions (oracle.image_f32). Returns an int64 [P, 2]
+    array with i < j, one row per (entry, bit) that passes (duplicates kept).
+    """
+    ci, cj, sh, mk, perm = exp["ci"], exp["cj"], exp["shift"], exp["mask"], exp["perm"]
+    if ci.size == 0:
+        return np.zeros((0, 2), np.int64)
+    bits = ((mk[:, None] >> np.arange(64, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(bool)
+    e_idx, bit = np.nonzero(bits)
+    a = bit // 8
+    b = bit % 8
+    p = perm[ci[e_idx] * 8 + a]
+    q = perm[cj[e_idx] * 8 + b]
+    assert (p >= 0).all() and (q >= 0).all(), "mask bit set on a padding slot"
+    s = sh[e_idx]
+    S = np.stack([(s // 9 - 1), ((s // 3) % 3 - 1), (s % 3 - 1)], axis=1).astype(np.float32) * box.astype(np.float32)
+    d = (y[p] - y[q]).astype(np.float32)
+    d = (d + S).astype(np.float32)
+    r2 = r2_contract(d[:, 0], d[:, 1], d[:, 2])
+    rc2 = np.float32(r_cut) * np.float32(r_cut)
+    keep = r2 < rc2
+    i = np.minimum(p[keep], q[keep])
+    j = np.maximum(p[keep], q[keep])
+    return np.stack([i, j], axis=1).astype(np.int64)
+
+
+def pair_set(arr):
+    return set(map(tuple, np.asarray(arr).tolist()))
+
+
+def compare_forces(F_gpu, F_ref, tol=F_TOL):
+    """max_i |F_gpu_i - F_ref_i| / rms(F_ref); asserts <= tol."""
+    F_gpu = np.asarray(F_gpu, np.float64)
+    rms = np.sqrt((F_ref ** 2).sum(1).mean())
+    err = np.sqrt(((F_gpu - F_ref) ** 2).sum(1))
+    worst = float(err.max() / rms)
+    assert worst <= tol, f"max per-atom |dF| = {err.max():.3e} = {worst:.2e} rms(F) (rms {rms:.3e})"
+    return worst
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def oracle_ref(box, rc, beta, coords=None):
+    x = box.coords if coords is None else coords
+    return oracle.energy_forces(x, box.q, box.type, box.ljparams, box.box, rc, beta, box.excl_off,
+                                box.excl_idx)
