@@ -290,6 +290,9 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.evals)]
+    for a, b in ev:  # torch only times events it has recorded once; libnb re-records them at the kernel
+        a.record(stream)
+        b.record(stream)
     sampler = ClockSampler(local) if rank == 0 else None
     step_ms, kern_ms = [], []
     searches = prunes = 0

@@ -9,8 +9,12 @@
 //
 // erfc(x) = exp(-x^2) R(x) with R(x) = P(x)/Q(x) a degree-4/4 rational fit
 // of erfcx on [0, 3.2] (relative error 1.6e-8 in FP64, 2.9e-7 evaluated in
-// FP32; coefficients from fit_erfcx.py). exp, 1/sqrt and the division use
-// the hardware approximations (ex2.approx, rsqrt.approx, rcp.approx).
+// FP32; coefficients from fit_coeffs.py). 1/sqrt(r2) is the hardware
+// estimate refined by a Newton step; exp and the division are chosen by
+// NB_EXP_MODE / NB_RCP_NR below. The energies are summed over ~10^7 terms
+// that cancel to ~1/400 of their absolute sum in water, so any error that
+// varies systematically with r is amplified; the refined forms keep every
+// factor free of approximation bias beyond FP32 rounding.
 #pragma once
 
 #include "nb_internal.cuh"
@@ -42,11 +46,60 @@ __device__ __forceinline__ float nb_rcp(float x) {
     return y;
 }
 
+// Variants of the two function approximations (compile-time):
+//   NB_EXP_MODE 0: 2^t by ex2.approx; 1: Cody-Waite reduction t = n + f and a
+//                  degree-6 polynomial for 2^f (fit_coeffs.py), no hardware
+//                  approximation in the result.
+//   NB_RCP_NR   0: 1/q by rcp.approx; 1: plus one Newton step.
+#ifndef NB_EXP_MODE
+#define NB_EXP_MODE 1
+#endif
+#ifndef NB_RCP_NR
+#define NB_RCP_NR 1
+#endif
+
+#define NB_EXP2_C1 6.931471825e-01f
+#define NB_EXP2_C2 2.402264923e-01f
+#define NB_EXP2_C3 5.550362542e-02f
+#define NB_EXP2_C4 9.618407115e-03f
+#define NB_EXP2_C5 1.338712522e-03f
+#define NB_EXP2_C6 1.533757168e-04f
+
+// 2^t for t <= 0. Results below 2^-125 are returned as about 2^-125.
+__device__ __forceinline__ float nb_exp2(float t) {
+#if NB_EXP_MODE == 0
+    return nb_ex2(t);
+#else
+    t = fmaxf(t, -125.0f);
+    const float magic = 12582912.0f;          // 1.5 * 2^23: adding it rounds to an integer
+    const float tn = t + magic;
+    const float n = tn - magic;               // rint(t)
+    const float f = t - n;                    // in [-0.5, 0.5]
+    float p = fmaf(NB_EXP2_C6, f, NB_EXP2_C5);
+    p = fmaf(p, f, NB_EXP2_C4);
+    p = fmaf(p, f, NB_EXP2_C3);
+    p = fmaf(p, f, NB_EXP2_C2);
+    p = fmaf(p, f, NB_EXP2_C1);
+    p = fmaf(p, f, 1.0f);                     // 2^f in [0.70, 1.42]
+    const int ni = __float_as_int(tn) - __float_as_int(magic);
+    return __int_as_float(__float_as_int(p) + ni * (1 << 23));  // times 2^n, stays normal
+#endif
+}
+
+__device__ __forceinline__ float nb_recip(float q) {
+    float y = nb_rcp(q);
+#if NB_RCP_NR
+    const float e = fmaf(-q, y, 1.0f);
+    y = fmaf(y, e, y);
+#endif
+    return y;
+}
+
 // R(x) = erfc(x) exp(x^2) for x in [0, 3.2].
 __device__ __forceinline__ float nb_erfcx(float x) {
     float p = fmaf(fmaf(fmaf(fmaf(NB_ERFCX_P4, x, NB_ERFCX_P3), x, NB_ERFCX_P2), x, NB_ERFCX_P1), x, 1.0f);
     float q = fmaf(fmaf(fmaf(fmaf(NB_ERFCX_Q4, x, NB_ERFCX_Q3), x, NB_ERFCX_Q2), x, NB_ERFCX_Q1), x, 1.0f);
-    return p * nb_rcp(q);
+    return p * nb_recip(q);
 }
 
 // Constants of one force call, shared by all pairs.
@@ -87,7 +140,7 @@ __device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const 
     const float v12 = lj.y * rinv6 * rinv6;  // C12 / r^12
     const float slj = fmaf(12.0f, v12, -6.0f * v6) * rinv2;
     const float r = r2 * rinv;
-    const float ex = nb_ex2(cc.kexp * r2);           // exp(-beta^2 r^2)
+    const float ex = nb_exp2(cc.kexp * r2);          // exp(-beta^2 r^2)
     const float a = ex * nb_erfcx(cc.beta * r) * rinv;  // erfc(beta r) / r
     const float qq = qi_f * xj.w;                    // f q_i q_j
     float s = fmaf(qq * fmaf(cc.c2b, ex, a), rinv2, slj);
