@@ -14,7 +14,8 @@ Functions:
 * ``pairs_f32`` - the set of pairs within rc under the FP32 contract that the
   GPU pair list must reproduce bit for bit.
 * ``image_f32`` - the FP32 positions that contract uses.
-* ``loss_grad`` - force-matching loss and its analytic gradients.
+* ``force_vjp`` - adjoint of the forces: dL/dx, dL/dq, dL/dC given dL/dF.
+* ``force_matching`` - loss (1/3N) sum |F - T|^2 and its gradients.
 
 Parity: pinned by the CPU tests in ``tests/test_oracle_*.py``.
 """
@@ -64,7 +65,7 @@ def _load():
             F = ctypes.c_float
             LL = ctypes.c_longlong
             lib.oracle_threads.restype = I
-            lib.oracle_energy_forces.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, P, P, P]
+            lib.oracle_energy_forces.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, P, P, P, P]
             lib.oracle_energy_forces.restype = I
             lib.oracle_forces_subset.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, P, P]
             lib.oracle_forces_subset.restype = I
@@ -74,9 +75,8 @@ def _load():
             lib.oracle_pairs_f32.restype = I
             lib.oracle_image_f32.argtypes = [I, P, P, P, P]
             lib.oracle_image_f32.restype = None
-            if hasattr(lib, "oracle_loss_grad"):
-                lib.oracle_loss_grad.argtypes = [I, P, P, P, I, P, P, D, D, P, P, P, P, P, P, P, P]
-                lib.oracle_loss_grad.restype = I
+            lib.oracle_force_vjp.argtypes = [I, P, P, P, I, P, P, D, D, P, P, P, P, P, P]
+            lib.oracle_force_vjp.restype = I
             _lib = lib
     return _lib
 
@@ -102,11 +102,13 @@ def threads() -> int:
     return int(_load().oracle_threads())
 
 
-def energy_forces(x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None, method="auto"):
+def energy_forces(x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None, method="auto",
+                  abs_sums=False):
     """FP64 energies and forces.
 
-    Returns ``(F [N,3], E_lj, E_coul, npairs)``. ``lj`` is [ntype, ntype, 2]
-    holding (C6, C12). ``method`` is "auto", "n2" or "cell".
+    Returns ``(F [N,3], E_lj, E_coul, npairs)``; with ``abs_sums`` also
+    ``(sum |e_lj|, sum |e_coul|)`` over the pairs as a fifth item. ``lj`` is
+    [ntype, ntype, 2] holding (C6, C12). ``method`` is "auto", "n2" or "cell".
     """
     lib = _load()
     x = _f64(x).reshape(-1, 3)
@@ -115,13 +117,16 @@ def energy_forces(x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None, 
     ntype = lj.shape[0]
     F = np.zeros((n, 3), dtype=np.float64)
     E = np.zeros(2, dtype=np.float64)
+    A = np.zeros(2, dtype=np.float64)
     npairs = ctypes.c_longlong(0)
     m = {"auto": 0, "n2": 1, "cell": 2}[method]
     rcode = lib.oracle_energy_forces(n, _p(x), _p(_f64(q)), _p(_i32(type_)), ntype, _p(lj),
                                      _p(_f64(box)), float(rc), float(beta), _p(_i32(excl_off)),
-                                     _p(_i32(excl_idx)), m, _p(F), _p(E), ctypes.byref(npairs))
+                                     _p(_i32(excl_idx)), m, _p(F), _p(E), ctypes.byref(npairs), _p(A))
     if rcode != 0:
         raise ValueError(f"oracle_energy_forces failed with code {rcode}")
+    if abs_sums:
+        return F, float(E[0]), float(E[1]), int(npairs.value), (float(A[0]), float(A[1]))
     return F, float(E[0]), float(E[1]), int(npairs.value)
 
 
@@ -198,3 +203,32 @@ def image_f32(x0, x, box):
     y = np.empty_like(x)
     lib.oracle_image_f32(x.shape[0], _p(x0), _p(x), _p(_f32(box)), _p(y))
     return y
+
+
+def force_vjp(x, q, type_, lj, box, rc, beta, g, excl_off=None, excl_idx=None):
+    """Adjoint of the forces: given g = dL/dF [N, 3], returns (gx [N,3], gq [N], glj [nt,nt,2])."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    n = x.shape[0]
+    lj = _f64(lj)
+    nt = lj.shape[0]
+    g = _f64(g).reshape(-1, 3)
+    gx = np.zeros((n, 3))
+    gq = np.zeros(n)
+    glj = np.zeros((nt, nt, 2))
+    rcode = lib.oracle_force_vjp(n, _p(x), _p(_f64(q)), _p(_i32(type_)), nt, _p(lj), _p(_f64(box)), float(rc),
+                                 float(beta), _p(_i32(excl_off)), _p(_i32(excl_idx)), _p(g), _p(gx), _p(gq), _p(glj))
+    if rcode != 0:
+        raise ValueError(f"oracle_force_vjp failed with code {rcode}")
+    return gx, gq, glj
+
+
+def force_matching(x, q, type_, lj, box, rc, beta, target, excl_off=None, excl_idx=None):
+    """Loss L = (1/3N) sum_i |F_i - T_i|^2 and (dL/dx, dL/dq, dL/dC, F)."""
+    F, _, _, _ = energy_forces(x, q, type_, lj, box, rc, beta, excl_off, excl_idx)
+    n = F.shape[0]
+    diff = F - np.asarray(target, np.float64).reshape(-1, 3)
+    L = float((diff ** 2).sum() / (3 * n))
+    g = 2.0 * diff / (3 * n)
+    gx, gq, glj = force_vjp(x, q, type_, lj, box, rc, beta, g, excl_off, excl_idx)
+    return L, gx, gq, glj, F

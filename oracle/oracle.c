@@ -148,14 +148,16 @@ static void neighbour_cells(int c, const int *nc, int *out) {
  * Energies and forces in FP64.
  *   x[3n], q[n], type[n], lj[ntype*ntype*2] = (C6, C12) per type pair,
  *   box[3], excl CSR (may be NULL), method 0 = auto, 1 = O(N^2), 2 = cell list.
- * Outputs: F[3n] (overwritten), E[2] = {E_LJ, E_C}, *npairs = pairs counted.
+ * Outputs: F[3n] (overwritten), E[2] = {E_LJ, E_C}, *npairs = pairs counted,
+ * Eabs[2] (may be NULL) = sums of the absolute pair energies |e_LJ|, |e_C|:
+ * the scale that FP32 rounding errors of a pair sum are proportional to.
  * Returns 0, or -1 if rc >= L/2 on some axis, -2 if the cell list was asked
  * for but the box has fewer than 3 cells per axis.
  */
 int oracle_energy_forces(int n, const double *x, const double *q, const int *type, int ntype,
                          const double *lj, const double *box, double rc, double beta,
                          const int *excl_off, const int *excl_idx, int method, double *F,
-                         double *E, long long *npairs) {
+                         double *E, long long *npairs, double *Eabs) {
     for (int k = 0; k < 3; ++k)
         if (!(rc < 0.5 * box[k])) return -1;
     int nc[3];
@@ -168,6 +170,8 @@ int oracle_energy_forces(int n, const double *x, const double *q, const int *typ
     double *Elj = (double *)calloc((size_t)nt, sizeof(double));
     double *Ec = (double *)calloc((size_t)nt, sizeof(double));
     long long *Np = (long long *)calloc((size_t)nt, sizeof(long long));
+    double *Alj = (double *)calloc((size_t)nt, sizeof(double));
+    double *Ac = (double *)calloc((size_t)nt, sizeof(double));
     double rc2 = rc * rc;
 
     int *cell_start = NULL, *cell_atoms = NULL, *atom_cell = NULL;
@@ -183,7 +187,7 @@ int oracle_energy_forces(int n, const double *x, const double *q, const int *typ
     {
         int tid = oracle_tid();
         double *Fl = Ft + (size_t)tid * 3 * (size_t)n;
-        double elj_sum = 0.0, ec_sum = 0.0;
+        double elj_sum = 0.0, ec_sum = 0.0, alj_sum = 0.0, ac_sum = 0.0;
         long long np = 0;
         int nb[27];
 #pragma omp for schedule(static)
@@ -212,6 +216,8 @@ int oracle_energy_forces(int n, const double *x, const double *q, const int *typ
                     pair_terms(r2, q[i], q[j], p[0], p[1], rc, beta, &elj, &ec, &s);
                     elj_sum += elj;
                     ec_sum += ec;
+                    alj_sum += fabs(elj);
+                    ac_sum += fabs(ec);
                     np++;
                     for (int k = 0; k < 3; ++k) {
                         Fl[3 * i + k] += s * d[k];
@@ -223,6 +229,8 @@ int oracle_energy_forces(int n, const double *x, const double *q, const int *typ
         Elj[tid] = elj_sum;
         Ec[tid] = ec_sum;
         Np[tid] = np;
+        Alj[tid] = alj_sum;
+        Ac[tid] = ac_sum;
     }
     /* fixed-order reduction: deterministic for a given thread count */
     for (size_t k = 0; k < 3 * (size_t)n; ++k) {
@@ -240,6 +248,17 @@ int oracle_energy_forces(int n, const double *x, const double *q, const int *typ
     E[0] = el;
     E[1] = ecs;
     if (npairs) *npairs = npt;
+    if (Eabs) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int t = 0; t < nt; ++t) {
+            a0 += Alj[t];
+            a1 += Ac[t];
+        }
+        Eabs[0] = a0;
+        Eabs[1] = a1;
+    }
+    free(Alj);
+    free(Ac);
     free(Ft);
     free(Elj);
     free(Ec);
@@ -452,4 +471,128 @@ int oracle_pairs_f32(int n, const float *x0, const float *x, const float *box, f
     free(atom_cell);
     if (status) return status;
     return (pi && c > cap) ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the forces (vector-Jacobian product), FP64.
+ *
+ * Given g = dL/dF for some scalar L(F) (e.g. a force-matching loss), returns
+ *   gx = dL/dx = sum_i g_i . dF_i/dx,   gq = dL/dq,   glj = dL/d(C6, C12).
+ * Per pair (i, j) with d = x_i - x_j, F_i += s d, F_j -= s d, so the pair's
+ * part of g.F is s(r) (u . d) with u = g_i - g_j, and
+ *   d/dx_i [s (u.d)] = s u + (s'/r)(u.d) d           (= -d/dx_j)
+ *   d/dq_i = f q_j B (u.d), d/dq_j = f q_i B (u.d),  B = [erfc(br)/r + c e]/r^2
+ *   d/dC6 = -6 r^-8 (u.d),  d/dC12 = 12 r^-14 (u.d)
+ * with c = 2b/sqrt(pi), e = exp(-b^2 r^2) and
+ *   s'/r = -3 s_C / r^2 - 2 f q_i q_j c b^2 e / r^2 - 168 C12 r^-16 + 48 C6 r^-10.
+ * The LJ matrix is one symmetric parameter set: the derivative for a type
+ * pair {a, b} is split evenly between entries (a, b) and (b, a), so that
+ * glj is symmetric and a symmetric perturbation of both entries changes L
+ * by (glj[a][b] + glj[b][a]) times the step.
+ * gx[3n], gq[n], glj[ntype*ntype*2] are overwritten. Same return codes as
+ * oracle_energy_forces. Pinned by finite differences of g.F and by the
+ * symmetry of the Hessian (tests/test_oracle_adjoint.py).
+ * ------------------------------------------------------------------------ */
+int oracle_force_vjp(int n, const double *x, const double *q, const int *type, int ntype,
+                     const double *lj, const double *box, double rc, double beta,
+                     const int *excl_off, const int *excl_idx, const double *g, double *gx,
+                     double *gq, double *glj) {
+    for (int k = 0; k < 3; ++k)
+        if (!(rc < 0.5 * box[k])) return -1;
+    int nc[3];
+    int use_cells = cell_grid(box, rc, nc) && n > 4096;
+    int nt = oracle_nthreads();
+    size_t nlj = (size_t)ntype * ntype * 2;
+    double *gxt = (double *)calloc((size_t)nt * 3 * (size_t)n, sizeof(double));
+    double *gqt = (double *)calloc((size_t)nt * (size_t)n, sizeof(double));
+    double *gljt = (double *)calloc((size_t)nt * nlj, sizeof(double));
+    int *cell_start = NULL, *cell_atoms = NULL, *atom_cell = NULL;
+    if (use_cells) {
+        int ncell = nc[0] * nc[1] * nc[2];
+        cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
+        cell_atoms = (int *)malloc(sizeof(int) * (size_t)n);
+        atom_cell = (int *)malloc(sizeof(int) * (size_t)n);
+        build_cells(n, x, box, nc, cell_start, cell_atoms, atom_cell);
+    }
+    const double rc2 = rc * rc;
+    const double cb = 2.0 * beta / sqrt(M_PI);
+#pragma omp parallel
+    {
+        int tid = oracle_tid();
+        double *gxl = gxt + (size_t)tid * 3 * (size_t)n;
+        double *gql = gqt + (size_t)tid * (size_t)n;
+        double *gljl = gljt + (size_t)tid * nlj;
+        int nb[27];
+#pragma omp for schedule(static)
+        for (int i = 0; i < n; ++i) {
+            int ncc = use_cells ? 27 : 1;
+            if (use_cells) neighbour_cells(atom_cell[i], nc, nb);
+            for (int cc = 0; cc < ncc; ++cc) {
+                int j0 = use_cells ? cell_start[nb[cc]] : i + 1;
+                int j1 = use_cells ? cell_start[nb[cc] + 1] : n;
+                for (int jj = j0; jj < j1; ++jj) {
+                    int j = use_cells ? cell_atoms[jj] : jj;
+                    if (j <= i) continue;
+                    double d[3];
+                    min_image(x + 3 * i, x + 3 * j, box, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!(r2 < rc2)) continue;
+                    if (is_excluded(i, j, excl_off, excl_idx)) continue;
+                    const double *p = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+                    double c6 = p[0], c12 = p[1];
+                    double r = sqrt(r2), rinv2 = 1.0 / r2, rinv6 = rinv2 * rinv2 * rinv2;
+                    double K = ORACLE_COULOMB_F * q[i] * q[j];
+                    double e = exp(-beta * beta * r2);
+                    double A = erfc(beta * r) / r;
+                    double B = (A + cb * e) * rinv2;
+                    double sC = K * B;
+                    double sLJ = (12.0 * c12 * rinv6 * rinv6 - 6.0 * c6 * rinv6) * rinv2;
+                    double s = sC + sLJ;
+                    double spr = -3.0 * sC * rinv2 - 2.0 * K * cb * beta * beta * e * rinv2 -
+                                 168.0 * c12 * rinv6 * rinv6 * rinv2 * rinv2 + 48.0 * c6 * rinv6 * rinv2 * rinv2;
+                    double u[3], ud = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        u[k] = g[3 * i + k] - g[3 * j + k];
+                        ud += u[k] * d[k];
+                    }
+                    for (int k = 0; k < 3; ++k) {
+                        double v = s * u[k] + spr * ud * d[k];
+                        gxl[3 * i + k] += v;
+                        gxl[3 * j + k] -= v;
+                    }
+                    gql[i] += ORACLE_COULOMB_F * q[j] * B * ud;
+                    gql[j] += ORACLE_COULOMB_F * q[i] * B * ud;
+                    double d6 = -6.0 * rinv6 * rinv2 * ud, d12 = 12.0 * rinv6 * rinv6 * rinv2 * ud;
+                    size_t ab = 2 * ((size_t)type[i] * ntype + type[j]);
+                    size_t ba = 2 * ((size_t)type[j] * ntype + type[i]);
+                    gljl[ab] += 0.5 * d6;
+                    gljl[ab + 1] += 0.5 * d12;
+                    gljl[ba] += 0.5 * d6;
+                    gljl[ba + 1] += 0.5 * d12;
+                }
+            }
+        }
+    }
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) {
+        double v = 0.0;
+        for (int t = 0; t < nt; ++t) v += gxt[(size_t)t * 3 * (size_t)n + k];
+        gx[k] = v;
+    }
+    for (size_t k = 0; k < (size_t)n; ++k) {
+        double v = 0.0;
+        for (int t = 0; t < nt; ++t) v += gqt[(size_t)t * (size_t)n + k];
+        gq[k] = v;
+    }
+    for (size_t k = 0; k < nlj; ++k) {
+        double v = 0.0;
+        for (int t = 0; t < nt; ++t) v += gljt[(size_t)t * nlj + k];
+        glj[k] = v;
+    }
+    free(gxt);
+    free(gqt);
+    free(gljt);
+    free(cell_start);
+    free(cell_atoms);
+    free(atom_cell);
+    return 0;
 }

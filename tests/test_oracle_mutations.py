@@ -27,10 +27,21 @@ MUTATIONS = {
     "coulomb_constant_dropped": ("double qq = ORACLE_COULOMB_F * qi * qj;", "double qq = qi * qj;"),
 }
 
+# mistakes in the force adjoint, caught by tests/test_oracle_adjoint.py
+ADJOINT_MUTATIONS = {
+    "adjoint_missing_gaussian_term": (" - 2.0 * K * cb * beta * beta * e * rinv2", ""),
+    "adjoint_lj_second_derivative": ("168.0 * c12", "144.0 * c12"),
+    "adjoint_charge_uses_own_charge": ("gql[i] += ORACLE_COULOMB_F * q[j] * B * ud;",
+                                       "gql[i] += ORACLE_COULOMB_F * q[i] * B * ud;"),
+    "adjoint_lj_not_symmetrised": ("gljl[ba] += 0.5 * d6;", ""),
+    "adjoint_reaction_sign": ("gxl[3 * j + k] -= v;", "gxl[3 * j + k] += v;"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(ADJOINT_MUTATIONS))
 def test_pins_catch_mutation(name, tmp_path):
-    old, new = MUTATIONS[name]
+    old, new = MUTATIONS[name] if name in MUTATIONS else ADJOINT_MUTATIONS[name]
+    pins = "test_oracle_pins.py" if name in MUTATIONS else "test_oracle_adjoint.py"
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
     mutated = tmp_path / "oracle_mut.c"
@@ -38,6 +49,6 @@ def test_pins_catch_mutation(name, tmp_path):
     lib = oracle.build(force=True, src=str(mutated), out=str(tmp_path / "liboracle_mut.so"))
     env = dict(os.environ, NB_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
