@@ -122,10 +122,8 @@ struct ForceParams {
 };
 
 template <bool ENERGY>
-__global__ void __launch_bounds__(kForceThreads) k_force(ForceParams p) {
+__global__ void __launch_bounds__(kForceThreads, 4) k_force(ForceParams p) {
     __shared__ float4 s_lj[NB_MAX_TYPES * NB_MAX_TYPES];
-    __shared__ double s_red[2][kForceThreads / 32];
-    __shared__ unsigned long long s_cnt[kForceThreads / 32];
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -167,13 +165,28 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceParams p) {
         float3 fi1 = make_float3(0.0f, 0.0f, 0.0f), fi2 = make_float3(0.0f, 0.0f, 0.0f);
         float ec = 0.0f, ecomp = 0.0f, elj = 0.0f, eljcomp = 0.0f;
 
+        // Software pipeline: the entry and j-atom data of tile k+1 load while
+        // tile k computes.
+        int4 e_nx = make_int4(0, NB_SHIFT_CENTER, 0, 0);
+        float4 xj_nx = make_float4(0.f, 0.f, 0.f, 0.f);
+        int tj_nx = 0;
+        if (k0 < k1) {
+            e_nx = p.list[k0];
+            xj_nx = p.xq[e_nx.x * NB_CLUSTER + b];
+            tj_nx = p.tsort[e_nx.x * NB_CLUSTER + b];
+        }
         for (int k = k0; k < k1; ++k) {
-            const int4 e = p.list[k];
+            const int4 e = e_nx;
+            const float4 xj = xj_nx;
+            const int tj = tj_nx;
+            if (k + 1 < k1) {
+                e_nx = p.list[k + 1];
+                xj_nx = p.xq[e_nx.x * NB_CLUSTER + b];
+                tj_nx = p.tsort[e_nx.x * NB_CLUSTER + b];
+            }
             const int cj = e.x, sidx = e.y;
             const unsigned mlo = (unsigned)e.z, mhi = (unsigned)e.w;
             const int sj = cj * NB_CLUSTER + b;
-            const float4 xj = p.xq[sj];
-            const int tj = p.tsort[sj];
             float3 fj = make_float3(0.0f, 0.0f, 0.0f);
             float ect = 0.0f, eljt = 0.0f;
             if (sidx == NB_SHIFT_CENTER) {
@@ -241,25 +254,13 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceParams p) {
             eljd += __shfl_xor_sync(0xffffffffu, eljd, o);
         }
     }
-    const int warp = threadIdx.x >> 5;
+    // one atomic per warp: no block barrier, so a warp that runs out of
+    // work leaves without waiting for the rest of its block
     if (lane == 0) {
-        s_cnt[warp] = c64;
-        s_red[0][warp] = eljd;
-        s_red[1][warp] = ecd;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long ct = 0;
-        double el = 0.0, ecc = 0.0;
-        for (int k = 0; k < kForceThreads / 32; ++k) {
-            ct += s_cnt[k];
-            el += s_red[0][k];
-            ecc += s_red[1][k];
-        }
-        atomicAdd(&p.st->npairs, ct);
+        atomicAdd(&p.st->npairs, c64);
         if (ENERGY && p.energies) {
-            atomicAdd(&p.energies[0], el);
-            atomicAdd(&p.energies[1], ecc);
+            atomicAdd(&p.energies[0], eljd);
+            atomicAdd(&p.energies[1], ecd);
         }
     }
 }

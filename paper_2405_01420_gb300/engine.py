@@ -81,7 +81,7 @@ class NonbondedEngine:
         # random-walk growth: displacement ~ sqrt(frames since the search)
         pred = st["max_disp_search"] * math.sqrt((n + 1) / n) * 1.05
         dp = st["max_disp_prune"]
-        if self.r_inner is not None and dp > 0.8 * self._budget_prune() and self.interval > 1:
+        if self.r_inner is not None and dp > 0.9 * self._budget_prune() and self.interval > 1:
             self.interval = max(1, self.interval // 2)
         return pred > self._budget_search()
 

@@ -237,10 +237,15 @@ def test_ragged_small_systems(nb, nw):
     pl.search(d["coords"], box, rc, d["excl_off"], d["excl_idx"])
     F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
     assert pl.status() == 0
-    Fo, elj, ec, n = oracle.energy_forces(coords, b.q, b.type, b.ljparams, box, rc, beta, b.excl_off, b.excl_idx)
+    Fo, elj, ec, n, (alj, ac) = oracle.energy_forces(coords, b.q, b.type, b.ljparams, box, rc, beta, b.excl_off,
+                                                     b.excl_idx, abs_sums=True)
     if n:
         compare_forces(F.cpu().numpy(), Fo)
-        check_energies(E, elj, ec)
+        # A handful of pairs cannot average FP32 rounding: the bound here is
+        # 1e-6 of the larger of |E| and the sum of |pair energies|.
+        e = E.cpu().numpy()
+        assert abs(e[0] - elj) <= 1e-6 * max(abs(elj), alj)
+        assert abs(e[1] - ec) <= 1e-6 * max(abs(ec), ac)
     assert pl.stats()["pairs_last"] == oracle.pairs_f32(coords, coords, box, rc, b.excl_off, b.excl_idx,
                                                        count_only=True)
     pl.close()
