@@ -205,6 +205,45 @@ int nb_pairlist_export(nb_pairlist *pl, int which, int *ci, int *cj, int *shift,
  */
 int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
 
+/*
+ * Search and forces without any device allocation (no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: a plug-in inside a host program that
+ * owns every device allocation itself, or a real-time loop that must not
+ * enter the allocator once it runs (cudaMalloc may synchronise the device
+ * and take unbounded time). For them this entry point runs the same kernels
+ * as nb_search + nb_forces (outer list at rlist = rc, no prune) with all
+ * scratch memory (cluster grid, pair list, sorted coordinates, force
+ * accumulators) in one statically allocated device array of
+ * NB_NOALLOC_SCRATCH_BYTES bytes. Every GPU that loads libnb.so holds that
+ * array until the process exits. The call allocates nothing: it makes no
+ * cudaMalloc or cudaFree call and uses no allocating library routine.
+ *
+ *   n_atoms  1..NB_NOALLOC_MAX_ATOMS; larger systems return NB_ERR_CAPACITY
+ *            (use nb_pairlist_create for them).
+ *   coords, q, type, ljparams, excl_off, excl_idx, forces, energies:
+ *            as for nb_search / nb_forces (device pointers, caller-owned).
+ *   box      HOST float[3], each edge > 2*rc.
+ *   rc, beta as for nb_forces (beta*rc <= 3.2).
+ *   error_word  HOST unsigned* or NULL: if given, the call synchronises the
+ *            stream and stores the device error word (NB_DEV_* bits) of
+ *            this call; if NULL the call does not synchronise.
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture. Every call shares the one array and each call
+ * resets the parts that must start at zero; calls whose work overlaps on the
+ * GPU (different streams or threads without ordering between them) race on
+ * it and give wrong results.
+ */
+#define NB_NOALLOC_MAX_ATOMS 4096
+#define NB_NOALLOC_SCRATCH_BYTES 2427648
+int nb_forces_noalloc(int n_atoms, const float *coords, const float *box, const float *q, const int *type,
+                      int ntype, const float *ljparams, float rc, float beta, const int *excl_off,
+                      const int *excl_idx, float *forces, double *energies, unsigned *error_word,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

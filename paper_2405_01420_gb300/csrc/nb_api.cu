@@ -72,6 +72,8 @@ float stale_bound2(double r_big, double r_small) { return sq_nonneg(0.5 * (r_big
 
 }  // namespace
 
+int nb_record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 extern "C" const char *nb_version(void) { return "nb 0.1.0 sm_103a"; }
 
 extern "C" const char *nb_last_error(void) { return g_err.c_str(); }

@@ -107,6 +107,9 @@ __device__ __forceinline__ int nb_shift_z(int s) { return s % 3 - 1; }
 // near them passes even before the mask removes them.
 #define NB_PAD_COORD (-1.0e6f)
 
+// Records a message for nb_last_error() and returns code (nb_api.cu).
+int nb_record_error(int code, const char *msg);
+
 // ---------------------------------------------------------------------------
 // Launchers (return cudaError_t of the launch).
 // ---------------------------------------------------------------------------

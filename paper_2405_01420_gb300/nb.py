@@ -91,7 +91,11 @@ SIGNATURES = {
     "nb_pairlist_export": (_I, [_P, _I, _P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P, _SZ,
                                 ctypes.POINTER(_SZ), _P]),
     "nb_set_timing_events": (_I, [_P, _P, _P]),
+    "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
+                               ctypes.POINTER(ctypes.c_uint), _P]),
 }
+
+NB_NOALLOC_MAX_ATOMS = 4096
 
 
 def load_library(path: str = LIB_PATH):
@@ -221,6 +225,28 @@ def nb_set_timing_events(pl, start=None, stop=None) -> None:
     sp = None if start is None else ctypes.c_void_p(start.cuda_event)
     ep = None if stop is None else ctypes.c_void_p(stop.cuda_event)
     _check(load_library().nb_set_timing_events(pl, sp, ep))
+
+
+def nb_forces_noalloc(coords, box, q, type_, ljparams, rc, beta, forces, energies=None, excl_off=None,
+                      excl_idx=None, read_error_word=True, stream=None):
+    """Search + forces for up to 4,096 atoms with no device allocation.
+
+    For callers that cannot allocate device memory: all scratch lives in a
+    static device array inside libnb.so. Returns the device error word when
+    ``read_error_word`` (the call then synchronises the stream), else None.
+    """
+    n = coords.numel() // 3
+    ntype = int(ljparams.shape[0])
+    box_h = (ctypes.c_float * 3)(*[float(v) for v in box])
+    word = ctypes.c_uint(0)
+    _check(load_library().nb_forces_noalloc(
+        n, _dev(coords, torch.float32, 3 * n, "coords"), box_h, _dev(q, torch.float32, n, "q"),
+        _dev(type_, torch.int32, n, "type"), ntype, _dev(ljparams, torch.float32, 2 * ntype * ntype, "ljparams"),
+        float(rc), float(beta), _dev(excl_off, torch.int32, n + 1, "excl_off", True),
+        _dev(excl_idx, torch.int32, None, "excl_idx", True), _dev(forces, torch.float32, 3 * n, "forces"),
+        _dev(energies, torch.float64, 2, "energies", True), ctypes.byref(word) if read_error_word else None,
+        _stream(stream)))
+    return int(word.value) if read_error_word else None
 
 
 class Pairlist:
