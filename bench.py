@@ -72,6 +72,7 @@ def parse_args():
     ap.add_argument("--evals", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the backward and batched legs")
     return ap.parse_args()
 
 
@@ -234,6 +235,186 @@ def load_traffic():
     return rec.get("bytes_per_launch_96k")
 
 
+def _median_ms(fn, reps: int, stream):
+    import torch
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def bench_backward(dev, reps: int = 30):
+    """Force-matching workload: 24,000 atoms, N(0, 0.4) charges, 4 LJ types.
+
+    Times one forward call (forces + energies) and one forward plus the
+    hand-written adjoint (nb_backward), each through the C ABI on resident
+    inputs, median of ``reps``.
+    """
+    import torch
+    from paper_2405_01420_gb300 import nb
+    b = synth.water_box(8000, 4)
+    p = synth.diff_params(b, seed=4)
+    lj = torch.from_numpy(synth.combine_geometric(p["c6"], p["c12"]).astype(np.float32)).to(dev)
+    x = torch.from_numpy(b.coords).to(dev)
+    q = torch.from_numpy(p["q"].astype(np.float32)).to(dev)
+    t = torch.from_numpy(p["type"]).to(dev)
+    eo = torch.from_numpy(b.excl_off).to(dev)
+    ei = torch.from_numpy(b.excl_idx).to(dev)
+    beta = synth.ewald_beta(RC)
+    pl = nb.Pairlist(b.n_atoms)
+    pl.search(x, b.box, RLIST, eo, ei)
+    pl.prune(x, R_INNER)
+    F = torch.empty((b.n_atoms, 3), dtype=torch.float32, device=dev)
+    E = torch.empty(2, dtype=torch.float64, device=dev)
+    g = torch.randn((b.n_atoms, 3), dtype=torch.float32, device=dev)
+    gx = torch.empty_like(F)
+    gq = torch.empty_like(q)
+    glj = torch.empty((4, 4, 2), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd():
+        nb.nb_forces(pl.handle, x, q, t, lj, RC, beta, F, E)
+
+    def fwd_bwd():
+        nb.nb_forces(pl.handle, x, q, t, lj, RC, beta, F, E)
+        nb.nb_backward(pl.handle, x, q, t, lj, RC, beta, g, gx, gq, glj)
+
+    for _ in range(5):
+        fwd_bwd()
+    t_f = _median_ms(fwd, reps, stream)
+    t_fb = _median_ms(fwd_bwd, reps, stream)
+    assert pl.status() == 0
+    pl.close()
+    return {"workload": "24,000-atom box (8,000 waters), charges N(0,0.4) neutralised, 4 LJ types, rc 1.0 / "
+                        "rlist 1.1 / r_inner 1.04 nm; forces+energies vs forces+energies then nb_backward "
+                        "(dL/dx, dL/dq, dL/dC); median of 30 calls, inputs resident",
+            "us_forward": 1e3 * t_f, "us_forward_backward": 1e3 * t_fb, "ratio_to_plain": t_fb / t_f}
+
+
+def _concat_systems(boxes):
+    off = np.zeros(len(boxes) + 1, np.int32)
+    for k, b in enumerate(boxes):
+        off[k + 1] = off[k] + b.n_atoms
+    eo = [np.zeros(1, np.int32)]
+    ei = []
+    base = 0
+    for k, b in enumerate(boxes):
+        eo.append(b.excl_off[1:] + base)
+        ei.append(b.excl_idx + off[k])
+        base += b.excl_off[-1]
+    return (off, np.concatenate([b.coords for b in boxes]), np.concatenate([b.q for b in boxes]),
+            np.concatenate([b.type for b in boxes]), np.concatenate(eo), np.concatenate(ei),
+            np.stack([b.box for b in boxes]))
+
+
+def _percentile(ts, p):
+    ts = sorted(ts)
+    return ts[min(len(ts) - 1, int(round(p / 100.0 * (len(ts) - 1))))]
+
+
+def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
+    """Batched form: 256 independent water boxes of 1,536..24,000 atoms.
+
+    One batch = search (rlist 1.0) + forces and energies (rc 0.9) of every box.
+    Batched: one pair list over all boxes, the whole batch captured in one
+    CUDA graph and replayed. Plain: one pair list per box, nb_search +
+    nb_forces launched box after box. Per-batch latency from CUDA events.
+    """
+    import torch
+    from paper_2405_01420_gb300 import nb
+    rc, rlist = 0.9, 1.0
+    beta = synth.ewald_beta(rc)
+    boxes = synth.batch_boxes(n_boxes, 1536, 24000, seed=5)
+    off, x, q, t, eo, ei, bx = _concat_systems(boxes)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    xd, qd, td, eod, eid = d(x), d(q), d(t), d(eo), d(ei)
+    lj = d(boxes[0].ljparams)
+    stream = torch.cuda.current_stream(dev)
+    counter = nb.Pairlist.batch(off, bx, count_pairs=True)
+    counter.search(xd, None, rlist, eod, eid)
+    counter.forces(xd, qd, td, lj, rc, beta)
+    pairs = counter.stats()["pairs_last"]
+    assert counter.status() == 0
+    counter.close()
+
+    pl = nb.Pairlist.batch(off, bx)
+    F = torch.empty((pl.n_atoms, 3), dtype=torch.float32, device=dev)
+    E = torch.empty(2 * pl.n_systems, dtype=torch.float64, device=dev)
+    pl.search(xd, None, rlist, eod, eid)
+    pl.forces(xd, qd, td, lj, rc, beta, F, E)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            pl.search(xd, None, rlist, eod, eid, stream=side)
+            pl.forces(xd, qd, td, lj, rc, beta, F, E, stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    graph_ms = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        graph_ms.append(a.elapsed_time(b))
+    assert pl.status() == 0
+    pl.close()
+
+    plain = []
+    for k, bxk in enumerate(boxes):
+        p1 = nb.Pairlist(bxk.n_atoms)
+        plain.append((p1, int(off[k]), int(off[k + 1]), bxk))
+    Fp = torch.empty_like(F)
+    Ep = torch.empty(2 * n_boxes, dtype=torch.float64, device=dev)
+
+    # per-system exclusion slices are rebuilt outside the timed region
+    excl = [((eod[a0:a1 + 1] - eod[a0]).contiguous(), (eid[int(eo[a0]):int(eo[a1])] - a0).contiguous())
+            for (_, a0, a1, _) in plain]
+
+    def plain_batch_pre():
+        for k, (p1, a0, a1, bxk) in enumerate(plain):
+            nb.nb_search(p1.handle, xd[a0:a1], bxk.box, rlist, excl[k][0], excl[k][1])
+            nb.nb_forces(p1.handle, xd[a0:a1], qd[a0:a1], td[a0:a1], lj, rc, beta, Fp[a0:a1], Ep[2 * k:2 * k + 2])
+
+    plain_batch_pre()
+    torch.cuda.synchronize()
+    plain_ms = []
+    for _ in range(plain_reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plain_batch_pre()
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+    for p1, _, _, _ in plain:
+        assert p1.status() == 0
+        p1.close()
+    torch.testing.assert_close(Fp, F, rtol=0, atol=1e-4 * F.abs().max().item())
+    g50, g99 = _percentile(graph_ms, 50), _percentile(graph_ms, 99)
+    p50, p99 = _percentile(plain_ms, 50), _percentile(plain_ms, 99)
+    return {"workload": f"{n_boxes} independent water boxes, {int(off[-1])} atoms in total (1,536..24,000 each, "
+                        "whole waters), rc 0.9 / rlist 1.0 nm; one batch = search + forces + energies of every box",
+            "pairs_per_batch": pairs,
+            "graph_p50_ms": g50, "graph_p99_ms": g99, "graph_pairs_per_s": pairs / (g50 / 1e3),
+            "plain_launches_p50_ms": p50, "plain_launches_p99_ms": p99, "plain_pairs_per_s": pairs / (p50 / 1e3),
+            "speedup_p50": p50 / g50, "graph_reps": reps, "plain_reps": plain_reps}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -276,13 +457,15 @@ def run_ours(args, rank, world, local):
         if kernel_events is not None:
             nb.nb_set_timing_events(eng.pl.handle, None, None)
 
-    # untimed pass: in-range pairs of each evaluation (synchronises every eval)
-    restart()
+    # untimed pass on a counting pair list: in-range pairs of each evaluation
+    # (the count is exact, so it does not depend on which list found them)
+    counter = NonbondedEngine(N, box.box, RC, beta, RLIST, R_INNER, PRUNE_INTERVAL, eo, ei, count_pairs=True)
     pairs = []
     for i in range(args.evals):
-        eng.compute(frames_d[i], q, typ, lj, forces, energies[i])
-        pairs.append(eng.pl.stats()["pairs_last"])
-    assert eng.check() == 0, "device error word set in the counting pass"
+        counter.compute(frames_d[i], q, typ, lj, forces, energies[i])
+        pairs.append(counter.pl.stats()["pairs_last"])
+    assert counter.check() == 0, "device error word set in the counting pass"
+    counter.close()
     pairs_per_step = float(sum(pairs))
 
     for _ in range(args.warmup):
@@ -357,6 +540,9 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": args.evals * (N * 12 + 16)}
         assert eng.check() == 0
 
+    backward = None if args.no_extras else bench_backward(dev)
+    batched = None if args.no_extras else bench_batch(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n_ev, dt, cores = time_oracle(box, frames)
@@ -392,6 +578,8 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": n_launch_search * searches + n_launch_prune * prunes + n_launch_force * args.evals,
+        "backward": backward,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
 

@@ -76,8 +76,12 @@ typedef struct {
     size_t capacity_entries; /* list entries (8x8 cluster pairs) to reserve; 0 = automatic:
                                 200 per 8-atom cluster + 65536, enough for rlist <= ~1.3 nm
                                 at water density */
-    unsigned flags;          /* reserved, must be 0 */
+    unsigned flags;          /* NB_FLAG_* bits, 0 for none */
 } nb_config;
+
+/* nb_config.flags: count the in-range pairs in nb_forces (nb_stats.pairs_last);
+   costs about one instruction per pair, so it is off unless asked for. */
+#define NB_FLAG_COUNT_PAIRS 0x1u
 
 /* Host-side snapshot of a pair list (filled by nb_pairlist_stats). */
 typedef struct {
@@ -88,7 +92,8 @@ typedef struct {
     long long outer_entries; /* cluster pairs in the outer (rlist) list */
     long long inner_entries; /* cluster pairs in the inner (r_inner) list */
     long long capacity_entries;
-    long long pairs_last;    /* in-range atom pairs counted by the last nb_forces */
+    long long pairs_last;    /* in-range atom pairs counted by the last nb_forces, or -1 if the
+                                pair list was created without NB_FLAG_COUNT_PAIRS */
     float rlist;             /* radius of the last search */
     float r_inner;           /* radius of the last prune (0 if none) */
     float max_disp_search;   /* largest atom displacement since the search, as seen by the last call */
@@ -110,6 +115,27 @@ const char *nb_last_error(void);
  */
 int nb_pairlist_create(nb_pairlist **pl, int n_atoms, const nb_config *cfg);
 
+/*
+ * Create one pair list over a batch of independent systems (boxes), for
+ * running many small systems with one set of launches (the batched form of
+ * the path; ensemble-style independent systems, §I-A). Systems are stored
+ * back to back:
+ *   atom_off HOST int[n_systems+1]: system b owns atoms atom_off[b] ..
+ *            atom_off[b+1]-1 of every per-atom array (coords, q, type,
+ *            forces, ...); atom_off[0] = 0.
+ *   boxes    HOST float[3*n_systems]: the orthorhombic box of each system,
+ *            fixed for the lifetime of the list.
+ * Afterwards nb_search (with box = NULL), nb_prune, nb_forces and
+ * nb_backward act on all systems at once; no pair ever joins atoms of two
+ * systems. Exclusion indices are global atom indices. nb_forces writes
+ * energies as double[2*n_systems] ({E_LJ, E_C} per system). Allocates like
+ * nb_pairlist_create and uploads the system table (synchronises once).
+ * Errors: NB_ERR_ARG (no systems, empty system, bad box), NB_ERR_NOMEM,
+ * NB_ERR_CUDA.
+ */
+int nb_batch_create(nb_pairlist **pl, int n_systems, const int *atom_off, const float *boxes,
+                    const nb_config *cfg);
+
 /* Free a pair list and its device buffers. Synchronises the device. NULL is a no-op. */
 int nb_pairlist_destroy(nb_pairlist *pl);
 
@@ -119,7 +145,8 @@ int nb_pairlist_destroy(nb_pairlist *pl);
  * rlist.
  *   coords   device float[3*n_atoms], x,y,z per atom in original order;
  *            any real values (wrapped into the box here).
- *   box      HOST float[3], orthorhombic box edges; each > 2*rlist.
+ *   box      HOST float[3], orthorhombic box edges; each > 2*rlist. Must be
+ *            NULL for a batch (its boxes were fixed at nb_batch_create).
  *   rlist    list radius (nm), > 0.
  *   excl_off device int[n_atoms+1], excl_idx device int[excl_off[n]]:
  *            symmetric exclusion lists in original atom indices (both
@@ -159,7 +186,8 @@ int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, void *stream);
  *   beta     Ewald splitting parameter (nm^-1), 0 <= beta*rc <= 3.2.
  *   forces   device float[3*n_atoms], overwritten, original order.
  *   energies device double[2] = {E_LJ, E_C}, overwritten; may be NULL
- *            (forces only).
+ *            (forces only). For a batch: double[2*n_systems], one pair per
+ *            system.
  * A pair counts iff its mask bit is set and r2 < fl(rc*rc) in FP32, with
  * d = (y_a - y_b) + S and r2 = fma(dz,dz,fma(dy,dy,dx*dx)); y is the image
  * of the current position nearest to the search-time wrapped position.
@@ -171,6 +199,28 @@ int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, void *stream);
 int nb_forces(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
               const float *ljparams, float rc, float beta, float *forces, double *energies,
               void *stream);
+
+/*
+ * Adjoint of nb_forces (the "differentiation" form of the path; the paper
+ * itself has no backward pass): given g = dL/dF for a scalar L of the
+ * forces, the gradients of L with respect to positions, charges and the LJ
+ * matrix, recomputing every pair term over the current list (nothing from
+ * the forward call is stored).
+ *   coords, q, type, ntype, ljparams, rc, beta: as for nb_forces;
+ *            ntype <= NB_BACKWARD_MAX_TYPES.
+ *   g        device float[3*n_atoms], dL/dF in original order.
+ *   grad_x   device float[3*n_atoms], dL/dx (overwritten). With F = -dE/dx
+ *            this is -H g, H the Hessian of E.
+ *   grad_q   device float[n_atoms], dL/dq (overwritten).
+ *   grad_lj  device double[ntype*ntype*2], dL/d(C6, C12) for the symmetric
+ *            LJ matrix: each type pair's derivative is split evenly between
+ *            entries (ti, tj) and (tj, ti) (overwritten).
+ * Errors and device error bits as for nb_forces.
+ */
+#define NB_BACKWARD_MAX_TYPES 4
+int nb_backward(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
+                const float *ljparams, float rc, float beta, const float *g, float *grad_x, float *grad_q,
+                double *grad_lj, void *stream);
 
 /*
  * Read the sticky device error word into *error_word (NB_DEV_* bits).
@@ -206,6 +256,16 @@ int nb_pairlist_export(nb_pairlist *pl, int which, int *ci, int *cj, int *shift,
 int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
 
 /*
+ * Launch shape of the force kernel for later nb_forces calls on this pair
+ * list (measurement and tuning; no counterpart in the paper). The results do
+ * not depend on it, only the speed: threads per block (128 or 256), list
+ * entries staged in shared memory per warp at a time (8 or 16) and CTAs per
+ * SM of the persistent grid (at most what fits; 0 = as many as fit). Zero
+ * for threads or chunk restores the default (256, 16).
+ */
+int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_sm);
+
+/*
  * Search and forces without any device allocation (no counterpart in the
  * paper; it exists for callers that cannot allocate device memory).
  *
@@ -238,7 +298,7 @@ int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
  * it and give wrong results.
  */
 #define NB_NOALLOC_MAX_ATOMS 4096
-#define NB_NOALLOC_SCRATCH_BYTES 2427648
+#define NB_NOALLOC_SCRATCH_BYTES 2450944
 int nb_forces_noalloc(int n_atoms, const float *coords, const float *box, const float *q, const int *type,
                       int ntype, const float *ljparams, float rc, float beta, const int *excl_off,
                       const int *excl_idx, float *forces, double *energies, unsigned *error_word,

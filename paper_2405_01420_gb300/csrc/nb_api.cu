@@ -52,7 +52,8 @@ void free_buffers(nb_pairlist *pl) {
                     pl->atom_slot, pl->xw,     pl->keys,           pl->perm,           pl->pos,
                     pl->xref,   pl->xprune,    pl->xq,             pl->tsort,          pl->fsort,
                     pl->bbox,   pl->outer,     pl->inner,          pl->ci_start,       pl->ci_len_outer,
-                    pl->ci_len_inner};
+                    pl->ci_len_inner, pl->gsort,   pl->bsort,          pl->glj_acc,        pl->sys,
+                    pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -70,6 +71,93 @@ float sq_nonneg(double x) { return x > 0.0 ? (float)(x * x) : 0.0f; }
 // FP32 rounding of the distances cannot use up the margin.
 float stale_bound2(double r_big, double r_small) { return sq_nonneg(0.5 * (r_big - r_small) - 1e-5); }
 
+
+
+// xy columns of ~cubic 8-atom cells at the mean density of one system,
+// at most ncol_cap columns.
+void grid_for(double Lx, double Ly, double Lz, double n, long long ncol_cap, int *ncx_out, int *ncy_out) {
+    const double side = std::cbrt(NB_CLUSTER * Lx * Ly * Lz / n);
+    int ncx = std::max(1, (int)std::floor(Lx / side));
+    int ncy = std::max(1, (int)std::floor(Ly / side));
+    while (n / ((double)ncx * ncy) > NB_MAX_COL_ATOMS / 4 && (long long)(ncx + 1) * (ncy + 1) <= ncol_cap) {
+        ++ncx;
+        ++ncy;
+    }
+    while ((long long)ncx * ncy > ncol_cap) {
+        if (ncx >= ncy) --ncx; else --ncy;
+    }
+    *ncx_out = ncx;
+    *ncy_out = ncy;
+}
+
+nb_sys make_sys(const float *box, int ncx, int ncy, int col_off, int atom_off, int n_atoms) {
+    nb_sys S;
+    std::memset(&S, 0, sizeof(S));
+    S.box = make_float4(box[0], box[1], box[2], 0.0f);
+    S.inv_sx = (float)(ncx / (double)box[0]);
+    S.inv_sy = (float)(ncy / (double)box[1]);
+    S.ncx = ncx;
+    S.ncy = ncy;
+    S.col_off = col_off;
+    S.atom_off = atom_off;
+    S.n_atoms = n_atoms;
+    return S;
+}
+
+// Allocates every device buffer of a pair list over n atoms in nsys systems.
+int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const char *who) {
+    if (cfg && (cfg->flags & ~(unsigned)NB_FLAG_COUNT_PAIRS) != 0u)
+        return fail(NB_ERR_ARG, "%s: unknown flags 0x%x", who, cfg->flags);
+    NB_CUDA(cudaGetDevice(&pl->device));
+    NB_CUDA(cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device));
+    const long long nclus = (n + NB_CLUSTER - 1) / NB_CLUSTER;
+    pl->n_atoms = (int)n;
+    size_t cap = (cfg && cfg->capacity_entries) ? cfg->capacity_entries : (size_t)nclus * 200 + 65536;
+    if (cap >= (size_t)1 << 31) return fail(NB_ERR_ARG, "%s: capacity_entries %zu >= 2^31", who, cap);
+    pl->cap = cap;
+    pl->flags = cfg ? cfg->flags : 0u;
+    const size_t nslot = (size_t)pl->nc_max * NB_CLUSTER;
+    size_t total = 0;
+    bool good = alloc(&pl->st, 1, &total) && alloc(&pl->col_count, pl->ncol_max, &total) &&
+                alloc(&pl->col_atom_start, pl->ncol_max + 1, &total) &&
+                alloc(&pl->col_clus_start, pl->ncol_max + 1, &total) && alloc(&pl->atom_col, n, &total) &&
+                alloc(&pl->atom_slot, n, &total) && alloc(&pl->xw, n, &total) && alloc(&pl->keys, n, &total) &&
+                alloc(&pl->perm, nslot, &total) && alloc(&pl->pos, n, &total) && alloc(&pl->xref, nslot, &total) &&
+                alloc(&pl->xprune, nslot, &total) && alloc(&pl->xq, nslot, &total) &&
+                alloc(&pl->tsort, nslot, &total) && alloc(&pl->fsort, nslot, &total) &&
+                alloc(&pl->bbox, 2 * (size_t)pl->nc_max, &total) && alloc(&pl->outer, cap, &total) &&
+                alloc(&pl->inner, cap, &total) && alloc(&pl->ci_start, pl->nc_max, &total) &&
+                alloc(&pl->ci_len_outer, pl->nc_max, &total) && alloc(&pl->ci_len_inner, pl->nc_max, &total) &&
+                alloc(&pl->gsort, nslot, &total) && alloc(&pl->bsort, nslot, &total) &&
+                alloc(&pl->glj_acc, 2 * NB_MAX_TYPES * NB_MAX_TYPES, &total) && alloc(&pl->sys, pl->nsys, &total) &&
+                alloc(&pl->sys_shift, 27 * (size_t)pl->nsys, &total) && alloc(&pl->atom_sys, n, &total) &&
+                alloc(&pl->col_sys, pl->ncol_max, &total) && alloc(&pl->clus_sys, pl->nc_max, &total);
+    if (!good) {
+        cudaGetLastError();  // clear the allocation error
+        return fail(NB_ERR_NOMEM, "%s: cudaMalloc of %zu bytes failed", who, total);
+    }
+    pl->sys_host = new (std::nothrow) nb_sys[pl->nsys];
+    if (!pl->sys_host) return fail(NB_ERR_NOMEM, "%s: host allocation failed", who);
+    // Defined contents for everything a kernel may read before the first search writes it.
+    NB_CUDA(cudaMemset(pl->st, 0, sizeof(nb_dev_state)));
+    NB_CUDA(cudaMemset(pl->pos, 0, sizeof(int) * (size_t)n));
+    NB_CUDA(cudaMemset(pl->perm, 0xff, sizeof(int) * nslot));
+    NB_CUDA(cudaMemset(pl->ci_start, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->ci_len_outer, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->ci_len_inner, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->fsort, 0, sizeof(float4) * nslot));
+    NB_CUDA(cudaMemset(pl->atom_sys, 0, sizeof(int) * (size_t)n));
+    NB_CUDA(cudaMemset(pl->col_sys, 0, sizeof(int) * (size_t)pl->ncol_max));
+    NB_CUDA(cudaMemset(pl->clus_sys, 0, sizeof(int) * (size_t)pl->nc_max));
+    return NB_OK;
+}
+
+void destroy_partial(nb_pairlist *pl) {
+    free_buffers(pl);
+    delete[] pl->sys_host;
+    delete pl;
+}
+
 }  // namespace
 
 int nb_record_error(int code, const char *msg) { return fail(code, "%s", msg); }
@@ -82,50 +170,79 @@ extern "C" int nb_pairlist_create(nb_pairlist **out, int n_atoms, const nb_confi
     if (!out) return fail(NB_ERR_ARG, "nb_pairlist_create: out is NULL");
     *out = nullptr;
     if (n_atoms < 1) return fail(NB_ERR_ARG, "nb_pairlist_create: n_atoms = %d < 1", n_atoms);
-    if (cfg && cfg->flags != 0u) return fail(NB_ERR_ARG, "nb_pairlist_create: flags must be 0");
     nb_pairlist *pl = new (std::nothrow) nb_pairlist;
     if (!pl) return fail(NB_ERR_NOMEM, "nb_pairlist_create: host allocation failed");
     std::memset(pl, 0, sizeof(*pl));
-    NB_CUDA(cudaGetDevice(&pl->device));
-    NB_CUDA(cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device));
-    const long long n = n_atoms;
-    const long long nclus = (n + NB_CLUSTER - 1) / NB_CLUSTER;
-    pl->n_atoms = n_atoms;
+    const long long nclus = ((long long)n_atoms + NB_CLUSTER - 1) / NB_CLUSTER;
+    pl->nsys = 1;
     pl->ncol_max = (int)nclus;
     pl->nc_max = (int)(nclus + pl->ncol_max);
-    size_t cap = (cfg && cfg->capacity_entries) ? cfg->capacity_entries : (size_t)nclus * 200 + 65536;
-    if (cap >= (size_t)1 << 31) {
-        delete pl;
-        return fail(NB_ERR_ARG, "nb_pairlist_create: capacity_entries %zu >= 2^31", cap);
+    const int rc = alloc_pairlist(pl, n_atoms, cfg, "nb_pairlist_create");
+    if (rc != NB_OK) {
+        destroy_partial(pl);
+        return rc;
     }
-    pl->cap = cap;
-    const size_t nslot = (size_t)pl->nc_max * NB_CLUSTER;
-    size_t total = 0;
-    bool good = alloc(&pl->st, 1, &total) && alloc(&pl->col_count, pl->ncol_max, &total) &&
-                alloc(&pl->col_atom_start, pl->ncol_max + 1, &total) &&
-                alloc(&pl->col_clus_start, pl->ncol_max + 1, &total) && alloc(&pl->atom_col, n, &total) &&
-                alloc(&pl->atom_slot, n, &total) && alloc(&pl->xw, n, &total) && alloc(&pl->keys, n, &total) &&
-                alloc(&pl->perm, nslot, &total) && alloc(&pl->pos, n, &total) && alloc(&pl->xref, nslot, &total) &&
-                alloc(&pl->xprune, nslot, &total) && alloc(&pl->xq, nslot, &total) &&
-                alloc(&pl->tsort, nslot, &total) && alloc(&pl->fsort, nslot, &total) &&
-                alloc(&pl->bbox, 2 * (size_t)pl->nc_max, &total) && alloc(&pl->outer, cap, &total) &&
-                alloc(&pl->inner, cap, &total) && alloc(&pl->ci_start, pl->nc_max, &total) &&
-                alloc(&pl->ci_len_outer, pl->nc_max, &total) && alloc(&pl->ci_len_inner, pl->nc_max, &total);
-    if (!good) {
-        cudaGetLastError();  // clear the allocation error
-        free_buffers(pl);
-        delete pl;
-        return fail(NB_ERR_NOMEM, "nb_pairlist_create: cudaMalloc of %zu bytes failed", total);
-    }
-    // Defined contents for everything a kernel may read before the first search writes it.
-    NB_CUDA(cudaMemset(pl->st, 0, sizeof(nb_dev_state)));
-    NB_CUDA(cudaMemset(pl->pos, 0, sizeof(int) * (size_t)n));
-    NB_CUDA(cudaMemset(pl->perm, 0xff, sizeof(int) * nslot));
-    NB_CUDA(cudaMemset(pl->ci_start, 0, sizeof(int) * (size_t)pl->nc_max));
-    NB_CUDA(cudaMemset(pl->ci_len_outer, 0, sizeof(int) * (size_t)pl->nc_max));
-    NB_CUDA(cudaMemset(pl->ci_len_inner, 0, sizeof(int) * (size_t)pl->nc_max));
-    NB_CUDA(cudaMemset(pl->fsort, 0, sizeof(float4) * nslot));
     NB_CUDA(cudaDeviceSynchronize());
+    *out = pl;
+    return ok();
+}
+
+extern "C" int nb_batch_create(nb_pairlist **out, int n_systems, const int *atom_off, const float *boxes,
+                               const nb_config *cfg) {
+    if (!out || !atom_off || !boxes) return fail(NB_ERR_ARG, "nb_batch_create: NULL argument");
+    *out = nullptr;
+    if (n_systems < 1) return fail(NB_ERR_ARG, "nb_batch_create: n_systems = %d < 1", n_systems);
+    if (atom_off[0] != 0) return fail(NB_ERR_ARG, "nb_batch_create: atom_off[0] must be 0");
+    for (int b = 0; b < n_systems; ++b) {
+        if (atom_off[b + 1] <= atom_off[b]) return fail(NB_ERR_ARG, "nb_batch_create: system %d has no atoms", b);
+        for (int k = 0; k < 3; ++k)
+            if (!(boxes[3 * b + k] > 0.0f) || !std::isfinite(boxes[3 * b + k]))
+                return fail(NB_ERR_ARG, "nb_batch_create: bad box edge for system %d", b);
+    }
+    const long long n = atom_off[n_systems];
+    std::vector<nb_sys> sys(n_systems);
+    long long ncol = 0, ncl = 0;
+    for (int b = 0; b < n_systems; ++b) {
+        const long long nb = atom_off[b + 1] - atom_off[b];
+        const long long cap_cols = (nb + NB_CLUSTER - 1) / NB_CLUSTER;
+        int ncx, ncy;
+        grid_for(boxes[3 * b], boxes[3 * b + 1], boxes[3 * b + 2], (double)nb, cap_cols, &ncx, &ncy);
+        sys[b] = make_sys(boxes + 3 * b, ncx, ncy, (int)ncol, atom_off[b], (int)nb);
+        ncol += (long long)ncx * ncy;
+        ncl += cap_cols;
+    }
+    if (n + ncol + ncl >= ((long long)1 << 28)) return fail(NB_ERR_ARG, "nb_batch_create: batch too large");
+    nb_pairlist *pl = new (std::nothrow) nb_pairlist;
+    if (!pl) return fail(NB_ERR_NOMEM, "nb_batch_create: host allocation failed");
+    std::memset(pl, 0, sizeof(*pl));
+    pl->nsys = n_systems;
+    pl->batch = 1;
+    pl->ncol_max = (int)ncol;
+    pl->ncol = (int)ncol;
+    pl->nc_max = (int)(ncl + ncol);
+    int rc = alloc_pairlist(pl, n, cfg, "nb_batch_create");
+    if (rc == NB_OK) {
+        std::vector<float4> shift(27 * (size_t)n_systems);
+        std::vector<int> atom_sys(n), col_sys(ncol);
+        for (int b = 0; b < n_systems; ++b) {
+            pl->sys_host[b] = sys[b];
+            for (int k = 0; k < 27; ++k)
+                shift[27 * b + k] = make_float4((float)((k / 9) - 1) * boxes[3 * b], (float)(((k / 3) % 3) - 1) * boxes[3 * b + 1],
+                                                (float)((k % 3) - 1) * boxes[3 * b + 2], 0.0f);
+            for (int i = atom_off[b]; i < atom_off[b + 1]; ++i) atom_sys[i] = b;
+            for (int c = 0; c < sys[b].ncx * sys[b].ncy; ++c) col_sys[sys[b].col_off + c] = b;
+        }
+        if (cudaMemcpy(pl->sys, sys.data(), sizeof(nb_sys) * n_systems, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->sys_shift, shift.data(), sizeof(float4) * shift.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->atom_sys, atom_sys.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(pl->col_sys, col_sys.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            rc = fail(NB_ERR_CUDA, "nb_batch_create: upload of the system table failed");
+    }
+    if (rc != NB_OK) {
+        destroy_partial(pl);
+        return rc;
+    }
     *out = pl;
     return ok();
 }
@@ -135,48 +252,50 @@ extern "C" int nb_pairlist_destroy(nb_pairlist *pl) {
     DeviceGuard g(pl->device);
     cudaDeviceSynchronize();
     free_buffers(pl);
+    delete[] pl->sys_host;
     delete pl;
     return ok();
 }
 
 extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box, float rlist,
                          const int *excl_off, const int *excl_idx, void *stream) {
-    if (!pl || !coords || !box) return fail(NB_ERR_ARG, "nb_search: NULL pair list, coords or box");
+    if (!pl || !coords) return fail(NB_ERR_ARG, "nb_search: NULL pair list or coords");
+    if (pl->batch && box)
+        return fail(NB_ERR_ARG, "nb_search: the boxes of a batch are fixed at nb_batch_create; pass box = NULL");
+    if (!pl->batch && !box) return fail(NB_ERR_ARG, "nb_search: box is NULL");
     if ((excl_off == nullptr) != (excl_idx == nullptr))
         return fail(NB_ERR_ARG, "nb_search: excl_off and excl_idx must both be given or both NULL");
     if (!(rlist > 0.0f) || !std::isfinite(rlist)) return fail(NB_ERR_ARG, "nb_search: rlist = %g", rlist);
-    for (int k = 0; k < 3; ++k) {
-        if (!std::isfinite(box[k]) || !(box[k] > 2.0f * rlist))
-            return fail(NB_ERR_ARG, "nb_search: box[%d] = %g must exceed 2*rlist = %g", k, box[k], 2.0f * rlist);
+    const float *boxes = pl->batch ? nullptr : box;
+    float lmax = 0.0f;
+    for (int b = 0; b < pl->nsys; ++b) {
+        float L[3];
+        for (int k = 0; k < 3; ++k) {
+            L[k] = boxes ? boxes[k] : (k == 0 ? pl->sys_host[b].box.x : (k == 1 ? pl->sys_host[b].box.y : pl->sys_host[b].box.z));
+            if (!std::isfinite(L[k]) || !(L[k] > 2.0f * rlist))
+                return fail(NB_ERR_ARG, "nb_search: box edge %g (system %d) must exceed 2*rlist = %g", L[k], b,
+                            2.0f * rlist);
+            lmax = std::max(lmax, L[k]);
+        }
     }
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
-    for (int k = 0; k < 3; ++k) pl->box[k] = box[k];
-
-    // xy columns of ~cubic 8-atom cells at the mean density
-    const double Lx = box[0], Ly = box[1], Lz = box[2];
-    const double n = pl->n_atoms;
-    const double side = std::cbrt(NB_CLUSTER * Lx * Ly * Lz / n);
-    int ncx = std::max(1, (int)std::floor(Lx / side));
-    int ncy = std::max(1, (int)std::floor(Ly / side));
-    while (n / ((double)ncx * ncy) > NB_MAX_COL_ATOMS / 4 && (long long)(ncx + 1) * (ncy + 1) <= pl->ncol_max) {
-        ++ncx;
-        ++ncy;
+    if (!pl->batch) {
+        for (int k = 0; k < 3; ++k) pl->box[k] = box[k];
+        int ncx, ncy;
+        grid_for(box[0], box[1], box[2], (double)pl->n_atoms, pl->ncol_max, &ncx, &ncy);
+        pl->ncx = ncx;
+        pl->ncy = ncy;
+        pl->ncol = ncx * ncy;
+        pl->sys_host[0] = make_sys(box, ncx, ncy, 0, 0, pl->n_atoms);
+        NB_CUDA(nb_launch_set_system(pl, pl->sys_host[0], s));
     }
-    while ((long long)ncx * ncy > pl->ncol_max) {
-        if (ncx >= ncy) --ncx; else --ncy;
-    }
-    pl->ncx = ncx;
-    pl->ncy = ncy;
-    pl->ncol = ncx * ncy;
-
     NB_CUDA(cudaMemsetAsync(&pl->st->list_count, 0, sizeof(unsigned long long), s));
-    NB_CUDA(nb_launch_grid_sort(pl, coords, (float)(ncx / Lx), (float)(ncy / Ly), s));
+    NB_CUDA(nb_launch_grid_sort(pl, coords, s));
 
     // The bounding-box test uses a radius inflated by a few ulps of the box
     // edge, so that every pair within rlist under the FP32 distance contract
     // is in the list (the list is a buffered superset anyway).
-    const float lmax = std::max(box[0], std::max(box[1], box[2]));
     const double ulp = (double)std::nextafter(lmax, 2.0f * lmax) - lmax;
     const double rle = rlist + std::max(1e-5, 8.0 * ulp) + 1e-6 * rlist;
     const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
@@ -227,6 +346,27 @@ extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, c
     return ok();
 }
 
+extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
+                           const float *ljparams, float rc, float beta, const float *g, float *grad_x,
+                           float *grad_q, double *grad_lj, void *stream) {
+    if (!pl || !coords || !q || !type || !ljparams || !g || !grad_x || !grad_q || !grad_lj)
+        return fail(NB_ERR_ARG, "nb_backward: NULL argument");
+    if (!pl->searched) return fail(NB_ERR_STATE, "nb_backward: no search yet");
+    if (ntype < 1 || ntype > NB_BACKWARD_MAX_TYPES)
+        return fail(NB_ERR_ARG, "nb_backward: ntype = %d not in [1, %d]", ntype, NB_BACKWARD_MAX_TYPES);
+    const float rmax = pl->has_inner ? pl->r_inner : pl->rlist;
+    if (!(rc > 0.0f) || !(rc <= rmax))
+        return fail(NB_ERR_ARG, "nb_backward: rc = %g must be in (0, %g] (list radius)", rc, rmax);
+    if (!(beta >= 0.0f) || !((double)beta * rc <= 3.2))
+        return fail(NB_ERR_ARG, "nb_backward: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
+    DeviceGuard gd(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, nullptr, s));
+    NB_CUDA(nb_launch_backward(pl, ntype, ljparams, rc, beta, g, grad_x, grad_q, grad_lj,
+                               stale_bound2(pl->rlist, rc), stale_bound2(pl->r_inner, rc), s));
+    return ok();
+}
+
 extern "C" int nb_status(nb_pairlist *pl, unsigned *error_word, int clear, void *stream) {
     if (!pl || !error_word) return fail(NB_ERR_ARG, "nb_status: NULL argument");
     DeviceGuard g(pl->device);
@@ -254,7 +394,7 @@ extern "C" int nb_pairlist_stats(nb_pairlist *pl, nb_stats *out, void *stream) {
     out->outer_entries = (long long)st.list_count;
     out->inner_entries = pl->has_inner ? (long long)st.inner_count : 0;
     out->capacity_entries = (long long)pl->cap;
-    out->pairs_last = (long long)st.npairs;
+    out->pairs_last = (pl->flags & NB_FLAG_COUNT_PAIRS) ? (long long)st.npairs : -1;
     out->rlist = pl->rlist;
     out->r_inner = pl->r_inner;
     float ds, dp;
@@ -319,5 +459,17 @@ extern "C" int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop) {
         return fail(NB_ERR_ARG, "nb_set_timing_events: give both events or neither");
     pl->ev_start = (cudaEvent_t)start;
     pl->ev_stop = (cudaEvent_t)stop;
+    return ok();
+}
+
+extern "C" int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_sm) {
+    if (!pl) return fail(NB_ERR_ARG, "nb_set_force_shape: NULL pair list");
+    if (threads != 0 && threads != 128 && threads != 256)
+        return fail(NB_ERR_ARG, "nb_set_force_shape: threads must be 0, 128 or 256");
+    if (chunk != 0 && chunk != 8 && chunk != 16) return fail(NB_ERR_ARG, "nb_set_force_shape: chunk must be 0, 8 or 16");
+    if (blocks_per_sm < 0) return fail(NB_ERR_ARG, "nb_set_force_shape: blocks_per_sm < 0");
+    pl->force_threads = threads;
+    pl->force_chunk = chunk;
+    pl->force_blocks_per_sm = blocks_per_sm;
     return ok();
 }

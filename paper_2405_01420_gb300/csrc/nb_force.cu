@@ -7,7 +7,8 @@
 //            position. Zeroes the force accumulators, tracks the largest
 //            displacement since the search and since the last prune.
 // k_force    persistent grid, one warp per i-cluster taken from a work
-//            counter. Lane l owns j-atom b = l & 7 and i-atoms l >> 3 and
+//            counter. List entries and their j-cluster data are staged in
+//            shared memory 16 at a time. Lane l owns j-atom b = l & 7 and i-atoms l >> 3 and
 //            (l >> 3) + 4, i.e. exactly mask bits l (low word) and 32 + l
 //            (high word). i-forces stay in registers for the whole list of
 //            ci; j-forces are reduced across the four lanes sharing b with
@@ -21,7 +22,6 @@
 
 namespace {
 
-constexpr int kForceThreads = 256;
 
 struct GatherParams {
     const int *perm;
@@ -34,8 +34,10 @@ struct GatherParams {
     int *tsort;
     float4 *fsort;
     nb_dev_state *st;
-    double *energies;
-    float Lx, Ly, Lz;
+    double *energies;  // [2 nsys] or NULL
+    const nb_sys *sys;
+    const int *atom_sys;
+    int nsys;
     int snapshot;
     int ntype;
 };
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
         p.fsort[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (atom < 0) continue;
         const float4 r = p.xref[slot];
+        const float4 L = p.sys[p.atom_sys[atom]].box;
         float x = p.coords[3 * atom + 0], y = p.coords[3 * atom + 1], z = p.coords[3 * atom + 2];
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
             atomicOr(&p.st->err, NB_DEV_NONFINITE);
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
             y = r.y;
             z = r.z;
         }
-        const float yx = nb_image(x, r.x, p.Lx), yy = nb_image(y, r.y, p.Ly), yz = nb_image(z, r.z, p.Lz);
+        const float yx = nb_image(x, r.x, L.x), yy = nb_image(y, r.y, L.y), yz = nb_image(z, r.z, L.z);
         p.xq[slot] = make_float4(yx, yy, yz, p.q ? p.q[atom] : 0.0f);
         if (p.type) {
             int t = p.type[atom];
@@ -89,17 +92,17 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
         if (d2s_max > 0.0f) atomicMax(&p.st->cur_d2_search, __float_as_uint(d2s_max));
         if (d2p_max > 0.0f) atomicMax(&p.st->cur_d2_prune, __float_as_uint(d2p_max));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        p.st->work = 0u;
-        p.st->npairs = 0ull;
-        if (p.snapshot) {  // a prune follows this gather
-            p.st->work_prune = 0u;
-            p.st->inner_count = 0ull;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            p.st->work = 0u;
+            p.st->npairs = 0ull;
+            if (p.snapshot) {  // a prune follows this gather
+                p.st->work_prune = 0u;
+                p.st->inner_count = 0ull;
+            }
         }
-        if (p.energies) {
-            p.energies[0] = 0.0;
-            p.energies[1] = 0.0;
-        }
+        if (p.energies)
+            for (int k = threadIdx.x; k < 2 * p.nsys; k += blockDim.x) p.energies[k] = 0.0;
     }
 }
 
@@ -112,18 +115,39 @@ struct ForceParams {
     const int *ci_len;
     const float *ljparams;
     nb_dev_state *st;
-    double *energies;
+    double *energies;         // [2 nsys]
+    const float4 *sys_shift;  // [27 nsys]
+    const int *clus_sys;
     int ntype;
     float rc6inv, rc12inv;  // 1/rc^6, 1/rc^12 for the LJ potential shift
-    float Lx, Ly, Lz;
     nb_coul cc;
     float stale_search2, stale_prune2;
     int has_inner;
 };
 
-template <bool ENERGY>
-__global__ void __launch_bounds__(kForceThreads, 4) k_force(ForceParams p) {
-    __shared__ float4 s_lj[NB_MAX_TYPES * NB_MAX_TYPES];
+
+// Adds a warp's FP64 energy partials (E_LJ, E_C) of one system to out[0..1].
+__device__ __forceinline__ void flush_energies(double ec, double elj, int lane, double *out) {
+    for (int o = 16; o > 0; o >>= 1) {
+        ec += __shfl_xor_sync(0xffffffffu, ec, o);
+        elj += __shfl_xor_sync(0xffffffffu, elj, o);
+    }
+    if (lane == 0 && out) {
+        atomicAdd(&out[0], elj);
+        atomicAdd(&out[1], ec);
+    }
+}
+
+// THREADS per block and CHUNK list entries staged per warp are launch
+// shapes the autotuner chooses among (nb_set_force_shape); both keep the
+// register cap at 64 (4 blocks of 256 or 8 of 128 threads per SM).
+template <bool ENERGY, bool COUNT, int THREADS, int CHUNK>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p) {
+    constexpr int kWarps = THREADS / 32;
+    extern __shared__ float4 s_lj[];  // ntype^2 entries (C6, C12, E shift, 0)
+    __shared__ int4 s_ent[kWarps][CHUNK];
+    __shared__ float4 s_xj[kWarps][CHUNK * NB_CLUSTER];
+    __shared__ int s_tj[kWarps][CHUNK * NB_CLUSTER];
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -142,21 +166,33 @@ __global__ void __launch_bounds__(kForceThreads, 4) k_force(ForceParams p) {
     }
     __syncthreads();
 
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = lane & 7, a1 = lane >> 3, a2 = a1 + 4;
     const unsigned lanebit = 1u << lane;
     const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
     const int comp = (hi16 ? 2 : 0) + (hi8 ? 1 : 0);  // component this lane adds after the reduce-scatter
+    int4 *ent = s_ent[warp];
+    float4 *sxj = s_xj[warp];
+    int *stj = s_tj[warp];
     const int nc = p.st->nc;
-    double ecd = 0.0, eljd = 0.0;
+    double ecd = 0.0, eljd = 0.0;  // energies of system cur_sys not yet added to the output
+    int cur_sys = -1;
     unsigned cnt = 0;
 
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= (unsigned)nc) break;
         const int ci = (int)w;
+        const int csys = (w < (unsigned)nc) ? p.clus_sys[ci] : -1;
+        if (ENERGY && csys != cur_sys) {
+            if (cur_sys >= 0) flush_energies(ecd, eljd, lane, p.energies + 2 * cur_sys);
+            ecd = 0.0;
+            eljd = 0.0;
+            cur_sys = csys;
+        }
+        if (w >= (unsigned)nc) break;
+        const float4 *shift = p.sys_shift + 27 * csys;
         const int k0 = p.ci_start[ci], k1 = k0 + p.ci_len[ci];
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
         const float qi1 = xi1.w * NB_COULOMB_F, qi2 = xi2.w * NB_COULOMB_F;
@@ -165,62 +201,61 @@ __global__ void __launch_bounds__(kForceThreads, 4) k_force(ForceParams p) {
         float3 fi1 = make_float3(0.0f, 0.0f, 0.0f), fi2 = make_float3(0.0f, 0.0f, 0.0f);
         float ec = 0.0f, ecomp = 0.0f, elj = 0.0f, eljcomp = 0.0f;
 
-        // Software pipeline: the entry and j-atom data of tile k+1 load while
-        // tile k computes.
-        int4 e_nx = make_int4(0, NB_SHIFT_CENTER, 0, 0);
-        float4 xj_nx = make_float4(0.f, 0.f, 0.f, 0.f);
-        int tj_nx = 0;
-        if (k0 < k1) {
-            e_nx = p.list[k0];
-            xj_nx = p.xq[e_nx.x * NB_CLUSTER + b];
-            tj_nx = p.tsort[e_nx.x * NB_CLUSTER + b];
-        }
-        for (int k = k0; k < k1; ++k) {
-            const int4 e = e_nx;
-            const float4 xj = xj_nx;
-            const int tj = tj_nx;
-            if (k + 1 < k1) {
-                e_nx = p.list[k + 1];
-                xj_nx = p.xq[e_nx.x * NB_CLUSTER + b];
-                tj_nx = p.tsort[e_nx.x * NB_CLUSTER + b];
+        for (int base = k0; base < k1; base += CHUNK) {
+            // Stage up to CHUNK entries and their j-cluster coordinates and
+            // types: independent, batched loads instead of one dependent
+            // chain per tile.
+            const int nch = min(CHUNK, k1 - base);
+            __syncwarp();
+            if (lane < nch) ent[lane] = p.list[base + lane];
+            __syncwarp();
+            for (int idx = lane; idx < nch * NB_CLUSTER; idx += 32) {
+                const int slot = ent[idx >> 3].x * NB_CLUSTER + (idx & 7);
+                sxj[idx] = p.xq[slot];
+                stj[idx] = p.tsort[slot];
             }
-            const int cj = e.x, sidx = e.y;
-            const unsigned mlo = (unsigned)e.z, mhi = (unsigned)e.w;
-            const int sj = cj * NB_CLUSTER + b;
-            float3 fj = make_float3(0.0f, 0.0f, 0.0f);
-            float ect = 0.0f, eljt = 0.0f;
-            if (sidx == NB_SHIFT_CENTER) {
-                if (mlo) cnt += nb_pair<false, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
-                                                       (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
-                if (mhi) cnt += nb_pair<false, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
-                                                       (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
-            } else {
-                const float Sx = (float)nb_shift_x(sidx) * p.Lx;
-                const float Sy = (float)nb_shift_y(sidx) * p.Ly;
-                const float Sz = (float)nb_shift_z(sidx) * p.Lz;
-                if (mlo) cnt += nb_pair<true, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], Sx, Sy, Sz,
-                                                      (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
-                if (mhi) cnt += nb_pair<true, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], Sx, Sy, Sz,
-                                                      (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
-            }
-            // Reduce fj over the lanes l, l^8, l^16, l^24 (same b) as a
-            // reduce-scatter: afterwards lane l holds component comp.
-            float ka = hi16 ? fj.z : fj.x, sa = hi16 ? fj.x : fj.z;
-            float kb = hi16 ? 0.0f : fj.y, sb = hi16 ? fj.y : 0.0f;
-            ka += __shfl_xor_sync(0xffffffffu, sa, 16);
-            kb += __shfl_xor_sync(0xffffffffu, sb, 16);
-            float kk = hi8 ? kb : ka, ss = hi8 ? ka : kb;
-            kk += __shfl_xor_sync(0xffffffffu, ss, 8);
-            if (comp < 3) atomicAdd(p.fsort + 4 * sj + comp, kk);
-            if (ENERGY) {  // Kahan-compensated sums across the tiles of ci
-                const float y = ect - ecomp;
-                const float t = ec + y;
-                ecomp = (t - ec) - y;
-                ec = t;
-                const float yl = eljt - eljcomp;
-                const float tl = elj + yl;
-                eljcomp = (tl - elj) - yl;
-                elj = tl;
+            __syncwarp();
+            for (int t = 0; t < nch; ++t) {
+                const int4 e = ent[t];
+                const float4 xj = sxj[t * NB_CLUSTER + b];
+                const int tj = stj[t * NB_CLUSTER + b];
+                const int sidx = e.y;
+                const unsigned mlo = (unsigned)e.z, mhi = (unsigned)e.w;
+                float3 fj = make_float3(0.0f, 0.0f, 0.0f);
+                float ect = 0.0f, eljt = 0.0f;
+                int c1 = 0, c2 = 0;
+                if (sidx == NB_SHIFT_CENTER) {
+                    if (mlo) c1 = nb_pair<false, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
+                                                         (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
+                    if (mhi) c2 = nb_pair<false, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
+                                                         (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
+                } else {
+                    const float4 S = shift[sidx];
+                    if (mlo) c1 = nb_pair<true, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], S.x, S.y, S.z,
+                                                        (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
+                    if (mhi) c2 = nb_pair<true, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], S.x, S.y, S.z,
+                                                        (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
+                }
+                if (COUNT) cnt += c1 + c2;
+                // Reduce fj over the lanes l, l^8, l^16, l^24 (same b) as a
+                // reduce-scatter: afterwards lane l holds component comp.
+                float ka = hi16 ? fj.z : fj.x, sa = hi16 ? fj.x : fj.z;
+                float kb = hi16 ? 0.0f : fj.y, sb = hi16 ? fj.y : 0.0f;
+                ka += __shfl_xor_sync(0xffffffffu, sa, 16);
+                kb += __shfl_xor_sync(0xffffffffu, sb, 16);
+                float kk = hi8 ? kb : ka, ss = hi8 ? ka : kb;
+                kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+                if (comp < 3) atomicAdd(p.fsort + 4 * (e.x * NB_CLUSTER + b) + comp, kk);
+                if (ENERGY) {  // Kahan-compensated sums across the tiles of ci
+                    const float y = ect - ecomp;
+                    const float tt = ec + y;
+                    ecomp = (tt - ec) - y;
+                    ec = tt;
+                    const float yl = eljt - eljcomp;
+                    const float tl = elj + yl;
+                    eljcomp = (tl - elj) - yl;
+                    elj = tl;
+                }
             }
         }
         // i-forces: sum over the 8 lanes sharing a1 (b varies: xor 1, 2, 4)
@@ -245,23 +280,13 @@ __global__ void __launch_bounds__(kForceThreads, 4) k_force(ForceParams p) {
         }
     }
 
-    // grid-wide reduction of energies (FP64) and of the pair count
-    unsigned long long c64 = cnt;
-    for (int o = 16; o > 0; o >>= 1) {
-        c64 += __shfl_xor_sync(0xffffffffu, c64, o);
-        if (ENERGY) {
-            ecd += __shfl_xor_sync(0xffffffffu, ecd, o);
-            eljd += __shfl_xor_sync(0xffffffffu, eljd, o);
-        }
-    }
-    // one atomic per warp: no block barrier, so a warp that runs out of
-    // work leaves without waiting for the rest of its block
-    if (lane == 0) {
-        atomicAdd(&p.st->npairs, c64);
-        if (ENERGY && p.energies) {
-            atomicAdd(&p.energies[0], eljd);
-            atomicAdd(&p.energies[1], ecd);
-        }
+    // pair count: one atomic per warp, no block barrier, so a warp that runs
+    // out of work leaves without waiting for the rest of its block (the
+    // energies were flushed when the loop ended)
+    if (COUNT) {
+        unsigned long long c64 = cnt;
+        for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+        if (lane == 0) atomicAdd(&p.st->npairs, c64);
     }
 }
 
@@ -275,7 +300,15 @@ __global__ void k_scatter(int n, const int *__restrict__ pos, const float4 *__re
     forces[3 * i + 2] = f.z;
 }
 
-int g_force_blocks_per_sm[2] = {0, 0};
+// kernel variants: [energy][count][threads 128/256][chunk 8/16]
+using ForceFn = void (*)(ForceParams);
+template <bool E, bool C>
+ForceFn pick(int threads, int chunk) {
+    if (threads == 128) return chunk == 8 ? k_force<E, C, 128, 8> : k_force<E, C, 128, 16>;
+    return chunk == 8 ? k_force<E, C, 256, 8> : k_force<E, C, 256, 16>;
+}
+
+int g_blocks_per_sm[2][2][2][2] = {};
 
 }  // namespace
 
@@ -294,9 +327,9 @@ cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *
     p.fsort = pl->fsort;
     p.st = pl->st;
     p.energies = energies;
-    p.Lx = pl->box[0];
-    p.Ly = pl->box[1];
-    p.Lz = pl->box[2];
+    p.sys = pl->sys;
+    p.atom_sys = pl->atom_sys;
+    p.nsys = pl->nsys;
     p.snapshot = snapshot;
     int blocks = (pl->nc_max * NB_CLUSTER + 255) / 256;
     blocks = max(1, min(blocks, pl->num_sms * 8));
@@ -317,13 +350,12 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     p.ljparams = ljparams;
     p.st = pl->st;
     p.energies = energies;
+    p.sys_shift = pl->sys_shift;
+    p.clus_sys = pl->clus_sys;
     p.ntype = ntype;
     const double rc6 = 1.0 / ((double)rc * rc * rc * rc * rc * rc);
     p.rc6inv = (float)rc6;
     p.rc12inv = (float)(rc6 * rc6);
-    p.Lx = pl->box[0];
-    p.Ly = pl->box[1];
-    p.Lz = pl->box[2];
     p.cc.rc2 = rc * rc;
     p.cc.beta = beta;
     p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
@@ -332,20 +364,25 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     p.stale_prune2 = stale_prune2;
     p.has_inner = pl->has_inner;
     const int e = energies ? 1 : 0;
-    if (g_force_blocks_per_sm[e] == 0) {
+    const int c = (pl->flags & NB_FLAG_COUNT_PAIRS) ? 1 : 0;
+    const int threads = pl->force_threads == 128 ? 128 : 256;
+    const int chunk = pl->force_chunk == 8 ? 8 : 16;
+    ForceFn fn = e ? (c ? pick<true, true>(threads, chunk) : pick<true, false>(threads, chunk))
+                   : (c ? pick<false, true>(threads, chunk) : pick<false, false>(threads, chunk));
+    const size_t smem = sizeof(float4) * (size_t)ntype * ntype;
+    int &per_sm = g_blocks_per_sm[e][c][threads == 128][chunk == 8];
+    if (per_sm == 0) {
+        // occupancy at the largest LJ table, so that the grid never exceeds residency
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &g_force_blocks_per_sm[e], e ? (const void *)k_force<true> : (const void *)k_force<false>,
-            kForceThreads, 0);
+            &per_sm, (const void *)fn, threads, sizeof(float4) * NB_MAX_TYPES * NB_MAX_TYPES);
         if (err != cudaSuccess) return err;
-        if (g_force_blocks_per_sm[e] < 1) g_force_blocks_per_sm[e] = 1;
+        if (per_sm < 1) per_sm = 1;
     }
-    int blocks = pl->num_sms * g_force_blocks_per_sm[e];
-    blocks = min(blocks, (pl->nc_max + kForceThreads / 32 - 1) / (kForceThreads / 32));
+    int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
+    int blocks = pl->num_sms * use;
+    blocks = min(blocks, (pl->nc_max + threads / 32 - 1) / (threads / 32));
     blocks = max(blocks, 1);
-    if (e)
-        k_force<true><<<blocks, kForceThreads, 0, s>>>(p);
-    else
-        k_force<false><<<blocks, kForceThreads, 0, s>>>(p);
+    fn<<<blocks, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

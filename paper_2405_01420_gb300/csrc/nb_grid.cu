@@ -15,12 +15,23 @@
 
 namespace {
 
-__global__ void k_bin(int n, const float *__restrict__ coords, float Lx, float Ly, float Lz,
-                      float inv_sx, float inv_sy, int ncx, int ncy, int *__restrict__ col_count,
-                      int *__restrict__ atom_col, int *__restrict__ atom_slot,
-                      float4 *__restrict__ xw, nb_dev_state *st) {
+// Writes the system table of a single-system pair list (one entry and its
+// 27 shift vectors) from kernel arguments, so that a search can be captured
+// in a CUDA graph without a host-to-device copy.
+__global__ void k_set_system(nb_sys *sys, float4 *sys_shift, nb_sys one) {
+    const int k = threadIdx.x;
+    if (k == 0) sys[0] = one;
+    if (k < 27)
+        sys_shift[k] = make_float4((float)nb_shift_x(k) * one.box.x, (float)nb_shift_y(k) * one.box.y,
+                                   (float)nb_shift_z(k) * one.box.z, 0.0f);
+}
+
+__global__ void k_bin(int n, const float *__restrict__ coords, const int *__restrict__ atom_sys,
+                      const nb_sys *__restrict__ sys, int *__restrict__ col_count, int *__restrict__ atom_col,
+                      int *__restrict__ atom_slot, float4 *__restrict__ xw, nb_dev_state *st) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const nb_sys S = sys[atom_sys[i]];
     float x = coords[3 * i + 0], y = coords[3 * i + 1], z = coords[3 * i + 2];
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
         atomicOr(&st->err, NB_DEV_NONFINITE);
@@ -28,10 +39,10 @@ __global__ void k_bin(int n, const float *__restrict__ coords, float Lx, float L
         y = 0.0f;
         z = 0.0f;
     }
-    float4 w = make_float4(nb_wrap(x, Lx), nb_wrap(y, Ly), nb_wrap(z, Lz), 0.0f);
-    int cx = min(ncx - 1, max(0, (int)floorf(w.x * inv_sx)));
-    int cy = min(ncy - 1, max(0, (int)floorf(w.y * inv_sy)));
-    int col = cx * ncy + cy;
+    float4 w = make_float4(nb_wrap(x, S.box.x), nb_wrap(y, S.box.y), nb_wrap(z, S.box.z), 0.0f);
+    int cx = min(S.ncx - 1, max(0, (int)floorf(w.x * S.inv_sx)));
+    int cy = min(S.ncy - 1, max(0, (int)floorf(w.y * S.inv_sy)));
+    int col = S.col_off + cx * S.ncy + cy;
     xw[i] = w;
     atom_col[i] = col;
     atom_slot[i] = atomicAdd(&col_count[col], 1);
@@ -118,9 +129,9 @@ __global__ void k_col_scatter(int n, const float4 *__restrict__ xw, const int *_
 __global__ void __launch_bounds__(256) k_col_sort(
     const int *__restrict__ col_count, const int *__restrict__ col_atom_start,
     const int *__restrict__ col_clus_start, const unsigned long long *__restrict__ keys,
-    const float4 *__restrict__ xw, int *__restrict__ perm, int *__restrict__ pos,
-    float4 *__restrict__ xref, float4 *__restrict__ xprune, float4 *__restrict__ xq,
-    int *__restrict__ tsort, float4 *__restrict__ bbox) {
+    const float4 *__restrict__ xw, const int *__restrict__ col_sys, int *__restrict__ perm,
+    int *__restrict__ pos, float4 *__restrict__ xref, float4 *__restrict__ xprune, float4 *__restrict__ xq,
+    int *__restrict__ tsort, float4 *__restrict__ bbox, int *__restrict__ clus_sys) {
     __shared__ unsigned long long sk[NB_MAX_COL_ATOMS];
     int col = blockIdx.x;
     int cnt = min(col_count[col], NB_MAX_COL_ATOMS);  // overflow already flagged by the scan
@@ -167,7 +178,9 @@ __global__ void __launch_bounds__(256) k_col_sort(
         }
     }
     // bounding boxes: one thread per cluster, real atoms only
+    const int csys = col_sys[col];
     for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
+        clus_sys[c0 + c] = csys;
         int nreal = min(NB_CLUSTER, cnt - c * NB_CLUSTER);
         float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, __int_as_float(nreal));
         float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, __int_as_float(col));
@@ -187,20 +200,22 @@ __global__ void __launch_bounds__(256) k_col_sort(
 
 }  // namespace
 
-cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, float inv_sx, float inv_sy,
-                                cudaStream_t s) {
+cudaError_t nb_launch_set_system(nb_pairlist *pl, const nb_sys &one, cudaStream_t s) {
+    k_set_system<<<1, 32, 0, s>>>(pl->sys, pl->sys_shift, one);
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream_t s) {
     int n = pl->n_atoms;
     cudaError_t e = cudaMemsetAsync(pl->col_count, 0, sizeof(int) * (size_t)pl->ncol, s);
     if (e != cudaSuccess) return e;
     int bs = 256, gb = (n + bs - 1) / bs;
-    k_bin<<<gb, bs, 0, s>>>(n, coords, pl->box[0], pl->box[1], pl->box[2], inv_sx, inv_sy, pl->ncx,
-                            pl->ncy, pl->col_count, pl->atom_col, pl->atom_slot, pl->xw, pl->st);
-    k_col_scan<<<1, 1024, 0, s>>>(pl->ncol, pl->col_count, pl->col_atom_start, pl->col_clus_start,
-                                  pl->st);
-    k_col_scatter<<<gb, bs, 0, s>>>(n, pl->xw, pl->atom_col, pl->atom_slot, pl->col_atom_start,
-                                    pl->keys);
-    k_col_sort<<<pl->ncol, 256, 0, s>>>(pl->col_count, pl->col_atom_start, pl->col_clus_start,
-                                        pl->keys, pl->xw, pl->perm, pl->pos, pl->xref, pl->xprune,
-                                        pl->xq, pl->tsort, pl->bbox);
+    k_bin<<<gb, bs, 0, s>>>(n, coords, pl->atom_sys, pl->sys, pl->col_count, pl->atom_col, pl->atom_slot, pl->xw,
+                            pl->st);
+    k_col_scan<<<1, 1024, 0, s>>>(pl->ncol, pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->st);
+    k_col_scatter<<<gb, bs, 0, s>>>(n, pl->xw, pl->atom_col, pl->atom_slot, pl->col_atom_start, pl->keys);
+    k_col_sort<<<pl->ncol, 256, 0, s>>>(pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->keys, pl->xw,
+                                        pl->col_sys, pl->perm, pl->pos, pl->xref, pl->xprune, pl->xq, pl->tsort,
+                                        pl->bbox, pl->clus_sys);
     return cudaGetLastError();
 }

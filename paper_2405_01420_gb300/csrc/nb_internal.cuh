@@ -30,6 +30,19 @@ struct nb_dev_state {
     unsigned long long npairs;     // in-range pairs counted by the last force call
 };
 
+// Per-system parameters (one entry per independent box). A single-system
+// pair list has one entry; a batch has one per system.
+struct nb_sys {
+    float4 box;        // (Lx, Ly, Lz, 0)
+    float inv_sx;      // ncx / Lx: x -> column
+    float inv_sy;      // ncy / Ly
+    int ncx, ncy;      // xy grid columns of this system
+    int col_off;       // first global column of this system
+    int atom_off;      // first atom of this system
+    int n_atoms;       // atoms of this system
+    int pad;
+};
+
 // Host handle. Device buffers are sized at creation for n_atoms.
 struct nb_pairlist {
     int device;
@@ -46,6 +59,10 @@ struct nb_pairlist {
     float rlist;
     float r_inner;
     int ncx, ncy, ncol;
+    unsigned flags;                 // nb_config.flags given at creation
+    int force_threads;              // force kernel launch shape (0 = default), see nb_set_force_shape
+    int force_chunk;
+    int force_blocks_per_sm;
     cudaEvent_t ev_start, ev_stop;  // optional timing events around the force kernel
 
     // device buffers
@@ -70,6 +87,18 @@ struct nb_pairlist {
     int *ci_start;        // [nc_max] first entry of i-cluster ci (both lists)
     int *ci_len_outer;    // [nc_max]
     int *ci_len_inner;    // [nc_max]
+    // systems (a batch of independent boxes; one entry for a single system)
+    int nsys;
+    int batch;            // created by nb_batch_create (boxes fixed at creation)
+    nb_sys *sys;          // [nsys]
+    float4 *sys_shift;    // [27 nsys] periodic shift vectors per system and shift index
+    int *atom_sys;        // [N] system of each atom
+    int *col_sys;         // [ncol_max] system of each grid column
+    int *clus_sys;        // [nc_max] system of each cluster
+    nb_sys *sys_host;     // host copy of the table [nsys]
+    float4 *gsort;        // [8 nc_max] dL/dF in cluster order (adjoint)
+    float4 *bsort;        // [8 nc_max] adjoint accumulators (dL/dx, dL/dq)
+    double *glj_acc;      // [NB_MAX_TYPES^2 * 2] adjoint LJ accumulators
 };
 
 // ---------------------------------------------------------------------------
@@ -113,8 +142,8 @@ int nb_record_error(int code, const char *msg);
 // ---------------------------------------------------------------------------
 // Launchers (return cudaError_t of the launch).
 // ---------------------------------------------------------------------------
-cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, float inv_sx, float inv_sy,
-                                cudaStream_t s);
+cudaError_t nb_launch_set_system(nb_pairlist *pl, const nb_sys &one, cudaStream_t s);
+cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream_t s);
 cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *excl_idx, float rl2,
                              float rl_col, cudaStream_t s);
 cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
@@ -124,3 +153,6 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
                             double *energies, float stale_search2, float stale_prune2,
                             cudaStream_t s);
 cudaError_t nb_launch_scatter(nb_pairlist *pl, float *forces, cudaStream_t s);
+cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
+                               const float *g, float *grad_x, float *grad_q, double *grad_lj,
+                               float stale_search2, float stale_prune2, cudaStream_t s);

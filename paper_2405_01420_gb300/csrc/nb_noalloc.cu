@@ -45,7 +45,12 @@ constexpr size_t kOffList = kOffBbox + align256(sizeof(float4) * 2 * kMaxNc);
 constexpr size_t kOffCiStart = kOffList + align256(sizeof(int4) * kCapEntries);
 constexpr size_t kOffCiLenO = kOffCiStart + align256(sizeof(int) * kMaxNc);
 constexpr size_t kOffCiLenI = kOffCiLenO + align256(sizeof(int) * kMaxNc);
-constexpr size_t kScratchBytes = kOffCiLenI + align256(sizeof(int) * kMaxNc);
+constexpr size_t kOffSys = kOffCiLenI + align256(sizeof(int) * kMaxNc);
+constexpr size_t kOffShift = kOffSys + align256(sizeof(nb_sys));
+constexpr size_t kOffAtomSys = kOffShift + align256(sizeof(float4) * 27);
+constexpr size_t kOffColSys = kOffAtomSys + align256(sizeof(int) * kMaxAtoms);
+constexpr size_t kOffClusSys = kOffColSys + align256(sizeof(int) * kMaxCols);
+constexpr size_t kScratchBytes = kOffClusSys + align256(sizeof(int) * kMaxNc);
 
 static_assert(kScratchBytes == NB_NOALLOC_SCRATCH_BYTES, "update NB_NOALLOC_SCRATCH_BYTES in nb.h");
 
@@ -125,6 +130,12 @@ extern "C" int nb_forces_noalloc(int n_atoms, const float *coords, const float *
     pl.ci_start = (int *)(base + kOffCiStart);
     pl.ci_len_outer = (int *)(base + kOffCiLenO);
     pl.ci_len_inner = (int *)(base + kOffCiLenI);
+    pl.nsys = 1;
+    pl.sys = (nb_sys *)(base + kOffSys);
+    pl.sys_shift = (float4 *)(base + kOffShift);
+    pl.atom_sys = (int *)(base + kOffAtomSys);
+    pl.col_sys = (int *)(base + kOffColSys);
+    pl.clus_sys = (int *)(base + kOffClusSys);
     for (int k = 0; k < 3; ++k) pl.box[k] = box[k];
 
     // same grid rule as nb_search
@@ -143,13 +154,24 @@ extern "C" int nb_forces_noalloc(int n_atoms, const float *coords, const float *
     // (error word, counters, cluster count) and the atom -> slot map, which
     // the permute-back reads for every atom.
     if (cudaMemsetAsync(pl.st, 0, sizeof(nb_dev_state), s) != cudaSuccess ||
-        cudaMemsetAsync(pl.pos, 0, sizeof(int) * (size_t)n_atoms, s) != cudaSuccess)
+        cudaMemsetAsync(pl.pos, 0, sizeof(int) * (size_t)n_atoms, s) != cudaSuccess ||
+        cudaMemsetAsync(pl.atom_sys, 0, sizeof(int) * (size_t)n_atoms, s) != cudaSuccess ||
+        cudaMemsetAsync(pl.col_sys, 0, sizeof(int) * (size_t)pl.ncol, s) != cudaSuccess)
         return fail(NB_ERR_CUDA, "nb_forces_noalloc: cudaMemsetAsync failed");
+    nb_sys one;
+    std::memset(&one, 0, sizeof(one));
+    one.box = make_float4(box[0], box[1], box[2], 0.0f);
+    one.inv_sx = (float)(ncx / Lx);
+    one.inv_sy = (float)(ncy / Ly);
+    one.ncx = ncx;
+    one.ncy = ncy;
+    one.n_atoms = n_atoms;
     const float lmax = std::max(box[0], std::max(box[1], box[2]));
     const double ulp = (double)std::nextafter(lmax, 2.0f * lmax) - lmax;
     const double rle = rc + std::max(1e-5, 8.0 * ulp) + 1e-6 * rc;
     const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
-    cudaError_t e = nb_launch_grid_sort(&pl, coords, (float)(ncx / Lx), (float)(ncy / Ly), s);
+    cudaError_t e = nb_launch_set_system(&pl, one, s);
+    if (e == cudaSuccess) e = nb_launch_grid_sort(&pl, coords, s);
     if (e == cudaSuccess) e = nb_launch_search(&pl, excl_off, excl_idx, rl2, (float)(rle + 1e-3), s);
     pl.searched = 1;
     pl.has_inner = 0;

@@ -65,12 +65,13 @@ __device__ __forceinline__ float nb_rcp(float x) {
 #define NB_EXP2_C5 1.338712522e-03f
 #define NB_EXP2_C6 1.533757168e-04f
 
-// 2^t for t <= 0. Results below 2^-125 are returned as about 2^-125.
+// 2^t for -125 <= t <= 0. Pairs inside the cutoff have t >= -(beta rc)^2
+// log2(e) > -15; for t below -125 the result is meaningless, which is
+// harmless because the callers select such pairs away (never multiply).
 __device__ __forceinline__ float nb_exp2(float t) {
 #if NB_EXP_MODE == 0
     return nb_ex2(t);
 #else
-    t = fmaxf(t, -125.0f);
     const float magic = 12582912.0f;          // 1.5 * 2^23: adding it rounds to an integer
     const float tn = t + magic;
     const float n = tn - magic;               // rint(t)
@@ -81,8 +82,9 @@ __device__ __forceinline__ float nb_exp2(float t) {
     p = fmaf(p, f, NB_EXP2_C2);
     p = fmaf(p, f, NB_EXP2_C1);
     p = fmaf(p, f, 1.0f);                     // 2^f in [0.70, 1.42]
-    const int ni = __float_as_int(tn) - __float_as_int(magic);
-    return __int_as_float(__float_as_int(p) + ni * (1 << 23));  // times 2^n, stays normal
+    // bits(tn) = bits(magic) + n and bits(magic) * 2^23 = 0 (mod 2^32), so
+    // adding bits(tn) * 2^23 to the bits of p multiplies p by 2^n.
+    return __int_as_float(__float_as_int(p) + __float_as_int(tn) * (1 << 23));
 #endif
 }
 

@@ -21,7 +21,8 @@ struct PruneParams {
     const int *ci_len_outer;
     int *ci_len_inner;
     nb_dev_state *st;
-    float Lx, Ly, Lz;
+    const float4 *sys_shift;  // [27 nsys]
+    const int *clus_sys;
     float r2cut;
     float stale_search2;
 };
@@ -40,17 +41,15 @@ __device__ __forceinline__ bool in_range(const float4 xi, const float4 xj, float
 
 // Tests the 64 atom pairs of one entry; returns the two new mask words.
 __device__ __forceinline__ uint2 prune_entry(const int4 e, const float4 xi1, const float4 xi2, const float4 xj,
-                                             const unsigned lanebit, const PruneParams &p) {
+                                             const unsigned lanebit, const float4 *shift, const PruneParams &p) {
     bool in1, in2;
     if (e.y == NB_SHIFT_CENTER) {
         in1 = in_range<false>(xi1, xj, 0.f, 0.f, 0.f, p.r2cut);
         in2 = in_range<false>(xi2, xj, 0.f, 0.f, 0.f, p.r2cut);
     } else {
-        const float Sx = (float)nb_shift_x(e.y) * p.Lx;
-        const float Sy = (float)nb_shift_y(e.y) * p.Ly;
-        const float Sz = (float)nb_shift_z(e.y) * p.Lz;
-        in1 = in_range<true>(xi1, xj, Sx, Sy, Sz, p.r2cut);
-        in2 = in_range<true>(xi2, xj, Sx, Sy, Sz, p.r2cut);
+        const float4 S = shift[e.y];
+        in1 = in_range<true>(xi1, xj, S.x, S.y, S.z, p.r2cut);
+        in2 = in_range<true>(xi2, xj, S.x, S.y, S.z, p.r2cut);
     }
     in1 = in1 && ((unsigned)e.z & lanebit);
     in2 = in2 && ((unsigned)e.w & lanebit);
@@ -84,6 +83,7 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= (unsigned)nc) break;
         const int ci = (int)w;
+        const float4 *shift = p.sys_shift + 27 * p.clus_sys[ci];
         const int k0 = p.ci_start[ci], n = p.ci_len_outer[ci];
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
         int out = 0;
@@ -98,14 +98,14 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
                 const int4 e0 = ent[t], e1 = ent[t + 1];
                 const float4 xj0 = p.xq[e0.x * NB_CLUSTER + b];
                 const float4 xj1 = p.xq[e1.x * NB_CLUSTER + b];
-                const uint2 m0 = prune_entry(e0, xi1, xi2, xj0, lanebit, p);
-                const uint2 m1 = prune_entry(e1, xi1, xi2, xj1, lanebit, p);
+                const uint2 m0 = prune_entry(e0, xi1, xi2, xj0, lanebit, shift, p);
+                const uint2 m1 = prune_entry(e1, xi1, xi2, xj1, lanebit, shift, p);
                 if (lane == t) mine = m0;
                 if (lane == t + 1) mine = m1;
             }
             if (t < cnt) {
                 const int4 e0 = ent[t];
-                const uint2 m0 = prune_entry(e0, xi1, xi2, p.xq[e0.x * NB_CLUSTER + b], lanebit, p);
+                const uint2 m0 = prune_entry(e0, xi1, xi2, p.xq[e0.x * NB_CLUSTER + b], lanebit, shift, p);
                 if (lane == t) mine = m0;
             }
             const bool keep = lane < cnt && (mine.x | mine.y) != 0u;
@@ -134,9 +134,8 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     p.ci_len_outer = pl->ci_len_outer;
     p.ci_len_inner = pl->ci_len_inner;
     p.st = pl->st;
-    p.Lx = pl->box[0];
-    p.Ly = pl->box[1];
-    p.Lz = pl->box[2];
+    p.sys_shift = pl->sys_shift;
+    p.clus_sys = pl->clus_sys;
     p.r2cut = r_inner2;
     p.stale_search2 = stale_search2;
     // work_prune and inner_count were reset by the snapshot gather before this launch

@@ -34,9 +34,8 @@ struct SearchParams {
     int *ci_len;
     int *ci_len_inner;
     nb_dev_state *st;
-    float Lx, Ly, Lz;
-    float inv_sx, inv_sy;
-    int ncx, ncy;
+    const nb_sys *sys;
+    const int *clus_sys;
     int n_atoms;
     float rl2;     // squared radius of the bounding-box test (already inflated)
     float rl_col;  // radius of the column / z-image pre-selection (inflated further)
@@ -61,6 +60,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
     for (int ci = blockIdx.x * kSearchWarps + warp; ci < nc; ci += gridDim.x * kSearchWarps) {
         const float4 lo = p.bbox[2 * ci], hi = p.bbox[2 * ci + 1];
         const int ni = __float_as_int(lo.w);
+        const nb_sys S = p.sys[p.clus_sys[ci]];  // every candidate column belongs to this system
 
         // exclusions of the i-atoms: (row a, slot of the excluded partner)
         if (lane == 0) s_nexcl[warp] = 0;
@@ -87,25 +87,25 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
         }
 
         int nout = 0;
-        int jx0 = max((int)floorf((lo.x - p.rl_col) * p.inv_sx), -p.ncx);
-        int jx1 = min((int)floorf((hi.x + p.rl_col) * p.inv_sx), 2 * p.ncx - 1);
-        int jy0 = max((int)floorf((lo.y - p.rl_col) * p.inv_sy), -p.ncy);
-        int jy1 = min((int)floorf((hi.y + p.rl_col) * p.inv_sy), 2 * p.ncy - 1);
+        int jx0 = max((int)floorf((lo.x - p.rl_col) * S.inv_sx), -S.ncx);
+        int jx1 = min((int)floorf((hi.x + p.rl_col) * S.inv_sx), 2 * S.ncx - 1);
+        int jy0 = max((int)floorf((lo.y - p.rl_col) * S.inv_sy), -S.ncy);
+        int jy1 = min((int)floorf((hi.y + p.rl_col) * S.inv_sy), 2 * S.ncy - 1);
         for (int jxu = jx0; jxu <= jx1; ++jxu) {
-            const int kx = image_of(jxu, p.ncx);
-            const int jx = jxu - kx * p.ncx;
-            const float ox = (float)kx * p.Lx;  // j image at x_b + ox, i.e. S_x = -ox
+            const int kx = image_of(jxu, S.ncx);
+            const int jx = jxu - kx * S.ncx;
+            const float ox = (float)kx * S.box.x;  // j image at x_b + ox, i.e. S_x = -ox
             for (int jyu = jy0; jyu <= jy1; ++jyu) {
-                const int ky = image_of(jyu, p.ncy);
-                const int jy = jyu - ky * p.ncy;
-                const float oy = (float)ky * p.Ly;
-                const int col = jx * p.ncy + jy;
+                const int ky = image_of(jyu, S.ncy);
+                const int jy = jyu - ky * S.ncy;
+                const float oy = (float)ky * S.box.y;
+                const int col = S.col_off + jx * S.ncy + jy;
                 const int c0 = p.col_clus_start[col], c1 = p.col_clus_start[col + 1];
                 if (c1 <= ci) continue;  // every cluster of this column precedes ci
                 const int cs = max(c0, ci);
                 for (int kz = -1; kz <= 1; ++kz) {
-                    const float oz = (float)kz * p.Lz;
-                    if (lo.z - p.rl_col > oz + p.Lz || hi.z + p.rl_col < oz) continue;
+                    const float oz = (float)kz * S.box.z;
+                    if (lo.z - p.rl_col > oz + S.box.z || hi.z + p.rl_col < oz) continue;
                     const int sidx = (1 - kx) * 9 + (1 - ky) * 3 + (1 - kz);
                     for (int cb = cs; cb < c1; cb += 32) {
                         const int c = cb + lane;
@@ -180,23 +180,20 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
     p.ci_len = pl->ci_len_outer;
     p.ci_len_inner = pl->ci_len_inner;
     p.st = pl->st;
-    p.Lx = pl->box[0];
-    p.Ly = pl->box[1];
-    p.Lz = pl->box[2];
-    p.inv_sx = (float)pl->ncx / pl->box[0];
-    p.inv_sy = (float)pl->ncy / pl->box[1];
-    p.ncx = pl->ncx;
-    p.ncy = pl->ncy;
+    p.sys = pl->sys;
+    p.clus_sys = pl->clus_sys;
     p.n_atoms = pl->n_atoms;
     p.rl2 = rl2;
     p.rl_col = rl_col;
     p.cap = (unsigned long long)pl->cap;
     const size_t smem = sizeof(int4) * kSearchWarps * NB_CI_ENTRY_BUF;
-    static bool attr_set = false;
-    if (!attr_set) {
+    // once per device (outside any stream capture: the first search on a
+    // device must not be captured)
+    static bool attr_done[64] = {};
+    if (pl->device < 0 || pl->device >= 64 || !attr_done[pl->device]) {
         cudaError_t e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (pl->device >= 0 && pl->device < 64) attr_done[pl->device] = true;
     }
     int blocks = (pl->nc_max + kSearchWarps - 1) / kSearchWarps;
     blocks = min(blocks, pl->num_sms * 16);

@@ -30,7 +30,7 @@ from . import nb
 class NonbondedEngine:
     def __init__(self, n_atoms: int, box, rc: float, beta: float, rlist: float,
                  r_inner: float | None = None, prune_interval: int = 10, excl_off=None, excl_idx=None,
-                 capacity_entries: int = 0, stream=None):
+                 capacity_entries: int = 0, stream=None, count_pairs: bool = False):
         self.n_atoms = int(n_atoms)
         self.box = [float(v) for v in box]
         self.rc = float(rc)
@@ -43,7 +43,7 @@ class NonbondedEngine:
         self.excl_off = excl_off
         self.excl_idx = excl_idx
         self.stream = stream
-        self.pl = nb.Pairlist(self.n_atoms, capacity_entries)
+        self.pl = nb.Pairlist(self.n_atoms, capacity_entries, count_pairs)
         self.evals = 0
         self.evals_since_search = None
         self.evals_since_prune = 0

@@ -38,6 +38,8 @@ NB_DEV_BAD_TYPE = 0x80
 NB_LIST_OUTER = 0
 NB_LIST_INNER = 1
 
+NB_FLAG_COUNT_PAIRS = 0x1
+
 
 class NBError(RuntimeError):
     """A libnb call returned a non-zero status."""
@@ -83,6 +85,7 @@ SIGNATURES = {
     "nb_last_error": (ctypes.c_char_p, []),
     "nb_pairlist_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(nb_config)]),
     "nb_pairlist_destroy": (_I, [_P]),
+    "nb_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, ctypes.POINTER(nb_config)]),
     "nb_search": (_I, [_P, _P, _P, _F, _P, _P, _P]),
     "nb_prune": (_I, [_P, _P, _F, _P]),
     "nb_forces": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P]),
@@ -91,6 +94,8 @@ SIGNATURES = {
     "nb_pairlist_export": (_I, [_P, _I, _P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P, _SZ,
                                 ctypes.POINTER(_SZ), _P]),
     "nb_set_timing_events": (_I, [_P, _P, _P]),
+    "nb_set_force_shape": (_I, [_P, _I, _I, _I]),
+    "nb_backward": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P, _P]),
     "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
                                ctypes.POINTER(ctypes.c_uint), _P]),
 }
@@ -153,10 +158,21 @@ def nb_last_error() -> str:
     return load_library().nb_last_error().decode()
 
 
-def nb_pairlist_create(n_atoms: int, capacity_entries: int = 0) -> ctypes.c_void_p:
+def nb_pairlist_create(n_atoms: int, capacity_entries: int = 0, flags: int = 0) -> ctypes.c_void_p:
     handle = ctypes.c_void_p()
-    cfg = nb_config(capacity_entries, 0)
+    cfg = nb_config(capacity_entries, flags)
     _check(load_library().nb_pairlist_create(ctypes.byref(handle), int(n_atoms), ctypes.byref(cfg)))
+    return handle
+
+
+def nb_batch_create(atom_off, boxes, capacity_entries: int = 0, flags: int = 0) -> ctypes.c_void_p:
+    """Pair list over independent systems: atom_off [B+1] and boxes [B, 3] on the host."""
+    off = np.ascontiguousarray(np.asarray(atom_off, dtype=np.int32))
+    bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float32).reshape(-1))
+    handle = ctypes.c_void_p()
+    cfg = nb_config(capacity_entries, flags)
+    _check(load_library().nb_batch_create(ctypes.byref(handle), int(off.size - 1), off.ctypes.data_as(_P),
+                                          bx.ctypes.data_as(_P), ctypes.byref(cfg)))
     return handle
 
 
@@ -167,7 +183,7 @@ def nb_pairlist_destroy(pl) -> None:
 
 def nb_search(pl, coords, box, rlist, excl_off=None, excl_idx=None, stream=None) -> None:
     n = coords.numel() // 3
-    box_h = (ctypes.c_float * 3)(*[float(v) for v in box])
+    box_h = None if box is None else (ctypes.c_float * 3)(*[float(v) for v in box])
     _check(load_library().nb_search(pl, _dev(coords, torch.float32, 3 * n, "coords"), box_h, float(rlist),
                                     _dev(excl_off, torch.int32, n + 1, "excl_off", True),
                                     _dev(excl_idx, torch.int32, None, "excl_idx", True), _stream(stream)))
@@ -178,14 +194,27 @@ def nb_prune(pl, coords, r_inner, stream=None) -> None:
                                    _stream(stream)))
 
 
-def nb_forces(pl, coords, q, type_, ljparams, rc, beta, forces, energies=None, stream=None) -> None:
+def nb_forces(pl, coords, q, type_, ljparams, rc, beta, forces, energies=None, stream=None, n_systems=1) -> None:
     n = coords.numel() // 3
     ntype = int(ljparams.shape[0])
     _check(load_library().nb_forces(pl, _dev(coords, torch.float32, 3 * n, "coords"),
                                     _dev(q, torch.float32, n, "q"), _dev(type_, torch.int32, n, "type"), ntype,
                                     _dev(ljparams, torch.float32, 2 * ntype * ntype, "ljparams"), float(rc),
                                     float(beta), _dev(forces, torch.float32, 3 * n, "forces"),
-                                    _dev(energies, torch.float64, 2, "energies", True), _stream(stream)))
+                                    _dev(energies, torch.float64, 2 * n_systems, "energies", True),
+                                    _stream(stream)))
+
+
+def nb_backward(pl, coords, q, type_, ljparams, rc, beta, g, grad_x, grad_q, grad_lj, stream=None) -> None:
+    n = coords.numel() // 3
+    ntype = int(ljparams.shape[0])
+    _check(load_library().nb_backward(pl, _dev(coords, torch.float32, 3 * n, "coords"),
+                                      _dev(q, torch.float32, n, "q"), _dev(type_, torch.int32, n, "type"), ntype,
+                                      _dev(ljparams, torch.float32, 2 * ntype * ntype, "ljparams"), float(rc),
+                                      float(beta), _dev(g, torch.float32, 3 * n, "g"),
+                                      _dev(grad_x, torch.float32, 3 * n, "grad_x"),
+                                      _dev(grad_q, torch.float32, n, "grad_q"),
+                                      _dev(grad_lj, torch.float64, 2 * ntype * ntype, "grad_lj"), _stream(stream)))
 
 
 def nb_status(pl, clear: bool = False, stream=None) -> int:
@@ -249,12 +278,25 @@ def nb_forces_noalloc(coords, box, q, type_, ljparams, rc, beta, forces, energie
     return int(word.value) if read_error_word else None
 
 
+def nb_set_force_shape(pl, threads: int = 0, chunk: int = 0, blocks_per_sm: int = 0) -> None:
+    _check(load_library().nb_set_force_shape(pl, int(threads), int(chunk), int(blocks_per_sm)))
+
+
 class Pairlist:
     """Owns one nb_pairlist handle (destroyed on close / garbage collection)."""
 
-    def __init__(self, n_atoms: int, capacity_entries: int = 0):
+    def __init__(self, n_atoms: int, capacity_entries: int = 0, count_pairs: bool = False, _handle=None,
+                 _n_systems: int = 1):
         self.n_atoms = int(n_atoms)
-        self.handle = nb_pairlist_create(self.n_atoms, capacity_entries)
+        self.n_systems = int(_n_systems)
+        self.handle = _handle if _handle is not None else nb_pairlist_create(
+            self.n_atoms, capacity_entries, NB_FLAG_COUNT_PAIRS if count_pairs else 0)
+
+    @classmethod
+    def batch(cls, atom_off, boxes, capacity_entries: int = 0, count_pairs: bool = False):
+        """A pair list over independent systems (see nb_batch_create)."""
+        h = nb_batch_create(atom_off, boxes, capacity_entries, NB_FLAG_COUNT_PAIRS if count_pairs else 0)
+        return cls(int(atom_off[-1]), _handle=h, _n_systems=len(atom_off) - 1)
 
     def search(self, coords, box, rlist, excl_off=None, excl_idx=None, stream=None):
         nb_search(self.handle, coords, box, rlist, excl_off, excl_idx, stream)
@@ -267,9 +309,18 @@ class Pairlist:
         if forces is None:
             forces = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=coords.device)
         if energies is None and want_energy:
-            energies = torch.empty(2, dtype=torch.float64, device=coords.device)
-        nb_forces(self.handle, coords, q, type_, ljparams, rc, beta, forces, energies, stream)
+            energies = torch.empty(2 * self.n_systems, dtype=torch.float64, device=coords.device)
+        nb_forces(self.handle, coords, q, type_, ljparams, rc, beta, forces, energies, stream, self.n_systems)
         return forces, energies
+
+    def backward(self, coords, q, type_, ljparams, rc, beta, g, stream=None):
+        """dL/dx [N,3], dL/dq [N], dL/dC [nt,nt,2] (FP64) for g = dL/dF."""
+        nt = int(ljparams.shape[0])
+        gx = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=coords.device)
+        gq = torch.empty(self.n_atoms, dtype=torch.float32, device=coords.device)
+        glj = torch.empty((nt, nt, 2), dtype=torch.float64, device=coords.device)
+        nb_backward(self.handle, coords, q, type_, ljparams, rc, beta, g, gx, gq, glj, stream)
+        return gx, gq, glj
 
     def status(self, clear=False, stream=None) -> int:
         return nb_status(self.handle, clear, stream)

@@ -1,0 +1,118 @@
+"""Batched form: many independent boxes in one pair list, one set of launches.
+
+Each system's forces and energies from the batch must equal the oracle's
+for that system alone (standard tolerances) and the plain single-system
+path's; the batch must replay correctly from a captured CUDA graph.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_common import E_TOL, compare_forces, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    from paper_2405_01420_gb300 import nb as nbmod
+    nbmod.load_library()
+    return nbmod
+
+
+def concat(boxes):
+    off = np.zeros(len(boxes) + 1, np.int32)
+    for k, b in enumerate(boxes):
+        off[k + 1] = off[k] + b.n_atoms
+    x = np.concatenate([b.coords for b in boxes])
+    q = np.concatenate([b.q for b in boxes])
+    t = np.concatenate([b.type for b in boxes])
+    eo = [np.zeros(1, np.int32)]
+    ei = []
+    base = 0
+    for k, b in enumerate(boxes):
+        eo.append(b.excl_off[1:] + base)
+        ei.append(b.excl_idx + off[k])
+        base += b.excl_off[-1]
+    return off, x, q, t, np.concatenate(eo), np.concatenate(ei), np.stack([b.box for b in boxes])
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def batch():
+    sizes = [1536, 3000, 903, 6003, 2400]  # atoms, rounded down to whole waters (every box edge > 2 rlist)
+    return [synth.water_box_for_atoms(n, 100 + k) for k, n in enumerate(sizes)]
+
+
+def test_batch_matches_oracle_and_plain(nb, batch):
+    rc, rlist = 0.9, 1.0
+    beta = synth.ewald_beta(rc)
+    off, x, q, t, eo, ei, boxes = concat(batch)
+    lj = dev(batch[0].ljparams)
+    pl = nb.Pairlist.batch(off, boxes, count_pairs=True)
+    pl.search(dev(x), None, rlist, dev(eo), dev(ei))
+    F, E = pl.forces(dev(x), dev(q), dev(t), lj, rc, beta)
+    assert pl.status() == 0
+    F = F.cpu().numpy()
+    E = E.cpu().numpy().reshape(-1, 2)
+    total_pairs = 0
+    for k, b in enumerate(batch):
+        Fo, elj, ec, n = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                              b.excl_idx)
+        compare_forces(F[off[k]:off[k + 1]], Fo)
+        assert rel(E[k, 0], elj) <= E_TOL and rel(E[k, 1], ec) <= E_TOL, k
+        total_pairs += oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx, count_only=True)
+        # the plain path on this system alone
+        p1 = nb.Pairlist(b.n_atoms)
+        p1.search(dev(b.coords), b.box, rlist, dev(b.excl_off), dev(b.excl_idx))
+        F1, E1 = p1.forces(dev(b.coords), dev(b.q), dev(b.type), lj, rc, beta)
+        np.testing.assert_allclose(F[off[k]:off[k + 1]], F1.cpu().numpy(), rtol=0,
+                                   atol=1e-5 * np.abs(Fo).max())
+        assert rel(E[k, 0], E1[0].item()) <= 1e-7 and rel(E[k, 1], E1[1].item()) <= 1e-7
+        p1.close()
+    assert pl.stats()["pairs_last"] == total_pairs
+    # prune on top of the batch list
+    pl.prune(dev(x), rc + 0.02)
+    F2, E2 = pl.forces(dev(x), dev(q), dev(t), lj, rc, beta)
+    assert pl.status() == 0
+    np.testing.assert_allclose(F2.cpu().numpy(), F, rtol=0, atol=1e-5 * np.abs(F).max())
+    pl.close()
+
+
+def test_batch_graph_replay(nb, batch):
+    """search + forces of the whole batch captured in one CUDA graph and replayed."""
+    rc, rlist = 0.9, 1.0
+    beta = synth.ewald_beta(rc)
+    off, x, q, t, eo, ei, boxes = concat(batch)
+    xd, qd, td, eod, eid = dev(x), dev(q), dev(t), dev(eo), dev(ei)
+    lj = dev(batch[0].ljparams)
+    pl = nb.Pairlist.batch(off, boxes)
+    F = torch.empty((pl.n_atoms, 3), dtype=torch.float32, device="cuda")
+    E = torch.empty(2 * pl.n_systems, dtype=torch.float64, device="cuda")
+    # eager once (also runs every one-time set-up outside the capture)
+    pl.search(xd, None, rlist, eod, eid)
+    pl.forces(xd, qd, td, lj, rc, beta, F, E)
+    torch.cuda.synchronize()
+    F_eager, E_eager = F.clone(), E.clone()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            pl.search(xd, None, rlist, eod, eid, stream=s)
+            pl.forces(xd, qd, td, lj, rc, beta, F, E, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        F.zero_()
+        E.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        torch.testing.assert_close(F, F_eager, rtol=0, atol=1e-5 * F_eager.abs().max().item())
+        torch.testing.assert_close(E, E_eager, rtol=1e-9, atol=0)
+    assert pl.status() == 0
+    pl.close()

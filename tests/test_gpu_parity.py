@@ -38,7 +38,7 @@ def test_small_box_search_and_forces(nb):
     rc = 0.9
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, rc, d["excl_off"], d["excl_idx"])
     F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
     torch.cuda.synchronize()
@@ -61,7 +61,7 @@ def test_list_covers_rlist(nb):
     b = synth.water_box(4000, 7)
     rlist = 1.1
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, rlist, d["excl_off"], d["excl_idx"])
     exp = pl.export(nb.NB_LIST_OUTER)
     assert pl.status() == 0
@@ -84,7 +84,7 @@ def test_prune_and_displaced_frames(nb):
     beta = synth.ewald_beta(rc)
     frames = synth.random_walk_frames(b, 14, 0.001, seed=31)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     x0 = frames[0]
     pl.search(torch.from_numpy(x0).cuda(), b.box, rlist, d["excl_off"], d["excl_idx"])
     for f in range(14):
@@ -113,10 +113,11 @@ def test_force_only_path_matches(nb):
     rc = 1.0
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms)  # no pair counting: the kernels without the counter
     pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
     pl.prune(d["coords"], 1.04)
     F1, _ = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta, want_energy=False)
+    assert pl.stats()["pairs_last"] == -1
     F2, E2 = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
     Fo, elj, ec, _ = oracle_ref(b, rc, beta)
     compare_forces(F1.cpu().numpy(), Fo)
@@ -135,7 +136,7 @@ def test_four_types_random_charges(nb):
     rc = 1.0
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
     pl.prune(d["coords"], 1.04)
     F, E = pl.forces(d["coords"], torch.from_numpy(q).cuda(), torch.from_numpy(p["type"]).cuda(),
@@ -150,7 +151,7 @@ def test_four_types_random_charges(nb):
 def test_repeated_search_is_deterministic(nb):
     b = synth.water_box(1000, 12)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, 1.0, d["excl_off"], d["excl_idx"])
     e1 = pl.export(nb.NB_LIST_OUTER)
     pl.search(d["coords"], b.box, 1.0, d["excl_off"], d["excl_idx"])
@@ -168,7 +169,7 @@ def test_production_box_96k(nb):
     rc = 1.0
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
     pl.prune(d["coords"], 1.04)
     F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
@@ -189,7 +190,7 @@ def test_million_atom_box_sampled(nb):
     rc = 1.0
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
     pl.prune(d["coords"], 1.04)
     F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
@@ -213,7 +214,7 @@ def test_single_water(nb):
     b = synth.water_box(1, 1)
     box = np.array([3.0, 3.0, 3.0], np.float32)
     d = to_dev(b)
-    pl = nb.Pairlist(3)
+    pl = nb.Pairlist(3, count_pairs=True)
     pl.search(d["coords"], box, 0.9, d["excl_off"], d["excl_idx"])
     F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], 0.9, synth.ewald_beta(0.9))
     assert pl.status() == 0
@@ -233,7 +234,7 @@ def test_ragged_small_systems(nb, nw):
     rc = 0.9
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], box, rc, d["excl_off"], d["excl_idx"])
     F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
     assert pl.status() == 0
@@ -266,7 +267,7 @@ def test_unwrapped_and_edge_coordinates(nb):
     d = to_dev(b)
     for x in (x_unwrapped, x_edge):
         xd = torch.from_numpy(x).cuda()
-        pl = nb.Pairlist(b.n_atoms)
+        pl = nb.Pairlist(b.n_atoms, count_pairs=True)
         pl.search(xd, b.box, rc, d["excl_off"], d["excl_idx"])
         F, E = pl.forces(xd, d["q"], d["type"], d["lj"], rc, beta)
         assert pl.status() == 0
@@ -283,7 +284,7 @@ def test_zero_charges(nb):
     beta = synth.ewald_beta(rc)
     d = to_dev(b)
     q0 = torch.zeros_like(d["q"])
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     pl.search(d["coords"], b.box, rc, d["excl_off"], d["excl_idx"])
     F, E = pl.forces(d["coords"], q0, d["type"], d["lj"], rc, beta)
     Fo, elj, ec, _ = oracle.energy_forces(b.coords, np.zeros(b.n_atoms), b.type, b.ljparams, b.box, rc, beta,
@@ -299,7 +300,7 @@ def test_zero_charges(nb):
 def test_host_argument_errors(nb):
     b = synth.water_box(64, 1)
     d = to_dev(b)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     F = torch.empty((b.n_atoms, 3), device="cuda")
     with pytest.raises(nb.NBError) as e:
         pl.forces(d["coords"], d["q"], d["type"], d["lj"], 0.5, 3.0, F)
@@ -330,7 +331,7 @@ def test_device_error_bits(nb):
     assert small.status() & nb.NB_DEV_LIST_OVERFLOW
     small.close()
 
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
     bad_t = d["type"].clone()
     bad_t[5] = 7
     pl.search(d["coords"], b.box, rc, d["excl_off"], d["excl_idx"])
