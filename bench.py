@@ -344,18 +344,26 @@ def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
     assert counter.status() == 0
     counter.close()
 
+    from paper_2405_01420_gb300.tune import tune_batch_prune, tune_force_shape
     pl = nb.Pairlist.batch(off, bx)
     F = torch.empty((pl.n_atoms, 3), dtype=torch.float32, device=dev)
     E = torch.empty(2 * pl.n_systems, dtype=torch.float64, device=dev)
     pl.search(xd, None, rlist, eod, eid)
     pl.forces(xd, qd, td, lj, rc, beta, F, E)
     torch.cuda.synchronize()
+    # autotune (untimed): force launch shape, then whether to prune to rc before the forces
+    shape, _ = tune_force_shape(pl, lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
+    use_prune, prune_times = tune_batch_prune(lambda: pl.search(xd, None, rlist, eod, eid),
+                                              lambda: pl.prune(xd, rc),
+                                              lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     with torch.cuda.stream(side):
         with torch.cuda.graph(g, stream=side):
             pl.search(xd, None, rlist, eod, eid, stream=side)
+            if use_prune:
+                pl.prune(xd, rc, stream=side)
             pl.forces(xd, qd, td, lj, rc, beta, F, E, stream=side)
     stream.wait_stream(side)
     torch.cuda.synchronize()
@@ -412,7 +420,9 @@ def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
             "pairs_per_batch": pairs,
             "graph_p50_ms": g50, "graph_p99_ms": g99, "graph_pairs_per_s": pairs / (g50 / 1e3),
             "plain_launches_p50_ms": p50, "plain_launches_p99_ms": p99, "plain_pairs_per_s": pairs / (p50 / 1e3),
-            "speedup_p50": p50 / g50, "graph_reps": reps, "plain_reps": plain_reps}
+            "speedup_p50": p50 / g50, "graph_reps": reps, "plain_reps": plain_reps,
+            "tuned": {"force_shape": list(shape), "prune_before_forces": bool(use_prune),
+                      "prune_choice_ms": prune_times}}
 
 
 def run_ours(args, rank, world, local):
@@ -467,6 +477,13 @@ def run_ours(args, rank, world, local):
     assert counter.check() == 0, "device error word set in the counting pass"
     counter.close()
     pairs_per_step = float(sum(pairs))
+
+    # autotune the force kernel's launch shape on this workload (untimed)
+    from paper_2405_01420_gb300.tune import tune_force_shape
+    restart()
+    eng.compute(frames_d[0], q, typ, lj, forces, energies[0])
+    shape, shape_times = tune_force_shape(
+        eng.pl, lambda: nb.nb_forces(eng.pl.handle, frames_d[0], q, typ, lj, RC, beta, forces, energies[0]))
 
     for _ in range(args.warmup):
         one_step(lambda i: frames_d[i])
@@ -573,6 +590,7 @@ def run_ours(args, rank, world, local):
         "us_per_eval": 1e3 * ms_step / args.evals,
         "pairs_per_eval": pairs_per_eval,
         "searches_per_step": searches, "prunes_per_step": prunes,
+        "force_shape": {"threads": shape[0], "chunk": shape[1], "blocks_per_sm": shape[2], "tuned_ms": shape_times},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

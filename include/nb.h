@@ -82,6 +82,10 @@ typedef struct {
 /* nb_config.flags: count the in-range pairs in nb_forces (nb_stats.pairs_last);
    costs about one instruction per pair, so it is off unless asked for. */
 #define NB_FLAG_COUNT_PAIRS 0x1u
+/* nb_config.flags: do not sort i-clusters by list length after each search
+   and prune (§III-A: the post-pruning list sorting that shortens the tail
+   of the force kernel; on by default). */
+#define NB_FLAG_NO_LIST_SORT 0x2u
 
 /* Host-side snapshot of a pair list (filled by nb_pairlist_stats). */
 typedef struct {

@@ -53,7 +53,8 @@ void free_buffers(nb_pairlist *pl) {
                     pl->xref,   pl->xprune,    pl->xq,             pl->tsort,          pl->fsort,
                     pl->bbox,   pl->outer,     pl->inner,          pl->ci_start,       pl->ci_len_outer,
                     pl->ci_len_inner, pl->gsort,   pl->bsort,          pl->glj_acc,        pl->sys,
-                    pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys};
+                    pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys,       pl->len_hist,
+                    pl->len_offsets, pl->len_cursor, pl->ci_order};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -106,7 +107,7 @@ nb_sys make_sys(const float *box, int ncx, int ncy, int col_off, int atom_off, i
 
 // Allocates every device buffer of a pair list over n atoms in nsys systems.
 int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const char *who) {
-    if (cfg && (cfg->flags & ~(unsigned)NB_FLAG_COUNT_PAIRS) != 0u)
+    if (cfg && (cfg->flags & ~(unsigned)(NB_FLAG_COUNT_PAIRS | NB_FLAG_NO_LIST_SORT)) != 0u)
         return fail(NB_ERR_ARG, "%s: unknown flags 0x%x", who, cfg->flags);
     NB_CUDA(cudaGetDevice(&pl->device));
     NB_CUDA(cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device));
@@ -131,7 +132,9 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
                 alloc(&pl->gsort, nslot, &total) && alloc(&pl->bsort, nslot, &total) &&
                 alloc(&pl->glj_acc, 2 * NB_MAX_TYPES * NB_MAX_TYPES, &total) && alloc(&pl->sys, pl->nsys, &total) &&
                 alloc(&pl->sys_shift, 27 * (size_t)pl->nsys, &total) && alloc(&pl->atom_sys, n, &total) &&
-                alloc(&pl->col_sys, pl->ncol_max, &total) && alloc(&pl->clus_sys, pl->nc_max, &total);
+                alloc(&pl->col_sys, pl->ncol_max, &total) && alloc(&pl->clus_sys, pl->nc_max, &total) &&
+                alloc(&pl->len_hist, NB_LEN_BINS, &total) && alloc(&pl->len_offsets, NB_LEN_BINS, &total) &&
+                alloc(&pl->len_cursor, NB_LEN_BINS, &total) && alloc(&pl->ci_order, pl->nc_max, &total);
     if (!good) {
         cudaGetLastError();  // clear the allocation error
         return fail(NB_ERR_NOMEM, "%s: cudaMalloc of %zu bytes failed", who, total);
@@ -301,6 +304,11 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
     const float rl_col = (float)(rle + 1e-3);
     NB_CUDA(nb_launch_search(pl, excl_off, excl_idx, rl2, rl_col, s));
+    pl->sorted = 0;
+    if (!(pl->flags & NB_FLAG_NO_LIST_SORT)) {
+        NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_outer, s));
+        pl->sorted = 1;
+    }
     pl->searched = 1;
     pl->has_inner = 0;
     pl->rlist = rlist;
@@ -318,6 +326,11 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
     NB_CUDA(nb_launch_gather(pl, coords, nullptr, nullptr, 1, 1, nullptr, s));
     const float r2cut = r_inner * r_inner;
     NB_CUDA(nb_launch_prune(pl, r2cut, stale_bound2(pl->rlist, r_inner), s));
+    pl->sorted = 0;
+    if (!(pl->flags & NB_FLAG_NO_LIST_SORT)) {
+        NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_inner, s));
+        pl->sorted = 1;
+    }
     pl->has_inner = 1;
     pl->r_inner = r_inner;
     return ok();

@@ -37,6 +37,7 @@ struct BwdParams {
     const int4 *list;
     const int *ci_start;
     const int *ci_len;
+    const int *order;  // i-clusters by decreasing list length, or NULL
     const float *ljparams;
     nb_dev_state *st;
     const float4 *sys_shift;  // [27 nsys]
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdParams p) {
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= (unsigned)nc) break;
-        const int ci = (int)w;
+        const int ci = p.order ? p.order[w] : (int)w;
         const float4 *shift = p.sys_shift + 27 * p.clus_sys[ci];
         const int k0 = p.ci_start[ci], k1 = k0 + p.ci_len[ci];
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
@@ -314,6 +315,7 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
     p.list = pl->has_inner ? pl->inner : pl->outer;
     p.ci_start = pl->ci_start;
     p.ci_len = pl->has_inner ? pl->ci_len_inner : pl->ci_len_outer;
+    p.order = pl->sorted ? pl->ci_order : nullptr;
     p.ljparams = ljparams;
     p.st = pl->st;
     p.sys_shift = pl->sys_shift;

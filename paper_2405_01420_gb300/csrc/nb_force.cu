@@ -113,6 +113,7 @@ struct ForceParams {
     const int4 *list;
     const int *ci_start;
     const int *ci_len;
+    const int *order;         // i-clusters by decreasing list length, or NULL
     const float *ljparams;
     nb_dev_state *st;
     double *energies;         // [2 nsys]
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        const int ci = (int)w;
+        const int ci = (w < (unsigned)nc && p.order) ? p.order[w] : (int)w;
         const int csys = (w < (unsigned)nc) ? p.clus_sys[ci] : -1;
         if (ENERGY && csys != cur_sys) {
             if (cur_sys >= 0) flush_energies(ecd, eljd, lane, p.energies + 2 * cur_sys);
@@ -347,6 +348,7 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     p.list = pl->has_inner ? pl->inner : pl->outer;
     p.ci_start = pl->ci_start;
     p.ci_len = pl->has_inner ? pl->ci_len_inner : pl->ci_len_outer;
+    p.order = pl->sorted ? pl->ci_order : nullptr;
     p.ljparams = ljparams;
     p.st = pl->st;
     p.energies = energies;

@@ -13,6 +13,7 @@
 #define NB_CI_ENTRY_BUF 512     // list entries one i-cluster may own
 #define NB_CI_EXCL_BUF 256      // exclusions within one i-cluster
 #define NB_SHIFT_CENTER 13      // shift index of S = (0, 0, 0)
+#define NB_LEN_BINS 512         // list-length histogram bins (lengths >= 511 share the last)
 #define NB_COULOMB_F 138.935458f
 
 // Device-side state of one pair list (one allocation, zeroed at creation).
@@ -96,6 +97,11 @@ struct nb_pairlist {
     int *col_sys;         // [ncol_max] system of each grid column
     int *clus_sys;        // [nc_max] system of each cluster
     nb_sys *sys_host;     // host copy of the table [nsys]
+    int *len_hist;        // [NB_LEN_BINS] list-length histogram (post-prune sorting)
+    int *len_offsets;     // [NB_LEN_BINS]
+    int *len_cursor;      // [NB_LEN_BINS]
+    int *ci_order;        // [nc_max] i-clusters by decreasing list length
+    int sorted;           // ci_order matches the list the forces will use
     float4 *gsort;        // [8 nc_max] dL/dF in cluster order (adjoint)
     float4 *bsort;        // [8 nc_max] adjoint accumulators (dL/dx, dL/dq)
     double *glj_acc;      // [NB_MAX_TYPES^2 * 2] adjoint LJ accumulators
@@ -149,6 +155,7 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
 cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
                              int ntype, int snapshot, double *energies, cudaStream_t s);
 cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2, cudaStream_t s);
+cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, cudaStream_t s);
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
                             double *energies, float stale_search2, float stale_prune2,
                             cudaStream_t s);

@@ -1,0 +1,60 @@
+// Post-prune list sorting (§III-A: the HIP fork's "post-pruning list
+// sorting strategy" that cuts the tail of the NBNXM and prune kernels, with
+// the prune computing a "list size histogram").
+//
+// The force kernel hands out i-clusters from a work counter; taking them in
+// order of decreasing list length lets the longest lists start first, so the
+// persistent grid ends with short items and a short tail.
+//
+// k_len_hist     histogram of the per-i-cluster list lengths
+// k_len_offsets  exclusive scan of the histogram from the longest length down
+// k_len_scatter  ci -> order[offset(len) + rank within its length]
+#include "nb_internal.cuh"
+
+namespace {
+
+__global__ void k_len_hist(const int *__restrict__ ci_len, const nb_dev_state *st, int *__restrict__ hist) {
+    const int nc = st->nc;
+    for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < nc; ci += gridDim.x * blockDim.x)
+        atomicAdd(&hist[min(ci_len[ci], NB_LEN_BINS - 1)], 1);
+}
+
+// One CTA of NB_LEN_BINS threads: offsets[len] = number of clusters with a
+// longer list.
+__global__ void __launch_bounds__(NB_LEN_BINS) k_len_offsets(const int *__restrict__ hist, int *__restrict__ offsets,
+                                                           int *__restrict__ cursor) {
+    __shared__ int s[NB_LEN_BINS];
+    const int t = threadIdx.x;
+    s[t] = hist[NB_LEN_BINS - 1 - t];  // reversed: longest first
+    __syncthreads();
+    for (int o = 1; o < NB_LEN_BINS; o <<= 1) {
+        const int v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    const int len = NB_LEN_BINS - 1 - t;
+    offsets[len] = s[t] - hist[len];  // exclusive
+    cursor[len] = 0;
+}
+
+__global__ void k_len_scatter(const int *__restrict__ ci_len, const nb_dev_state *st, const int *__restrict__ offsets,
+                              int *__restrict__ cursor, int *__restrict__ order) {
+    const int nc = st->nc;
+    for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < nc; ci += gridDim.x * blockDim.x) {
+        const int len = min(ci_len[ci], NB_LEN_BINS - 1);
+        order[offsets[len] + atomicAdd(&cursor[len], 1)] = ci;
+    }
+}
+
+}  // namespace
+
+cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(pl->len_hist, 0, sizeof(int) * NB_LEN_BINS, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = max(1, min((pl->nc_max + 255) / 256, pl->num_sms * 4));
+    k_len_hist<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_hist);
+    k_len_offsets<<<1, NB_LEN_BINS, 0, s>>>(pl->len_hist, pl->len_offsets, pl->len_cursor);
+    k_len_scatter<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_offsets, pl->len_cursor, pl->ci_order);
+    return cudaGetLastError();
+}

@@ -39,6 +39,7 @@ NB_LIST_OUTER = 0
 NB_LIST_INNER = 1
 
 NB_FLAG_COUNT_PAIRS = 0x1
+NB_FLAG_NO_LIST_SORT = 0x2
 
 
 class NBError(RuntimeError):
@@ -285,17 +286,21 @@ def nb_set_force_shape(pl, threads: int = 0, chunk: int = 0, blocks_per_sm: int 
 class Pairlist:
     """Owns one nb_pairlist handle (destroyed on close / garbage collection)."""
 
-    def __init__(self, n_atoms: int, capacity_entries: int = 0, count_pairs: bool = False, _handle=None,
-                 _n_systems: int = 1):
+    def __init__(self, n_atoms: int, capacity_entries: int = 0, count_pairs: bool = False, sort_lists: bool = True,
+                 _handle=None, _n_systems: int = 1):
         self.n_atoms = int(n_atoms)
         self.n_systems = int(_n_systems)
         self.handle = _handle if _handle is not None else nb_pairlist_create(
-            self.n_atoms, capacity_entries, NB_FLAG_COUNT_PAIRS if count_pairs else 0)
+            self.n_atoms, capacity_entries, self._flags(count_pairs, sort_lists))
+
+    @staticmethod
+    def _flags(count_pairs: bool, sort_lists: bool) -> int:
+        return (NB_FLAG_COUNT_PAIRS if count_pairs else 0) | (0 if sort_lists else NB_FLAG_NO_LIST_SORT)
 
     @classmethod
-    def batch(cls, atom_off, boxes, capacity_entries: int = 0, count_pairs: bool = False):
+    def batch(cls, atom_off, boxes, capacity_entries: int = 0, count_pairs: bool = False, sort_lists: bool = True):
         """A pair list over independent systems (see nb_batch_create)."""
-        h = nb_batch_create(atom_off, boxes, capacity_entries, NB_FLAG_COUNT_PAIRS if count_pairs else 0)
+        h = nb_batch_create(atom_off, boxes, capacity_entries, cls._flags(count_pairs, sort_lists))
         return cls(int(atom_off[-1]), _handle=h, _n_systems=len(atom_off) - 1)
 
     def search(self, coords, box, rlist, excl_off=None, excl_idx=None, stream=None):

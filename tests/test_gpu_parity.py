@@ -362,3 +362,24 @@ def test_device_error_bits(nb):
     assert pl2.status() == 0
     pl2.close()
     pl.close()
+
+
+def test_list_sorting_does_not_change_results(nb):
+    """Post-prune sorting by list length only reorders work: same forces and energies."""
+    b = synth.water_box(4000, 13)
+    rc = 1.0
+    beta = synth.ewald_beta(rc)
+    d = to_dev(b)
+    out = []
+    for sort in (True, False):
+        pl = nb.Pairlist(b.n_atoms, count_pairs=True, sort_lists=sort)
+        pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
+        pl.prune(d["coords"], 1.04)
+        F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
+        assert pl.status() == 0
+        out.append((F.cpu().numpy(), E.cpu().numpy(), pl.stats()["pairs_last"]))
+        pl.close()
+    (F1, E1, n1), (F2, E2, n2) = out
+    assert n1 == n2
+    np.testing.assert_allclose(F1, F2, rtol=0, atol=1e-5 * np.abs(F2).max())
+    assert rel(E1[0], E2[0]) <= 1e-7 and rel(E1[1], E2[1]) <= 1e-7
