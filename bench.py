@@ -228,7 +228,7 @@ def load_traffic():
         return None
     rec = json.load(open(path))
     h = hashlib.sha256()
-    for f in ("nb_force.cu", "nb_pair.cuh"):
+    for f in ("nb_force_vt.cu", "nb_pair.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2405_01420_gb300", "csrc", f), "rb").read())
     if rec.get("source_sha256") != h.hexdigest():
         return None
@@ -575,7 +575,7 @@ def run_ours(args, rank, world, local):
     achieved = FLOPS_PER_PAIR * pairs_per_eval / (kern_ms_per_launch / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
             "traffic": load_traffic(),
-            "kernel": "k_force (LJ + Ewald real-space, energies on)",
+            "kernel": "k_force_vt (gathered 4x8 tiles after the prune; LJ + Ewald real-space, energies on)",
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x 2070 MHz (max SM clock)",
             "kernel_us_per_launch": 1e3 * kern_ms_per_launch}
     if clocks and clocks.get("sm_mhz"):

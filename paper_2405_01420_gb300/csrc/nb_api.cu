@@ -54,7 +54,8 @@ void free_buffers(nb_pairlist *pl) {
                     pl->bbox,   pl->outer,     pl->inner,          pl->ci_start,       pl->ci_len_outer,
                     pl->ci_len_inner, pl->gsort,   pl->bsort,          pl->glj_acc,        pl->sys,
                     pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys,       pl->len_hist,
-                    pl->len_offsets, pl->len_cursor, pl->ci_order};
+                    pl->len_offsets, pl->len_cursor, pl->ci_order,     pl->vt_slot,        pl->vt_mask,
+                    pl->half_start, pl->half_len};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -107,7 +108,7 @@ nb_sys make_sys(const float *box, int ncx, int ncy, int col_off, int atom_off, i
 
 // Allocates every device buffer of a pair list over n atoms in nsys systems.
 int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const char *who) {
-    if (cfg && (cfg->flags & ~(unsigned)(NB_FLAG_COUNT_PAIRS | NB_FLAG_NO_LIST_SORT)) != 0u)
+    if (cfg && (cfg->flags & ~(unsigned)(NB_FLAG_COUNT_PAIRS | NB_FLAG_NO_LIST_SORT | NB_FLAG_CLUSTER_TILES)) != 0u)
         return fail(NB_ERR_ARG, "%s: unknown flags 0x%x", who, cfg->flags);
     NB_CUDA(cudaGetDevice(&pl->device));
     NB_CUDA(cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device));
@@ -117,7 +118,9 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
     if (cap >= (size_t)1 << 31) return fail(NB_ERR_ARG, "%s: capacity_entries %zu >= 2^31", who, cap);
     pl->cap = cap;
     pl->flags = cfg ? cfg->flags : 0u;
-    const size_t nslot = (size_t)pl->nc_max * NB_CLUSTER;
+    // one extra cluster of slots past the last cluster: slot 8 nc_max pads
+    // the last gathered tile of a half and never holds an atom
+    const size_t nslot = (size_t)pl->nc_max * NB_CLUSTER + NB_CLUSTER;
     size_t total = 0;
     bool good = alloc(&pl->st, 1, &total) && alloc(&pl->col_count, pl->ncol_max, &total) &&
                 alloc(&pl->col_atom_start, pl->ncol_max + 1, &total) &&
@@ -134,7 +137,13 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
                 alloc(&pl->sys_shift, 27 * (size_t)pl->nsys, &total) && alloc(&pl->atom_sys, n, &total) &&
                 alloc(&pl->col_sys, pl->ncol_max, &total) && alloc(&pl->clus_sys, pl->nc_max, &total) &&
                 alloc(&pl->len_hist, NB_LEN_BINS, &total) && alloc(&pl->len_offsets, NB_LEN_BINS, &total) &&
-                alloc(&pl->len_cursor, NB_LEN_BINS, &total) && alloc(&pl->ci_order, pl->nc_max, &total);
+                alloc(&pl->len_cursor, NB_LEN_BINS, &total) && alloc(&pl->ci_order, pl->nc_max, &total) &&
+                alloc(&pl->half_start, 2 * (size_t)pl->nc_max, &total) &&
+                alloc(&pl->half_len, 2 * (size_t)pl->nc_max, &total);
+    // gathered tiles pack a slot in 27 bits and index tiles with 32-bit ints;
+    // beyond that the force kernel stays on the cluster-pair tiles
+    if (good && nslot < ((size_t)1 << 27) && 2 * cap < ((size_t)1 << 31))
+        good = alloc(&pl->vt_slot, 16 * cap, &total) && alloc(&pl->vt_mask, 2 * cap, &total);
     if (!good) {
         cudaGetLastError();  // clear the allocation error
         return fail(NB_ERR_NOMEM, "%s: cudaMalloc of %zu bytes failed", who, total);
@@ -152,6 +161,9 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
     NB_CUDA(cudaMemset(pl->atom_sys, 0, sizeof(int) * (size_t)n));
     NB_CUDA(cudaMemset(pl->col_sys, 0, sizeof(int) * (size_t)pl->ncol_max));
     NB_CUDA(cudaMemset(pl->clus_sys, 0, sizeof(int) * (size_t)pl->nc_max));
+    NB_CUDA(cudaMemset(pl->tsort, 0, sizeof(int) * nslot));
+    const float4 far = make_float4(NB_PAD_COORD, NB_PAD_COORD, NB_PAD_COORD, 0.0f);
+    NB_CUDA(cudaMemcpy(pl->xq + (size_t)pl->nc_max * NB_CLUSTER, &far, sizeof(float4), cudaMemcpyHostToDevice));
     return NB_OK;
 }
 
@@ -311,6 +323,7 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     }
     pl->searched = 1;
     pl->has_inner = 0;
+    pl->has_vtiles = 0;
     pl->rlist = rlist;
     pl->r_inner = 0.0f;
     return ok();
@@ -332,6 +345,7 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
         pl->sorted = 1;
     }
     pl->has_inner = 1;
+    pl->has_vtiles = pl->vt_slot != nullptr;
     pl->r_inner = r_inner;
     return ok();
 }
@@ -352,8 +366,11 @@ extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, c
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, energies, s));
     if (pl->ev_start) NB_CUDA(cudaEventRecord(pl->ev_start, s));
-    NB_CUDA(nb_launch_force(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->rlist, rc),
-                            stale_bound2(pl->r_inner, rc), s));
+    if (pl->has_vtiles && !(pl->flags & NB_FLAG_CLUSTER_TILES))
+        NB_CUDA(nb_launch_force_vt(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->r_inner, rc), s));
+    else
+        NB_CUDA(nb_launch_force(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->rlist, rc),
+                                stale_bound2(pl->r_inner, rc), s));
     if (pl->ev_stop) NB_CUDA(cudaEventRecord(pl->ev_stop, s));
     NB_CUDA(nb_launch_scatter(pl, forces, s));
     return ok();
@@ -484,5 +501,38 @@ extern "C" int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int b
     pl->force_threads = threads;
     pl->force_chunk = chunk;
     pl->force_blocks_per_sm = blocks_per_sm;
+    return ok();
+}
+
+extern "C" int nb_pairlist_export_tiles(nb_pairlist *pl, int *half_id, int *slots, unsigned *masks, size_t cap,
+                                        size_t *n_out, void *stream) {
+    if (!pl || !n_out) return fail(NB_ERR_ARG, "nb_pairlist_export_tiles: NULL argument");
+    if (cap > 0 && (!half_id || !slots || !masks)) return fail(NB_ERR_ARG, "nb_pairlist_export_tiles: NULL arrays");
+    if (!pl->has_vtiles) return fail(NB_ERR_STATE, "nb_pairlist_export_tiles: no prune since the search");
+    DeviceGuard g(pl->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    nb_dev_state st;
+    NB_CUDA(cudaMemcpyAsync(&st, pl->st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    const int nh = 2 * st.nc;
+    std::vector<int> start(nh), len(nh);
+    NB_CUDA(cudaMemcpyAsync(start.data(), pl->half_start, sizeof(int) * nh, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(len.data(), pl->half_len, sizeof(int) * nh, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    size_t k = 0;
+    for (int hh = 0; hh < nh; ++hh) {
+        const size_t m = (size_t)len[hh];
+        if (m > 0 && k + m <= cap) {  // one copy per half: its tiles are contiguous
+            NB_CUDA(cudaMemcpyAsync(slots + 8 * k, pl->vt_slot + 8 * (size_t)start[hh], sizeof(int) * 8 * m,
+                                    cudaMemcpyDeviceToHost, s));
+            NB_CUDA(cudaMemcpyAsync(masks + k, pl->vt_mask + start[hh], sizeof(unsigned) * m,
+                                    cudaMemcpyDeviceToHost, s));
+            for (size_t t = 0; t < m; ++t) half_id[k + t] = hh;
+        }
+        k += m;
+    }
+    NB_CUDA(cudaStreamSynchronize(s));
+    *n_out = k;
+    if (k > cap) return fail(NB_ERR_CAPACITY, "nb_pairlist_export_tiles: %zu tiles > cap %zu", k, cap);
     return ok();
 }

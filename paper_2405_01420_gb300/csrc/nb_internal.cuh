@@ -102,6 +102,11 @@ struct nb_pairlist {
     int *len_cursor;      // [NB_LEN_BINS]
     int *ci_order;        // [nc_max] i-clusters by decreasing list length
     int sorted;           // ci_order matches the list the forces will use
+    int *vt_slot;         // [2 cap * 8] gathered tiles: j slot | shift << 27
+    unsigned *vt_mask;    // [2 cap] 4 x 8 in-range bits per gathered tile
+    int *half_start;      // [2 nc_max] first gathered tile of each half i-cluster
+    int *half_len;        // [2 nc_max]
+    int has_vtiles;       // the last prune built gathered tiles
     float4 *gsort;        // [8 nc_max] dL/dF in cluster order (adjoint)
     float4 *bsort;        // [8 nc_max] adjoint accumulators (dL/dx, dL/dq)
     double *glj_acc;      // [NB_MAX_TYPES^2 * 2] adjoint LJ accumulators
@@ -156,6 +161,8 @@ cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *
                              int ntype, int snapshot, double *energies, cudaStream_t s);
 cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2, cudaStream_t s);
 cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, cudaStream_t s);
+cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
+                               double *energies, float stale_prune2, cudaStream_t s);
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
                             double *energies, float stale_search2, float stale_prune2,
                             cudaStream_t s);

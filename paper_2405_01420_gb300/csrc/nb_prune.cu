@@ -23,9 +23,34 @@ struct PruneParams {
     nb_dev_state *st;
     const float4 *sys_shift;  // [27 nsys]
     const int *clus_sys;
+    int *vt_slot;        // [2 cap * 8] gathered j slots (shift index in the top 5 bits)
+    unsigned *vt_mask;   // [2 cap] 4 x 8 in-range bits (bit a*8 + p)
+    int *half_start;     // [2 nc_max]
+    int *half_len;       // [2 nc_max]
+    int pad_slot;        // a slot that never holds an atom (far away, q = 0)
     float r2cut;
     float stale_search2;
 };
+
+constexpr int kStage = 512;  // ring of staged j atoms per warp and half (>= 32 * 8 + 8)
+
+// Rows (a = 0..3) of column b of a 4 x 8 mask (bit a*8 + b) as 4 bits.
+__device__ __forceinline__ unsigned column_rows(unsigned m, int b) {
+    return ((m >> b) & 1u) | ((m >> (7 + b)) & 2u) | ((m >> (14 + b)) & 4u) | ((m >> (21 + b)) & 8u);
+}
+
+// Writes one gathered tile from the 8 staged atoms at ring position head.
+__device__ __forceinline__ void flush_tile(const int *ring_slot, const unsigned char *ring_rows, int head, int vt,
+                                           int lane, const PruneParams &p) {
+    const int idx = (head + (lane & 7)) & (kStage - 1);
+    const int v = ring_slot[idx];
+    const unsigned r = lane < 8 ? ring_rows[idx] : 0u;
+    if (lane < 8) p.vt_slot[8 * (size_t)vt + lane] = v;
+    unsigned m = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m |= (__ballot_sync(0xffffffffu, (r >> a) & 1u) & 0xffu) << (8 * a);
+    if (lane == 0) p.vt_mask[vt] = m;
+}
 
 template <bool SHIFT>
 __device__ __forceinline__ bool in_range(const float4 xi, const float4 xj, float Sx, float Sy, float Sz,
@@ -61,8 +86,11 @@ __device__ __forceinline__ uint2 prune_entry(const int4 e, const float4 xi1, con
 // iteration (independent loads for latency hiding); lane t keeps the new
 // masks of entry t, and the kept entries are written back compacted and
 // coalesced.
+template <bool TILES>
 __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
     __shared__ int4 s_ent[kPruneThreads / 32][32];
+    __shared__ int s_rslot[kPruneThreads / 32][2][kStage];
+    __shared__ unsigned char s_rrows[kPruneThreads / 32][2][kStage];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // displacement since the search must leave the outer list complete at r_inner
         const unsigned ds = p.st->cur_d2_search;
@@ -85,8 +113,10 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         const int ci = (int)w;
         const float4 *shift = p.sys_shift + 27 * p.clus_sys[ci];
         const int k0 = p.ci_start[ci], n = p.ci_len_outer[ci];
+        // tiles of half h go to [2 k0 + h n, 2 k0 + (h + 1) n): each entry adds at most 8 atoms
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
         int out = 0;
+        int head[2] = {0, 0}, fill[2] = {0, 0}, ntile[2] = {0, 0};
         for (int base = 0; base < n; base += 32) {
             const int cnt = min(32, n - base);
             __syncwarp();
@@ -110,12 +140,61 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
             }
             const bool keep = lane < cnt && (mine.x | mine.y) != 0u;
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int4 e = ent[lane];
+            const int4 e = ent[lane];
+            if (keep)
                 p.inner[k0 + out + __popc(bal & (lanebit - 1u))] = make_int4(e.x, e.y, (int)mine.x, (int)mine.y);
-            }
             out += __popc(bal);
+            // Gather, per half, the j atoms in range of any of its 4 rows.
+#pragma unroll
+            for (int h = 0; h < (TILES ? 2 : 0); ++h) {
+                const unsigned m = lane < cnt ? (h ? mine.y : mine.x) : 0u;
+                unsigned col = (m | (m >> 8) | (m >> 16) | (m >> 24)) & 0xffu;
+                const int c = __popc(col);
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                int pos = head[h] + fill[h] + incl - c;
+                while (col) {
+                    const int bb = __ffs(col) - 1;
+                    col &= col - 1u;
+                    const int idx = pos & (kStage - 1);
+                    s_rslot[warp][h][idx] = (int)((unsigned)(e.x * NB_CLUSTER + bb) | ((unsigned)e.y << 27));
+                    s_rrows[warp][h][idx] = (unsigned char)column_rows(m, bb);
+                    ++pos;
+                }
+                fill[h] += total;
+                __syncwarp();
+                while (fill[h] >= 8) {
+                    flush_tile(s_rslot[warp][h], s_rrows[warp][h], head[h], 2 * k0 + h * n + ntile[h], lane, p);
+                    head[h] += 8;
+                    fill[h] -= 8;
+                    ++ntile[h];
+                }
+                __syncwarp();
+            }
         }
+        // last partial tile of each half, padded with a slot that holds no atom
+#pragma unroll
+        for (int h = 0; h < (TILES ? 2 : 0); ++h) {
+            if (fill[h] > 0) {
+                if (lane >= fill[h] && lane < 8) {
+                    const int idx = (head[h] + lane) & (kStage - 1);
+                    s_rslot[warp][h][idx] = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+                    s_rrows[warp][h][idx] = 0;
+                }
+                __syncwarp();
+                flush_tile(s_rslot[warp][h], s_rrows[warp][h], head[h], 2 * k0 + h * n + ntile[h], lane, p);
+                ++ntile[h];
+            }
+            if (lane == 0) {
+                p.half_start[2 * ci + h] = 2 * k0 + h * n;
+                p.half_len[2 * ci + h] = ntile[h];
+            }
+        }
+        __syncwarp();
         if (lane == 0) {
             p.ci_len_inner[ci] = out;
             atomicAdd(&p.st->inner_count, (unsigned long long)out);
@@ -136,11 +215,19 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     p.st = pl->st;
     p.sys_shift = pl->sys_shift;
     p.clus_sys = pl->clus_sys;
+    p.vt_slot = pl->vt_slot;
+    p.vt_mask = pl->vt_mask;
+    p.half_start = pl->half_start;
+    p.half_len = pl->half_len;
+    p.pad_slot = pl->nc_max * NB_CLUSTER;
     p.r2cut = r_inner2;
     p.stale_search2 = stale_search2;
     // work_prune and inner_count were reset by the snapshot gather before this launch
     int blocks = pl->num_sms * 4;
     blocks = min(blocks, (pl->nc_max + kPruneThreads / 32 - 1) / (kPruneThreads / 32));
-    k_prune<<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
+    if (p.vt_slot)
+        k_prune<true><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
+    else
+        k_prune<false><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -40,6 +40,7 @@ NB_LIST_INNER = 1
 
 NB_FLAG_COUNT_PAIRS = 0x1
 NB_FLAG_NO_LIST_SORT = 0x2
+NB_FLAG_CLUSTER_TILES = 0x4
 
 
 class NBError(RuntimeError):
@@ -96,6 +97,7 @@ SIGNATURES = {
                                 ctypes.POINTER(_SZ), _P]),
     "nb_set_timing_events": (_I, [_P, _P, _P]),
     "nb_set_force_shape": (_I, [_P, _I, _I, _I]),
+    "nb_pairlist_export_tiles": (_I, [_P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P]),
     "nb_backward": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P, _P]),
     "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
                                ctypes.POINTER(ctypes.c_uint), _P]),
@@ -279,6 +281,20 @@ def nb_forces_noalloc(coords, box, q, type_, ljparams, rc, beta, forces, energie
     return int(word.value) if read_error_word else None
 
 
+def nb_pairlist_export_tiles(pl, stream=None) -> dict:
+    """Gathered 4x8 tiles of the last prune: half_id [T], slots [T, 8] (slot | shift << 27), masks [T]."""
+    st = nb_pairlist_stats(pl, stream)
+    cap = 2 * int(st["outer_entries"]) + 1
+    hid = np.empty(cap, np.int32)
+    slots = np.empty((cap, 8), np.int32)
+    masks = np.empty(cap, np.uint32)
+    n = ctypes.c_size_t(0)
+    _check(load_library().nb_pairlist_export_tiles(pl, hid.ctypes.data_as(_P), slots.ctypes.data_as(_P),
+                                                   masks.ctypes.data_as(_P), cap, ctypes.byref(n), _stream(stream)))
+    k = n.value
+    return {"half_id": hid[:k], "slots": slots[:k], "masks": masks[:k]}
+
+
 def nb_set_force_shape(pl, threads: int = 0, chunk: int = 0, blocks_per_sm: int = 0) -> None:
     _check(load_library().nb_set_force_shape(pl, int(threads), int(chunk), int(blocks_per_sm)))
 
@@ -287,15 +303,16 @@ class Pairlist:
     """Owns one nb_pairlist handle (destroyed on close / garbage collection)."""
 
     def __init__(self, n_atoms: int, capacity_entries: int = 0, count_pairs: bool = False, sort_lists: bool = True,
-                 _handle=None, _n_systems: int = 1):
+                 cluster_tiles: bool = False, _handle=None, _n_systems: int = 1):
         self.n_atoms = int(n_atoms)
         self.n_systems = int(_n_systems)
         self.handle = _handle if _handle is not None else nb_pairlist_create(
-            self.n_atoms, capacity_entries, self._flags(count_pairs, sort_lists))
+            self.n_atoms, capacity_entries, self._flags(count_pairs, sort_lists, cluster_tiles))
 
     @staticmethod
-    def _flags(count_pairs: bool, sort_lists: bool) -> int:
-        return (NB_FLAG_COUNT_PAIRS if count_pairs else 0) | (0 if sort_lists else NB_FLAG_NO_LIST_SORT)
+    def _flags(count_pairs: bool, sort_lists: bool, cluster_tiles: bool = False) -> int:
+        return ((NB_FLAG_COUNT_PAIRS if count_pairs else 0) | (0 if sort_lists else NB_FLAG_NO_LIST_SORT)
+                | (NB_FLAG_CLUSTER_TILES if cluster_tiles else 0))
 
     @classmethod
     def batch(cls, atom_off, boxes, capacity_entries: int = 0, count_pairs: bool = False, sort_lists: bool = True):
@@ -335,6 +352,9 @@ class Pairlist:
 
     def export(self, which=NB_LIST_OUTER, stream=None) -> dict:
         return nb_pairlist_export(self.handle, which, stream)
+
+    def export_tiles(self, stream=None) -> dict:
+        return nb_pairlist_export_tiles(self.handle, stream)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

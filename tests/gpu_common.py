@@ -50,6 +50,39 @@ def expand_counted_pairs(exp, y, box, r_cut):
     return np.stack([i, j], axis=1).astype(np.int64)
 
 
+def expand_tile_pairs(tiles, perm, y, box, r_cut):
+    """Atom pairs of the gathered 4 x 8 tiles whose mask bit is set and whose
+    FP32 contract distance is below r_cut (int64 [P, 2], i < j, duplicates kept).
+
+    Tile k covers rows 4h..4h+3 of i-cluster ci (half_id = 2 ci + h) and the
+    8 j atoms slots[k] (cluster slot in the low 27 bits, shift index above).
+    """
+    hid, slots, masks = tiles["half_id"], tiles["slots"], tiles["masks"]
+    if hid.size == 0:
+        return np.zeros((0, 2), np.int64)
+    bits = ((masks[:, None].astype(np.uint64) >> np.arange(32, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(bool)
+    t_idx, bit = np.nonzero(bits)
+    a = bit // 8
+    col = bit % 8
+    v = slots[t_idx, col].view(np.uint32)
+    jslot = (v & np.uint32(0x07FFFFFF)).astype(np.int64)
+    s = (v >> np.uint32(27)).astype(np.int64)
+    assert (jslot < perm.size).all(), "mask bit set on the pad slot"
+    islot = (hid[t_idx] // 2).astype(np.int64) * 8 + 4 * (hid[t_idx] % 2) + a
+    p = perm[islot]
+    q = perm[jslot]
+    assert (p >= 0).all() and (q >= 0).all(), "mask bit set on a padding slot"
+    assert (s < 27).all()
+    S = np.stack([(s // 9 - 1), ((s // 3) % 3 - 1), (s % 3 - 1)], axis=1).astype(np.float32) * box.astype(np.float32)
+    d = (y[p] - y[q]).astype(np.float32)
+    d = (d + S).astype(np.float32)
+    r2 = r2_contract(d[:, 0], d[:, 1], d[:, 2])
+    keep = r2 < np.float32(r_cut) * np.float32(r_cut)
+    i = np.minimum(p[keep], q[keep])
+    j = np.maximum(p[keep], q[keep])
+    return np.stack([i, j], axis=1).astype(np.int64)
+
+
 def pair_set(arr):
     return set(map(tuple, np.asarray(arr).tolist()))
 

@@ -10,7 +10,8 @@ import torch
 
 import oracle
 import synth
-from gpu_common import (E_TOL, compare_forces, expand_counted_pairs, oracle_ref, pair_set, rel, to_dev)
+from gpu_common import (E_TOL, compare_forces, expand_counted_pairs, expand_tile_pairs, oracle_ref, pair_set, rel,
+                        to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -106,6 +107,64 @@ def test_prune_and_displaced_frames(nb):
             compare_forces(F.cpu().numpy(), Fo)
             check_energies(E, elj, ec)
     pl.close()
+
+
+@pytest.mark.parametrize("nw,seed", [(4000, 3), (391, 8)])
+def test_gathered_tiles_cover_r_inner(nb, nw, seed):
+    """The gathered 4 x 8 tiles of a prune hold every pair within r_inner once
+    (bit for bit against the FP32 pair set), and no mask bit on a pad slot."""
+    b = synth.water_box(nw, seed)
+    rlist, r_in = 1.1, 1.04
+    frames = synth.random_walk_frames(b, 2, 0.002, seed=seed + 40)
+    d = to_dev(b)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
+    pl.search(torch.from_numpy(frames[0]).cuda(), b.box, rlist, d["excl_off"], d["excl_idx"])
+    pl.prune(torch.from_numpy(frames[1]).cuda(), r_in)
+    torch.cuda.synchronize()
+    assert pl.status() == 0
+    tiles = pl.export_tiles()
+    exp = pl.export(nb.NB_LIST_INNER)
+    y = oracle.image_f32(frames[0], frames[1], b.box)
+    got = expand_tile_pairs(tiles, exp["perm"], y, b.box, r_in)
+    ref = oracle.pairs_f32(frames[0], frames[1], b.box, r_in, b.excl_off, b.excl_idx)
+    assert len(pair_set(got)) == len(got), "an atom pair is in two tiles"
+    assert pair_set(got) == pair_set(ref)
+    # every set bit is within r_inner (nothing beyond the prune radius kept)
+    assert len(expand_tile_pairs(tiles, exp["perm"], y, b.box, 1e3)) == len(got)
+    # each half's tiles are dense: all but its last tile have 8 occupied columns
+    hid = tiles["half_id"]
+    last = np.r_[hid[1:] != hid[:-1], True]
+    cols = np.zeros(hid.size, np.int64)
+    for p_ in range(8):
+        cols += ((tiles["masks"] >> np.uint32(p_)) & np.uint32(0x01010101)) != 0
+    assert (cols[~last] == 8).all()
+    pl.close()
+
+
+@pytest.mark.parametrize("want_energy", [True, False])
+def test_cluster_tiles_and_gathered_tiles_agree(nb, want_energy):
+    """After a prune both force kernels (8 x 8 cluster tiles / gathered 4 x 8
+    tiles) meet the oracle bar and count the same pairs."""
+    b = synth.water_box(3000, 12)
+    rc = 1.0
+    beta = synth.ewald_beta(rc)
+    d = to_dev(b)
+    out = []
+    for cluster_tiles in (False, True):
+        pl = nb.Pairlist(b.n_atoms, count_pairs=True, cluster_tiles=cluster_tiles)
+        pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
+        pl.prune(d["coords"], 1.04)
+        F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta, want_energy=want_energy)
+        torch.cuda.synchronize()
+        assert pl.status() == 0
+        out.append((F.cpu().numpy(), None if E is None else E.cpu().numpy(), pl.stats()["pairs_last"]))
+        pl.close()
+    Fo, elj, ec, npairs = oracle_ref(b, rc, beta)
+    for F, E, np_ in out:
+        compare_forces(F, Fo)
+        assert np_ == npairs
+        if want_energy:
+            assert rel(E[0], elj) <= E_TOL and rel(E[1], ec) <= E_TOL
 
 
 def test_force_only_path_matches(nb):
