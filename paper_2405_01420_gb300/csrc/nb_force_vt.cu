@@ -35,6 +35,7 @@ struct VtParams {
     float rc6inv, rc12inv;
     nb_coul cc;
     float stale_prune2;
+    int pad_slot;             // never holds an atom: far away, q = 0, type 0
 };
 
 __device__ __forceinline__ void flush_energies_vt(double ec, double elj, int lane, double *out) {
@@ -48,15 +49,76 @@ __device__ __forceinline__ void flush_energies_vt(double ec, double elj, int lan
     }
 }
 
-template <bool ENERGY, bool COUNT, int THREADS, int CHUNK>
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Sums v[0..15] over the 32 lanes of the warp, reduce-scatter style: on
+// return lanes 2k and 2k + 1 hold the total of value k in v[0].
+__device__ __forceinline__ void reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+    for (int n = 16, o = 16; n > 1; n >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float send = upper ? v[i] : v[i + n / 2];
+            const float keep = upper ? v[i + n / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Per-lane staging of one group of 32 gathered j atoms (4 tiles of 8).
+struct VtStage {
+    float4 xj[32];
+    float4 S[32];
+    int tj[32];
+    unsigned m[32];
+};
+
+// Issues the copies of group g of the half with tiles [t0, t1) into st
+// (one j atom per lane); returns the lane's slot word. Lanes past the end
+// take the pad slot (never occupied, q = 0) with an empty mask.
+__device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, const float4 *shift, int t0, int t1, int g,
+                                           int lane) {
+    const int tile = t0 + 4 * g + (lane >> 3);
+    int v = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+    if (tile < t1) {
+        v = p.vt_slot[8 * (size_t)tile + (lane & 7)];
+        cp_async4(&st.m[lane], p.vt_mask + tile);
+    } else {
+        st.m[lane] = 0u;
+    }
+    const int slot = v & 0x07ffffff;
+    cp_async16(&st.xj[lane], p.xq + slot);
+    cp_async4(&st.tj[lane], p.tsort + slot);
+    cp_async16(&st.S[lane], shift + ((unsigned)v >> 27));
+    return v;
+}
+
+// j-stationary kernel over gathered tiles. A warp takes one half i-cluster
+// (4 i rows) at a time; its tiles are read in groups of 4 (32 j atoms, one
+// per lane), and each lane computes its j atom against the 4 rows. j forces
+// stay in registers for the 4 pairs and go out with 3 atomics per lane;
+// i forces stay in registers for the whole half and are reduced across the
+// warp at its end. Group g + 1 is copied (cp.async) into the other buffer
+// while group g is computed.
+template <bool ENERGY, bool COUNT, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p) {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ float4 s_lj[];
-    __shared__ unsigned s_mask[kWarps][CHUNK];
-    __shared__ float4 s_xj[kWarps][CHUNK * 8];
-    __shared__ float4 s_S[kWarps][CHUNK * 8];
-    __shared__ int s_tj[kWarps][CHUNK * 8];
-    __shared__ int s_slot[kWarps][CHUNK * 8];
+    __shared__ VtStage s_st[kWarps][2];
+    __shared__ float4 s_xi[kWarps][4];
+    __shared__ int s_tr[kWarps][4];
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -73,10 +135,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int pcol = lane & 7, a = lane >> 3;
-    const unsigned lanebit = 1u << lane;
-    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-    const int comp = (hi16 ? 2 : 0) + (hi8 ? 1 : 0);
     const unsigned nwork = 2u * (unsigned)p.st->nc;
     double ecd = 0.0, eljd = 0.0;
     int cur_sys = -1;
@@ -96,68 +154,67 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p
             cur_sys = csys;
         }
         if (w >= nwork) break;
-        const float4 *shift = p.sys_shift + 27 * csys;
-        const int islot = ci * NB_CLUSTER + 4 * h + a;
-        const float4 xi = p.xq[islot];
-        const float qi = xi.w * NB_COULOMB_F;
-        const int tr = p.tsort[islot] * p.ntype;
         const int t0 = p.half_start[2 * ci + h], t1 = t0 + p.half_len[2 * ci + h];
-        float3 fi = make_float3(0.f, 0.f, 0.f);
-        float ec = 0.0f, ecomp = 0.0f, elj = 0.0f, eljcomp = 0.0f;
-        for (int base = t0; base < t1; base += CHUNK) {
-            const int nch = min(CHUNK, t1 - base);
-            __syncwarp();
-            if (lane < nch) s_mask[warp][lane] = p.vt_mask[base + lane];
-            for (int idx = lane; idx < nch * 8; idx += 32) {
-                const int v = p.vt_slot[8 * (size_t)base + idx];
-                const int slot = v & 0x07ffffff;
-                s_slot[warp][idx] = slot;
-                s_xj[warp][idx] = p.xq[slot];
-                s_tj[warp][idx] = p.tsort[slot];
-                s_S[warp][idx] = shift[(unsigned)v >> 27];
-            }
-            __syncwarp();
-            for (int t = 0; t < nch; ++t) {
-                const unsigned m = s_mask[warp][t];
-                const int jdx = t * 8 + pcol;
-                const float4 xj = s_xj[warp][jdx];
-                const float4 S = s_S[warp][jdx];
-                const int tj = s_tj[warp][jdx];
-                float3 fj = make_float3(0.f, 0.f, 0.f);
-                float ect = 0.0f, eljt = 0.0f;
-                const int c1 = nb_pair<true, ENERGY>(xi, qi, xj, s_lj[tr + tj], S.x, S.y, S.z, (m & lanebit) != 0u,
-                                                     p.cc, fi, fj, ect, eljt);
+        if (t1 <= t0) continue;
+        const float4 *shift = p.sys_shift + 27 * csys;
+        const int ibase = ci * NB_CLUSTER + 4 * h;
+        int v = stage_group(p, s_st[warp][0], shift, t0, t1, 0, lane);
+        if (lane < 4) {
+            const float4 x = p.xq[ibase + lane];
+            s_xi[warp][lane] = make_float4(x.x, x.y, x.z, x.w * NB_COULOMB_F);
+            s_tr[warp][lane] = p.tsort[ibase + lane] * p.ntype;
+        }
+        float3 fi[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fi[a] = make_float3(0.f, 0.f, 0.f);
+        float ec = 0.0f, elj = 0.0f;
+        const int ngroups = (t1 - t0 + 3) >> 2;
+        cp_async_wait_all();
+        __syncwarp();
+        for (int g = 0; g < ngroups; ++g) {
+            VtStage &cs = s_st[warp][g & 1];
+            const float4 xj = cs.xj[lane];
+            const float4 S = cs.S[lane];
+            const int tj = cs.tj[lane];
+            const unsigned mrow = cs.m[lane] >> (lane & 7);
+            const int slot = v & 0x07ffffff;
+            float3 fj = make_float3(0.f, 0.f, 0.f);
+            int vn = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
+                    vn = stage_group(p, s_st[warp][(g + 1) & 1], shift, t0, t1, g + 1, lane);
+                const float4 xi = s_xi[warp][a];
+                const int c1 = nb_pair<true, ENERGY>(xi, xi.w, xj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
+                                                     ((mrow >> (8 * a)) & 1u) != 0u, p.cc, fi[a], fj, ec, elj);
                 if (COUNT) cnt += c1;
-                float ka = hi16 ? fj.z : fj.x, sa = hi16 ? fj.x : fj.z;
-                float kb = hi16 ? 0.0f : fj.y, sb = hi16 ? fj.y : 0.0f;
-                ka += __shfl_xor_sync(0xffffffffu, sa, 16);
-                kb += __shfl_xor_sync(0xffffffffu, sb, 16);
-                float kk = hi8 ? kb : ka, ss = hi8 ? ka : kb;
-                kk += __shfl_xor_sync(0xffffffffu, ss, 8);
-                if (comp < 3) atomicAdd(p.fsort + 4 * s_slot[warp][jdx] + comp, kk);
-                if (ENERGY) {
-                    const float y = ect - ecomp;
-                    const float tt = ec + y;
-                    ecomp = (tt - ec) - y;
-                    ec = tt;
-                    const float yl = eljt - eljcomp;
-                    const float tl = elj + yl;
-                    eljcomp = (tl - elj) - yl;
-                    elj = tl;
-                }
             }
+            if (slot != p.pad_slot) {  // all padding lanes share one slot: no atomics there
+                atomicAdd(p.fsort + 4 * slot + 0, fj.x);
+                atomicAdd(p.fsort + 4 * slot + 1, fj.y);
+                atomicAdd(p.fsort + 4 * slot + 2, fj.z);
+            }
+            v = vn;
+            cp_async_wait_all();
+            __syncwarp();
         }
-        // i forces: sum over the 8 lanes of a row, lane p < 3 adds component p
-        for (int o = 1; o < 8; o <<= 1) {
-            fi.x += __shfl_xor_sync(0xffffffffu, fi.x, o);
-            fi.y += __shfl_xor_sync(0xffffffffu, fi.y, o);
-            fi.z += __shfl_xor_sync(0xffffffffu, fi.z, o);
+        // i forces: row a component c is value 4a + c; lanes 2k hold value k
+        float r[16];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            r[4 * a + 0] = fi[a].x;
+            r[4 * a + 1] = fi[a].y;
+            r[4 * a + 2] = fi[a].z;
+            r[4 * a + 3] = 0.0f;
         }
-        if (pcol < 3) atomicAdd(p.fsort + 4 * islot + pcol, pcol == 0 ? fi.x : (pcol == 1 ? fi.y : fi.z));
+        reduce_scatter16(r, lane);
+        const int k = lane >> 1;
+        if ((lane & 1) == 0 && (k & 3) != 3) atomicAdd(p.fsort + 4 * (ibase + (k >> 2)) + (k & 3), r[0]);
         if (ENERGY) {
-            ecd += (double)ec - (double)ecomp;
-            eljd += (double)elj - (double)eljcomp;
+            ecd += (double)ec;
+            eljd += (double)elj;
         }
+        __syncwarp();
     }
     if (COUNT) {
         unsigned long long c64 = cnt;
@@ -168,12 +225,15 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p
 
 using VtFn = void (*)(VtParams);
 template <bool E, bool C>
-VtFn pick_vt(int threads, int chunk) {
-    if (threads == 128) return chunk == 8 ? k_force_vt<E, C, 128, 8> : k_force_vt<E, C, 128, 16>;
-    return chunk == 8 ? k_force_vt<E, C, 256, 8> : k_force_vt<E, C, 256, 16>;
+VtFn pick_vt(int threads) {
+    return threads == 128 ? k_force_vt<E, C, 128> : k_force_vt<E, C, 256>;
 }
 
-int g_vt_blocks_per_sm[2][2][2][2] = {};
+struct Occ {
+    size_t smem;
+    int per_sm;
+};
+Occ g_vt_occ[2][2][2] = {};
 
 }  // namespace
 
@@ -202,20 +262,22 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
     p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
     p.stale_prune2 = stale_prune2;
+    p.pad_slot = pl->nc_max * NB_CLUSTER;
     const int e = energies ? 1 : 0;
     const int c = (pl->flags & NB_FLAG_COUNT_PAIRS) ? 1 : 0;
     const int threads = pl->force_threads == 128 ? 128 : 256;
-    const int chunk = pl->force_chunk == 8 ? 8 : 16;
-    VtFn fn = e ? (c ? pick_vt<true, true>(threads, chunk) : pick_vt<true, false>(threads, chunk))
-                : (c ? pick_vt<false, true>(threads, chunk) : pick_vt<false, false>(threads, chunk));
+    VtFn fn = e ? (c ? pick_vt<true, true>(threads) : pick_vt<true, false>(threads))
+                : (c ? pick_vt<false, true>(threads) : pick_vt<false, false>(threads));
     const size_t smem = sizeof(float4) * (size_t)ntype * ntype;
-    int &per_sm = g_vt_blocks_per_sm[e][c][threads == 128][chunk == 8];
-    if (per_sm == 0) {
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)fn, threads, sizeof(float4) * NB_MAX_TYPES * NB_MAX_TYPES);
+    Occ &occ = g_vt_occ[e][c][threads == 128];
+    if (occ.per_sm == 0 || occ.smem != smem) {  // resident CTAs for this LJ table size
+        int n = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)fn, threads, smem);
         if (err != cudaSuccess) return err;
-        if (per_sm < 1) per_sm = 1;
+        occ.smem = smem;
+        occ.per_sm = n < 1 ? 1 : n;
     }
+    const int per_sm = occ.per_sm;
     const int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
     int blocks = pl->num_sms * use;
     blocks = min(blocks, (2 * pl->nc_max + threads / 32 - 1) / (threads / 32));
