@@ -45,7 +45,11 @@ RC, RLIST, R_INNER = 1.0, 1.1, 1.04
 PRUNE_INTERVAL = 10
 SIGMA = 0.001
 # FP32 operations per in-range pair in the force + energy formula as the
-# kernel evaluates it (FMA = 2): see DESIGN.md, "Roofline".
+# kernel evaluates it (FMA = 2): d 3, r^2 5, rsqrt 1, 1/r^2 and 1/r^6 3, C6/r^6 and
+# C12/r^12 3, LJ force scalar 4, r 1, beta r 1, exp 2, erfcx P/Q 18,
+# erfc/r 2, f qi qj 1, force scalar 5, the 6 force FMAs 12, energies 5. The
+# Newton steps of rsqrt and rcp and the exp polynomial's range reduction are
+# not counted (they refine, they add no work to the formula).
 FLOPS_PER_PAIR = 66
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
@@ -161,6 +165,12 @@ def dist_sum(x: float, world: int) -> float:
     return float(t.item())
 
 
+def replica_throughput(units_local: float, seconds_local: float, world: int) -> float:
+    """Whole-job throughput of independent replicas: the units of all ranks
+    divided by the slowest rank's time (max over ranks)."""
+    return dist_sum(units_local, world) / dist_max(seconds_local, world)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -211,7 +221,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_desc(1),
+        "config": dict(workload_desc(args.evals), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -296,6 +306,87 @@ def bench_backward(dev, reps: int = 30):
                         "rlist 1.1 / r_inner 1.04 nm; forces+energies vs forces+energies then nb_backward "
                         "(dL/dx, dL/dq, dL/dC); median of 30 calls, inputs resident",
             "us_forward": 1e3 * t_f, "us_forward_backward": 1e3 * t_fb, "ratio_to_plain": t_fb / t_f}
+
+
+def bench_million(dev, n_evals: int = 50, with_oracle: bool = True):
+    """1,000,002 atoms (333,334 waters): 1 search + 50 evaluations with the rolling prune.
+
+    Times each force kernel with events (inputs resident; the 50 frames of a
+    sigma = 0.001 nm walk are in HBM), counts the in-range pairs of every
+    evaluation on a separate counting list, and times one FP64 oracle
+    evaluation of the first frame on the host cores.
+    """
+    import torch
+    from paper_2405_01420_gb300 import nb
+    from paper_2405_01420_gb300.engine import NonbondedEngine
+    box = synth.water_box(333334, 3)
+    frames = synth.random_walk_frames(box, n_evals, SIGMA, seed=3)
+    N = box.n_atoms
+    beta = synth.ewald_beta(RC)
+    frames_d = torch.from_numpy(frames).to(dev)
+    q = torch.from_numpy(box.q).to(dev)
+    typ = torch.from_numpy(box.type).to(dev)
+    lj = torch.from_numpy(box.ljparams).to(dev)
+    eo = torch.from_numpy(box.excl_off).to(dev)
+    ei = torch.from_numpy(box.excl_idx).to(dev)
+    forces = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    energies = torch.zeros((n_evals, 2), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    counter = NonbondedEngine(N, box.box, RC, beta, RLIST, R_INNER, PRUNE_INTERVAL, eo, ei, count_pairs=True)
+    pairs = []
+    for i in range(n_evals):
+        counter.compute(frames_d[i], q, typ, lj, forces, energies[i])
+        pairs.append(counter.pl.stats()["pairs_last"])
+    assert counter.check() == 0
+    counter.close()
+
+    eng = NonbondedEngine(N, box.box, RC, beta, RLIST, R_INNER, PRUNE_INTERVAL, eo, ei)
+    for i in range(3):  # warm-up
+        eng.compute(frames_d[i], q, typ, lj, forces, energies[i])
+    eng.evals_since_search = None
+    eng.n_search = eng.n_prune = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_evals)]
+    for a, b in ev:
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(n_evals):
+        nb.nb_set_timing_events(eng.pl.handle, *ev[i])
+        eng.compute(frames_d[i], q, typ, lj, forces, energies[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    nb.nb_set_timing_events(eng.pl.handle, None, None)
+    assert eng.check() == 0
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    n_search, n_prune = eng.n_search, eng.n_prune
+    eng.close()
+    total_pairs = float(sum(pairs))
+    kern_mean = statistics.mean(kern_ms)
+    out = {"workload": "1,000,002-atom water box (333,334 waters, L=21.53 nm), rc 1.0 / rlist 1.1 / r_inner 1.04 nm, "
+                       f"1 search + {n_evals} force+energy evals with the rolling prune, sigma=0.001 nm walk, "
+                       "frames resident",
+           "pairs_per_eval": total_pairs / n_evals,
+           "pairs_per_s": total_pairs / (total_ms / 1e3),
+           "us_per_eval": 1e3 * total_ms / n_evals,
+           "kernel_us_per_launch": 1e3 * kern_mean,
+           "kernel_pairs_per_s": total_pairs / n_evals / (kern_mean / 1e3),
+           "searches": n_search, "prunes": n_prune}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out["fp32_frac"] = FLOPS_PER_PAIR * out["kernel_pairs_per_s"] / (sms * FP32_LANES_PER_SM * 2 * 2070e6)
+    if with_oracle:
+        import oracle
+        t = time.perf_counter()
+        oracle.energy_forces(frames[0], box.q, box.type, box.ljparams, box.box, RC, beta, box.excl_off,
+                             box.excl_idx)
+        dt = time.perf_counter() - t
+        out["cpu_oracle_s_per_eval"] = dt
+        out["cpu_oracle_pairs_per_s"] = pairs[0] / dt
+    return out
 
 
 def _concat_systems(boxes):
@@ -516,8 +607,7 @@ def run_ours(args, rank, world, local):
     assert err == 0, f"device error word 0x{err:x} in the timed steps"
 
     ms_step = dist_max(statistics.mean(step_ms), world)
-    total_pairs = dist_sum(pairs_per_step * args.steps, world)
-    value = total_pairs / (dist_max(sum(step_ms), world) / 1e3)
+    value = replica_throughput(pairs_per_step * args.steps, sum(step_ms) / 1e3, world)
     kern_ms_per_launch = statistics.mean(kern_ms) / args.evals
     pairs_per_eval = pairs_per_step / args.evals
 
@@ -552,13 +642,15 @@ def run_ours(args, rank, world, local):
             b.record(stream)
             torch.cuda.synchronize()
             e2e_ms.append(a.elapsed_time(b))
-        e2e_value = total_pairs / (dist_max(sum(e2e_ms), world) / 1e3)
+        e2e_value = replica_throughput(pairs_per_step * args.steps, sum(e2e_ms) / 1e3, world)
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": args.evals * N * 12,
                "d2h_bytes_per_step": args.evals * (N * 12 + 16)}
         assert eng.check() == 0
 
     backward = None if args.no_extras else bench_backward(dev)
     batched = None if args.no_extras else bench_batch(dev)
+    million = None if args.no_extras else bench_million(
+        dev, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -598,6 +690,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": n_launch_search * searches + n_launch_prune * prunes + n_launch_force * args.evals,
         "backward": backward,
         "batched": batched,
+        "million": million,
     }
     print(json.dumps(line), flush=True)
 

@@ -55,7 +55,7 @@ void free_buffers(nb_pairlist *pl) {
                     pl->ci_len_inner, pl->gsort,   pl->bsort,          pl->glj_acc,        pl->sys,
                     pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys,       pl->len_hist,
                     pl->len_offsets, pl->len_cursor, pl->ci_order,     pl->vt_slot,        pl->vt_mask,
-                    pl->half_start, pl->half_len};
+                    pl->half_start, pl->half_len,  pl->len_key};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -138,6 +138,7 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
                 alloc(&pl->col_sys, pl->ncol_max, &total) && alloc(&pl->clus_sys, pl->nc_max, &total) &&
                 alloc(&pl->len_hist, NB_LEN_BINS, &total) && alloc(&pl->len_offsets, NB_LEN_BINS, &total) &&
                 alloc(&pl->len_cursor, NB_LEN_BINS, &total) && alloc(&pl->ci_order, pl->nc_max, &total) &&
+                alloc(&pl->len_key, pl->nc_max, &total) &&
                 alloc(&pl->half_start, 2 * (size_t)pl->nc_max, &total) &&
                 alloc(&pl->half_len, 2 * (size_t)pl->nc_max, &total);
     // gathered tiles pack a slot in 27 bits and index tiles with 32-bit ints;
@@ -318,7 +319,7 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     NB_CUDA(nb_launch_search(pl, excl_off, excl_idx, rl2, rl_col, s));
     pl->sorted = 0;
     if (!(pl->flags & NB_FLAG_NO_LIST_SORT)) {
-        NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_outer, s));
+        NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_outer, false, s));
         pl->sorted = 1;
     }
     pl->searched = 1;
@@ -338,10 +339,12 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(nb_launch_gather(pl, coords, nullptr, nullptr, 1, 1, nullptr, s));
     const float r2cut = r_inner * r_inner;
+    const bool sort = !(pl->flags & NB_FLAG_NO_LIST_SORT);
+    if (sort) NB_CUDA(nb_clear_len_hist(pl, s));
     NB_CUDA(nb_launch_prune(pl, r2cut, stale_bound2(pl->rlist, r_inner), s));
     pl->sorted = 0;
-    if (!(pl->flags & NB_FLAG_NO_LIST_SORT)) {
-        NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_inner, s));
+    if (sort) {
+        NB_CUDA(nb_launch_sort_by_length(pl, pl->len_key, true, s));
         pl->sorted = 1;
     }
     pl->has_inner = 1;

@@ -108,12 +108,15 @@ __device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, const
 // j-stationary kernel over gathered tiles. A warp takes one half i-cluster
 // (4 i rows) at a time; its tiles are read in groups of 4 (32 j atoms, one
 // per lane), and each lane computes its j atom against the 4 rows. j forces
-// stay in registers for the 4 pairs and go out with 3 atomics per lane;
+// stay in registers for the 4 pairs and go out with one 16-byte vector
+// atomic per lane (fsort is float4 per slot);
 // i forces stay in registers for the whole half and are reduced across the
 // warp at its end. Group g + 1 is copied (cp.async) into the other buffer
 // while group g is computed.
+// 768 / THREADS resident CTAs per SM leave 80 registers per thread: enough
+// to keep the 4 rows' positions, LJ rows and forces in registers.
 template <bool ENERGY, bool COUNT, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p) {
+__global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p) {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ float4 s_lj[];
     __shared__ VtStage s_st[kWarps][2];
@@ -171,6 +174,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p
         const int ngroups = (t1 - t0 + 3) >> 2;
         cp_async_wait_all();
         __syncwarp();
+        float4 xr[4];
+        int trr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            xr[a] = s_xi[warp][a];
+            trr[a] = s_tr[warp][a];
+        }
         for (int g = 0; g < ngroups; ++g) {
             VtStage &cs = s_st[warp][g & 1];
             const float4 xj = cs.xj[lane];
@@ -184,16 +194,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p
             for (int a = 0; a < 4; ++a) {
                 if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
                     vn = stage_group(p, s_st[warp][(g + 1) & 1], shift, t0, t1, g + 1, lane);
-                const float4 xi = s_xi[warp][a];
-                const int c1 = nb_pair<true, ENERGY>(xi, xi.w, xj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
+                const float4 xi = xr[a];
+                const int c1 = nb_pair<true, ENERGY>(xi, xi.w, xj, s_lj[trr[a] + tj], S.x, S.y, S.z,
                                                      ((mrow >> (8 * a)) & 1u) != 0u, p.cc, fi[a], fj, ec, elj);
                 if (COUNT) cnt += c1;
             }
-            if (slot != p.pad_slot) {  // all padding lanes share one slot: no atomics there
-                atomicAdd(p.fsort + 4 * slot + 0, fj.x);
-                atomicAdd(p.fsort + 4 * slot + 1, fj.y);
-                atomicAdd(p.fsort + 4 * slot + 2, fj.z);
-            }
+            if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
+                atomicAdd(reinterpret_cast<float4 *>(p.fsort) + slot, make_float4(fj.x, fj.y, fj.z, 0.0f));
             v = vn;
             cp_async_wait_all();
             __syncwarp();
@@ -208,8 +215,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force_vt(VtParams p
             r[4 * a + 3] = 0.0f;
         }
         reduce_scatter16(r, lane);
-        const int k = lane >> 1;
-        if ((lane & 1) == 0 && (k & 3) != 3) atomicAdd(p.fsort + 4 * (ibase + (k >> 2)) + (k & 3), r[0]);
+        // lane 8a holds row a's x; its y and z sit 2 and 4 lanes up
+        const float ry = __shfl_down_sync(0xffffffffu, r[0], 2);
+        const float rz = __shfl_down_sync(0xffffffffu, r[0], 4);
+        if ((lane & 7) == 0)
+            atomicAdd(reinterpret_cast<float4 *>(p.fsort) + ibase + (lane >> 3), make_float4(r[0], ry, rz, 0.0f));
         if (ENERGY) {
             ecd += (double)ec;
             eljd += (double)elj;

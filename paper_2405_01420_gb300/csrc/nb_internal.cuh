@@ -98,6 +98,7 @@ struct nb_pairlist {
     int *clus_sys;        // [nc_max] system of each cluster
     nb_sys *sys_host;     // host copy of the table [nsys]
     int *len_hist;        // [NB_LEN_BINS] list-length histogram (post-prune sorting)
+    int *len_key;         // [nc_max] per-i-cluster work after a prune (gathered tiles, else inner entries)
     int *len_offsets;     // [NB_LEN_BINS]
     int *len_cursor;      // [NB_LEN_BINS]
     int *ci_order;        // [nc_max] i-clusters by decreasing list length
@@ -160,7 +161,11 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
 cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
                              int ntype, int snapshot, double *energies, cudaStream_t s);
 cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2, cudaStream_t s);
-cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, cudaStream_t s);
+// Orders i-clusters by decreasing ci_len. hist_ready: the histogram of
+// ci_len is already in len_hist (the prune computes it), else it is built here.
+cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, bool hist_ready, cudaStream_t s);
+// Clears the list-length histogram ahead of a prune that fills it.
+cudaError_t nb_clear_len_hist(nb_pairlist *pl, cudaStream_t s);
 cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
                                double *energies, float stale_prune2, cudaStream_t s);
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,

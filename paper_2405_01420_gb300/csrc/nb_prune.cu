@@ -1,5 +1,7 @@
 // Rolling prune (§III-A, "Prune-only kernel"): outer list at rlist ->
-// inner list at r_inner, with atom-pair in-range masks.
+// inner list at r_inner, with atom-pair in-range masks. As in the paper's
+// post-pruning list sorting, the prune also computes the list-size
+// histogram that the sort needs.
 //
 // One warp per i-cluster (work counter). For each outer entry the 32 lanes
 // test its 64 atom pairs (lane l: pairs (l>>3, l&7) and (l>>3 + 4, l&7),
@@ -28,6 +30,8 @@ struct PruneParams {
     int *half_start;     // [2 nc_max]
     int *half_len;       // [2 nc_max]
     int pad_slot;        // a slot that never holds an atom (far away, q = 0)
+    int *len_key;        // [nc_max] work of each i-cluster for the force kernel
+    int *len_hist;       // [NB_LEN_BINS] histogram of len_key, or NULL (no sorting)
     float r2cut;
     float stale_search2;
 };
@@ -198,6 +202,10 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         if (lane == 0) {
             p.ci_len_inner[ci] = out;
             atomicAdd(&p.st->inner_count, (unsigned long long)out);
+            // post-prune sorting: the force kernel's work for ci and its histogram
+            const int key = TILES ? ntile[0] + ntile[1] : out;
+            p.len_key[ci] = key;
+            if (p.len_hist) atomicAdd(&p.len_hist[min(key, NB_LEN_BINS - 1)], 1);
         }
     }
 }
@@ -220,6 +228,8 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     p.half_start = pl->half_start;
     p.half_len = pl->half_len;
     p.pad_slot = pl->nc_max * NB_CLUSTER;
+    p.len_key = pl->len_key;
+    p.len_hist = (pl->flags & NB_FLAG_NO_LIST_SORT) ? nullptr : pl->len_hist;
     p.r2cut = r_inner2;
     p.stale_search2 = stale_search2;
     // work_prune and inner_count were reset by the snapshot gather before this launch

@@ -6,7 +6,8 @@
 // order of decreasing list length lets the longest lists start first, so the
 // persistent grid ends with short items and a short tail.
 //
-// k_len_hist     histogram of the per-i-cluster list lengths
+// k_len_hist     histogram of the per-i-cluster list lengths (after a search;
+//                after a prune the prune kernel builds it, as in the paper)
 // k_len_offsets  exclusive scan of the histogram from the longest length down
 // k_len_scatter  ci -> order[offset(len) + rank within its length]
 #include "nb_internal.cuh"
@@ -49,11 +50,17 @@ __global__ void k_len_scatter(const int *__restrict__ ci_len, const nb_dev_state
 
 }  // namespace
 
-cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(pl->len_hist, 0, sizeof(int) * NB_LEN_BINS, s);
-    if (e != cudaSuccess) return e;
+cudaError_t nb_clear_len_hist(nb_pairlist *pl, cudaStream_t s) {
+    return cudaMemsetAsync(pl->len_hist, 0, sizeof(int) * NB_LEN_BINS, s);
+}
+
+cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, bool hist_ready, cudaStream_t s) {
     const int blocks = max(1, min((pl->nc_max + 255) / 256, pl->num_sms * 4));
-    k_len_hist<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_hist);
+    if (!hist_ready) {
+        cudaError_t e = nb_clear_len_hist(pl, s);
+        if (e != cudaSuccess) return e;
+        k_len_hist<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_hist);
+    }
     k_len_offsets<<<1, NB_LEN_BINS, 0, s>>>(pl->len_hist, pl->len_offsets, pl->len_cursor);
     k_len_scatter<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_offsets, pl->len_cursor, pl->ci_order);
     return cudaGetLastError();
