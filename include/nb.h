@@ -86,9 +86,9 @@ typedef struct {
    and prune (§III-A: the post-pruning list sorting that shortens the tail
    of the force kernel; on by default). */
 #define NB_FLAG_NO_LIST_SORT 0x2u
-/* nb_config.flags: after a prune, compute forces over the 8x8 cluster-pair
-   tiles of the inner list instead of the gathered 4x8 tiles (same results;
-   for comparison). */
+/* nb_config.flags: after a prune, compute forces (nb_forces) and the adjoint
+   (nb_backward) over the 8x8 cluster-pair tiles of the inner list instead
+   of the gathered 4x8 tiles (same results; for comparison). */
 #define NB_FLAG_CLUSTER_TILES 0x4u
 
 /* Host-side snapshot of a pair list (filled by nb_pairlist_stats). */
@@ -261,7 +261,8 @@ int nb_pairlist_export(nb_pairlist *pl, int which, int *ci, int *cj, int *shift,
  * r_inner of any of its rows into tiles of 8: slots[8*k + p] is the cluster
  * slot of j atom p (low 27 bits) and its shift index (top 5 bits);
  * masks[k] bit a*8+p marks row a with atom p in range. After a prune
- * nb_forces computes over these tiles unless NB_FLAG_CLUSTER_TILES is set.
+ * nb_forces and nb_backward compute over these tiles unless
+ * NB_FLAG_CLUSTER_TILES is set.
  * half_id, masks: [cap]; slots: [8*cap]. *n_out receives the tile count.
  */
 int nb_pairlist_export_tiles(nb_pairlist *pl, int *half_id, int *slots, unsigned *masks, size_t cap,

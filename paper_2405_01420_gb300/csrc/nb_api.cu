@@ -163,6 +163,7 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
     NB_CUDA(cudaMemset(pl->col_sys, 0, sizeof(int) * (size_t)pl->ncol_max));
     NB_CUDA(cudaMemset(pl->clus_sys, 0, sizeof(int) * (size_t)pl->nc_max));
     NB_CUDA(cudaMemset(pl->tsort, 0, sizeof(int) * nslot));
+    NB_CUDA(cudaMemset(pl->gsort, 0, sizeof(float4) * nslot));  // the pad slot's g stays 0
     const float4 far = make_float4(NB_PAD_COORD, NB_PAD_COORD, NB_PAD_COORD, 0.0f);
     NB_CUDA(cudaMemcpy(pl->xq + (size_t)pl->nc_max * NB_CLUSTER, &far, sizeof(float4), cudaMemcpyHostToDevice));
     return NB_OK;

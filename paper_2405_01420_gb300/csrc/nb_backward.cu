@@ -14,7 +14,9 @@
 //
 // k_gather_g   g (original order) -> gsort (cluster order); zeroes the
 //              gradient accumulators.
-// k_backward   one warp per i-cluster (work counter), list entries and their
+// k_backward   (8 x 8 cluster tiles; after a prune the gathered-tile form in
+//              nb_backward_vt.cu runs instead)
+//              one warp per i-cluster (work counter), list entries and their
 //              j data staged in shared memory, lane layout as in k_force;
 //              j-side gradients (x, y, z, q) reduce-scatter so every lane adds
 //              one component; per-lane LJ accumulators by j type (NT <= 4).
@@ -61,56 +63,6 @@ __global__ void k_gather_g(int nmax_slots, const int *__restrict__ perm, const f
     }
     if (blockIdx.x == 0)
         for (int k = threadIdx.x; k < nlj; k += blockDim.x) glj_acc[k] = 0.0;
-}
-
-// One pair of the adjoint. bi/bj accumulate (dL/dx, dL/dq); d6/d12 return
-// the pair's dL/dC6 and dL/dC12 (0 when the pair does not count).
-template <bool SHIFT>
-__device__ __forceinline__ void nb_pair_bwd(const float4 xi, const float qi_f, const float4 gi, const float4 xj,
-                                            const float qj_f, const float4 gj, const float4 lj, const float Sx,
-                                            const float Sy, const float Sz, const bool in_mask, const BwdParams &p,
-                                            float4 &bi, float4 &bj, float &d6, float &d12) {
-    float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y), dz = __fsub_rn(xi.z, xj.z);
-    if (SHIFT) {
-        dx = __fadd_rn(dx, Sx);
-        dy = __fadd_rn(dy, Sy);
-        dz = __fadd_rn(dz, Sz);
-    }
-    const float r2 = nb_r2(dx, dy, dz);
-    const bool in = in_mask && (r2 < p.cc.rc2);
-    const float y0 = nb_rsqrt(r2);
-    const float rinv = fmaf(0.5f * y0, fmaf(-(r2 * y0), y0, 1.0f), y0);
-    const float rinv2 = rinv * rinv;
-    const float rinv6 = rinv2 * rinv2 * rinv2;
-    const float v6 = lj.x * rinv6, v12 = lj.y * rinv6 * rinv6;
-    const float slj = fmaf(12.0f, v12, -6.0f * v6) * rinv2;
-    const float r = r2 * rinv;
-    const float ex = nb_exp2(p.cc.kexp * r2);
-    const float a = ex * nb_erfcx(p.cc.beta * r) * rinv;  // erfc(beta r)/r
-    const float Bc = fmaf(p.cc.c2b, ex, a) * rinv2;        // B
-    const float qq = qi_f * xj.w;                          // f q_a q_b
-    const float sC = qq * Bc;
-    const float s = sC + slj;
-    const float spr = rinv2 * fmaf(rinv2, fmaf(48.0f, v6, -168.0f * v12), fmaf(-3.0f, sC, -p.k2 * qq * ex));
-    const float ux = gi.x - gj.x, uy = gi.y - gj.y, uz = gi.z - gj.z;
-    const float ud = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
-    // Pairs that do not count can carry inf/NaN in their pair terms (r2 = 0
-    // on a masked diagonal): select, never multiply by a zero factor.
-    const float sm = in ? s : 0.0f;
-    const float t = in ? spr * ud : 0.0f;
-    const float vx = fmaf(sm, ux, t * dx), vy = fmaf(sm, uy, t * dy), vz = fmaf(sm, uz, t * dz);
-    bi.x += vx;
-    bi.y += vy;
-    bi.z += vz;
-    bj.x -= vx;
-    bj.y -= vy;
-    bj.z -= vz;
-    const float bud = in ? Bc * ud : 0.0f;
-    bi.w = fmaf(qj_f, bud, bi.w);
-    bj.w = fmaf(qi_f, bud, bj.w);
-    const float r8ud = rinv6 * rinv2 * ud;
-    d6 = in ? -6.0f * r8ud : 0.0f;
-    d12 = in ? 12.0f * rinv6 * r8ud : 0.0f;
 }
 
 template <int NT>
@@ -197,20 +149,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdParams p) {
                 float d6, d12;
                 if (mlo) {
                     if (e.y == NB_SHIFT_CENTER)
-                        nb_pair_bwd<false>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
-                                           (mlo & lanebit) != 0u, p, bi1, bj, d6, d12);
+                        nb_pair_adj<false>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
+                                           (mlo & lanebit) != 0u, p.cc, p.k2, bi1, bj, d6, d12);
                     else
-                        nb_pair_bwd<true>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], S.x, S.y, S.z,
-                                          (mlo & lanebit) != 0u, p, bi1, bj, d6, d12);
+                        nb_pair_adj<true>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], S.x, S.y, S.z,
+                                          (mlo & lanebit) != 0u, p.cc, p.k2, bi1, bj, d6, d12);
                     add_onehot<NT>(acc1, tj, d6, d12);
                 }
                 if (mhi) {
                     if (e.y == NB_SHIFT_CENTER)
-                        nb_pair_bwd<false>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
-                                           (mhi & lanebit) != 0u, p, bi2, bj, d6, d12);
+                        nb_pair_adj<false>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
+                                           (mhi & lanebit) != 0u, p.cc, p.k2, bi2, bj, d6, d12);
                     else
-                        nb_pair_bwd<true>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], S.x, S.y, S.z,
-                                          (mhi & lanebit) != 0u, p, bi2, bj, d6, d12);
+                        nb_pair_adj<true>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], S.x, S.y, S.z,
+                                          (mhi & lanebit) != 0u, p.cc, p.k2, bi2, bj, d6, d12);
                     add_onehot<NT>(acc2, tj, d6, d12);
                 }
                 // reduce-scatter (x, y, z, q) over the 4 lanes sharing b
@@ -330,7 +282,9 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
     p.stale_prune2 = stale_prune2;
     p.has_inner = pl->has_inner;
     cudaError_t e;
-    if (ntype == 1)
+    if (pl->has_vtiles && !(pl->flags & NB_FLAG_CLUSTER_TILES))  // gathered tiles after a prune
+        e = nb_launch_backward_vt(pl, ntype, ljparams, rc, beta, stale_prune2, s);
+    else if (ntype == 1)
         e = launch_bwd<1>(pl, p, s);
     else if (ntype == 2)
         e = launch_bwd<2>(pl, p, s);

@@ -1,0 +1,245 @@
+// Adjoint over gathered tiles (after a prune): the j-stationary layout of
+// the gathered-tile force kernel applied to nb_pair_adj.
+//
+// A warp takes one half i-cluster (4 i rows) at a time and reads its
+// gathered tiles in groups of 32 j atoms, one per lane; each lane computes
+// the adjoint of its j atom against the 4 rows.
+//  - j side (dL/dx, dL/dq): registers over the 4 rows, then one 16-byte
+//    vector atomic per lane into bsort (float4 per slot).
+//  - i side: registers over the whole half, reduced across the warp at its
+//    end (reduce-scatter), one vector atomic per row.
+//  - dL/dC6, dL/dC12: per-lane FP32 accumulators for each (row, j type),
+//    reduced across the warp once per half and added in FP64 to the
+//    unsymmetrised [ntype][ntype][2] accumulator.
+// Group g + 1's j data (coordinates and charge, g, type, mask word) are
+// copied into shared memory with cp.async while group g computes.
+#include "nb_pair.cuh"
+#include "nb_warp.cuh"
+
+namespace {
+
+constexpr int kBvtThreads = 128;
+constexpr int kBvtWarps = kBvtThreads / 32;
+
+struct BvtParams {
+    const float4 *xq;
+    const int *tsort;
+    const float4 *gsort;
+    float4 *bsort;            // (dL/dx, dL/dq) per slot
+    double *glj_acc;          // [ntype][ntype][2], unsymmetrised
+    const int *vt_slot;       // 8 per tile: slot | shift << 27
+    const unsigned *vt_mask;  // 4 x 8 bits per tile
+    const int *half_start;
+    const int *half_len;
+    const int *order;         // i-clusters by decreasing work, or NULL
+    const float *ljparams;
+    nb_dev_state *st;
+    const float4 *sys_shift;  // [27 nsys]
+    const int *clus_sys;
+    int ntype;
+    nb_coul cc;
+    float k2;  // 2 (2 beta/sqrt(pi)) beta^2
+    float stale_prune2;
+    int pad_slot;  // never holds an atom: far away, q = 0, type 0
+};
+
+struct BvtStage {
+    float4 xj[32];
+    float4 gj[32];
+    int tj[32];
+    unsigned m[32];
+};
+
+// Issues the copies of the lane's j atom in group g of the half with tiles
+// [t0, t1); returns its slot word (the pad slot with an empty mask past the end).
+__device__ __forceinline__ int stage_adj(const BvtParams &p, BvtStage &st, int t0, int t1, int g, int lane) {
+    const int tile = t0 + 4 * g + (lane >> 3);
+    int v = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+    if (tile < t1) {
+        v = p.vt_slot[8 * (size_t)tile + (lane & 7)];
+        cp_async4(&st.m[lane], p.vt_mask + tile);
+    } else {
+        st.m[lane] = 0u;
+    }
+    const int slot = v & 0x07ffffff;
+    cp_async16(&st.xj[lane], p.xq + slot);
+    cp_async16(&st.gj[lane], p.gsort + slot);
+    cp_async4(&st.tj[lane], p.tsort + slot);
+    return v;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
+    extern __shared__ float4 s_lj[];  // (C6, C12, 0, 0)
+    __shared__ BvtStage s_st[kBvtWarps][2];
+    __shared__ float4 s_shift[kBvtWarps][27];
+    __shared__ float4 s_xi[kBvtWarps][4];  // (x, y, z, f q)
+    __shared__ float4 s_gi[kBvtWarps][4];
+    __shared__ int s_tr[kBvtWarps][4];     // LJ table row of each i row
+    const int nt2 = p.ntype * p.ntype;
+    for (int k = threadIdx.x; k < nt2; k += blockDim.x)
+        s_lj[k] = make_float4(p.ljparams[2 * k], p.ljparams[2 * k + 1], 0.0f, 0.0f);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned ds = p.st->cur_d2_search, dp = p.st->cur_d2_prune;
+        p.st->last_d2_search = ds;
+        p.st->last_d2_prune = dp;
+        p.st->cur_d2_search = 0u;
+        p.st->cur_d2_prune = 0u;
+        if (__uint_as_float(dp) > p.stale_prune2) atomicOr(&p.st->err, NB_DEV_STALE_PRUNE);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned nwork = 2u * (unsigned)p.st->nc;
+    int shift_sys = -1;
+
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(&p.st->work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= nwork) break;
+        const int ci = p.order ? p.order[w >> 1] : (int)(w >> 1);
+        const int h = (int)(w & 1u);
+        const int t0 = p.half_start[2 * ci + h], t1 = t0 + p.half_len[2 * ci + h];
+        if (t1 <= t0) continue;
+        const int csys = p.clus_sys[ci];
+        if (csys != shift_sys) {
+            if (lane < 27) s_shift[warp][lane] = p.sys_shift[27 * csys + lane];
+            shift_sys = csys;
+        }
+        const int ibase = ci * NB_CLUSTER + 4 * h;
+        int v = stage_adj(p, s_st[warp][0], t0, t1, 0, lane);
+        if (lane < 4) {
+            const float4 x = p.xq[ibase + lane];
+            s_xi[warp][lane] = make_float4(x.x, x.y, x.z, x.w * NB_COULOMB_F);
+            s_gi[warp][lane] = p.gsort[ibase + lane];
+            s_tr[warp][lane] = p.tsort[ibase + lane] * p.ntype;
+        }
+        float4 bi[4];
+        float acc[4][NT][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            bi[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < NT; ++t) acc[a][t][0] = acc[a][t][1] = 0.0f;
+        }
+        const int ngroups = (t1 - t0 + 3) >> 2;
+        cp_async_wait_all();
+        __syncwarp();
+        for (int g = 0; g < ngroups; ++g) {
+            const BvtStage &cs = s_st[warp][g & 1];
+            const float4 xj = cs.xj[lane];
+            const float4 gj = cs.gj[lane];
+            const int tj = cs.tj[lane];
+            const unsigned mrow = cs.m[lane] >> (lane & 7);
+            const float4 S = s_shift[warp][(unsigned)v >> 27];
+            const int slot = v & 0x07ffffff;
+            const float qj_f = xj.w * NB_COULOMB_F;
+            float4 bj = make_float4(0.f, 0.f, 0.f, 0.f);
+            int vn = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
+                    vn = stage_adj(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
+                const float4 xi = s_xi[warp][a];
+                float d6, d12;
+                nb_pair_adj<true>(xi, xi.w, s_gi[warp][a], xj, qj_f, gj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
+                                  ((mrow >> (8 * a)) & 1u) != 0u, p.cc, p.k2, bi[a], bj, d6, d12);
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {  // one-hot by the j atom's type
+                    const float oh = (tj == t) ? 1.0f : 0.0f;
+                    acc[a][t][0] = fmaf(oh, d6, acc[a][t][0]);
+                    acc[a][t][1] = fmaf(oh, d12, acc[a][t][1]);
+                }
+            }
+            if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
+                atomicAdd(p.bsort + slot, bj);
+            v = vn;
+            cp_async_wait_all();
+            __syncwarp();
+        }
+        // i side: value 4a + c (c = x, y, z, q); lane 8a then holds row a's x
+        // and finds y, z, q 2, 4 and 6 lanes up
+        {
+            float r[16];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                r[4 * a + 0] = bi[a].x;
+                r[4 * a + 1] = bi[a].y;
+                r[4 * a + 2] = bi[a].z;
+                r[4 * a + 3] = bi[a].w;
+            }
+            reduce_scatter<16>(r, lane);
+            const float ry = __shfl_down_sync(0xffffffffu, r[0], 2);
+            const float rz = __shfl_down_sync(0xffffffffu, r[0], 4);
+            const float rq = __shfl_down_sync(0xffffffffu, r[0], 6);
+            if ((lane & 7) == 0) atomicAdd(p.bsort + ibase + (lane >> 3), make_float4(r[0], ry, rz, rq));
+        }
+        // LJ gradients: value (a NT + t) 2 + c
+        {
+            constexpr int kN = 8 * NT;
+            constexpr int kShift = NT == 4 ? 0 : (NT == 2 ? 1 : 2);  // lane -> value: lane >> kShift
+            float r[kN];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    r[(a * NT + t) * 2 + 0] = acc[a][t][0];
+                    r[(a * NT + t) * 2 + 1] = acc[a][t][1];
+                }
+            reduce_scatter<kN>(r, lane);
+            const int k = lane >> kShift;
+            const int a = k / (2 * NT), t = (k >> 1) % NT, c = k & 1;
+            if ((lane & ((1 << kShift) - 1)) == 0 && t < p.ntype)
+                atomicAdd(&p.glj_acc[2 * (s_tr[warp][a] + t) + c], (double)r[0]);
+        }
+        __syncwarp();
+    }
+}
+
+template <int NT>
+cudaError_t launch_bvt(nb_pairlist *pl, const BvtParams &p, cudaStream_t s) {
+    const size_t smem = sizeof(float4) * (size_t)p.ntype * p.ntype;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_vt<NT>, kBvtThreads,
+                                                                      sizeof(float4) * 16);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int blocks = min(pl->num_sms * per_sm, (2 * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
+    k_backward_vt<NT><<<max(blocks, 1), kBvtThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
+                                  float stale_prune2, cudaStream_t s) {
+    BvtParams p;
+    p.xq = pl->xq;
+    p.tsort = pl->tsort;
+    p.gsort = pl->gsort;
+    p.bsort = pl->bsort;
+    p.glj_acc = pl->glj_acc;
+    p.vt_slot = pl->vt_slot;
+    p.vt_mask = pl->vt_mask;
+    p.half_start = pl->half_start;
+    p.half_len = pl->half_len;
+    p.order = pl->sorted ? pl->ci_order : nullptr;
+    p.ljparams = ljparams;
+    p.st = pl->st;
+    p.sys_shift = pl->sys_shift;
+    p.clus_sys = pl->clus_sys;
+    p.ntype = ntype;
+    p.cc.rc2 = rc * rc;
+    p.cc.beta = beta;
+    p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
+    p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    p.k2 = (float)(2.0 * (2.0 * beta / 1.7724538509055159) * (double)beta * beta);
+    p.stale_prune2 = stale_prune2;
+    p.pad_slot = pl->nc_max * NB_CLUSTER;
+    if (ntype == 1) return launch_bvt<1>(pl, p, s);
+    if (ntype == 2) return launch_bvt<2>(pl, p, s);
+    return launch_bvt<4>(pl, p, s);
+}

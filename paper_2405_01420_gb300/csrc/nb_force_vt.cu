@@ -3,17 +3,27 @@
 // After a prune, each half i-cluster (rows 0-3 or 4-7 of an 8-atom cluster)
 // has a list of 4 x 8 tiles whose 8 j atoms are gathered from all its
 // cluster pairs: only j atoms within r_inner of at least one of the 4 rows
-// appear, each with its own periodic shift. On water at rc 1.0 / r_inner
-// 1.04 nm about 63% of the computed pair slots are in range, against 40% for
-// 8 x 8 cluster tiles with empty half-tiles skipped; the arithmetic per pair
-// is the same (nb_pair with d = (y_a - y_b) + S).
+// appear, each with its own periodic shift (nb_prune.cu writes them). The
+// arithmetic per pair is that of the cluster-pair kernel (nb_pair with
+// d = (y_a - y_b) + S), so both kernels make the same in-range decisions.
 //
-// One warp per half i-cluster; lane l owns i-row a = l >> 3 and tile column
-// p = l & 7, i.e. mask bit l. Tiles are staged in shared memory CHUNK at a
-// time (j coordinates, types, shift vectors, slots). j forces reduce-scatter
-// over the 4 lanes of a column and are added with one atomic per (atom,
-// component); i forces stay in registers for the whole half.
+// Layout (j-stationary): a warp takes one half at a time and reads its
+// tiles in groups of 4, i.e. 32 j atoms, one per lane; each lane computes
+// its j atom against the half's 4 i rows. On water at rc 1.0 / r_inner
+// 1.04 nm about 60% of these pair slots are in range, against 40% for 8 x 8
+// cluster tiles with empty half-tiles skipped.
+//
+//  - j data (coordinates and charge, type, mask word) of group g + 1 are
+//    copied into shared memory with cp.async while group g computes; the
+//    shift vectors come from a per-warp shared copy of the system's 27.
+//  - j forces stay in registers over the 4 rows and go out with one
+//    16-byte vector atomic per lane (fsort is float4 per slot).
+//  - i forces stay in registers over the whole half and are reduced across
+//    the warp at its end, one vector atomic per row.
+//  - Energies: FP32 per lane over a half, FP64 across halves, FP64 atomics
+//    per system when the warp moves to another system or finishes.
 #include "nb_pair.cuh"
+#include "nb_warp.cuh"
 
 namespace {
 
@@ -49,38 +59,9 @@ __device__ __forceinline__ void flush_energies_vt(double ec, double elj, int lan
     }
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Sums v[0..15] over the 32 lanes of the warp, reduce-scatter style: on
-// return lanes 2k and 2k + 1 hold the total of value k in v[0].
-__device__ __forceinline__ void reduce_scatter16(float (&v)[16], int lane) {
-#pragma unroll
-    for (int n = 16, o = 16; n > 1; n >>= 1, o >>= 1) {
-        const bool upper = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < n / 2; ++i) {
-            const float send = upper ? v[i] : v[i + n / 2];
-            const float keep = upper ? v[i + n / 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
 // Per-lane staging of one group of 32 gathered j atoms (4 tiles of 8).
 struct VtStage {
     float4 xj[32];
-    float4 S[32];
     int tj[32];
     unsigned m[32];
 };
@@ -88,7 +69,7 @@ struct VtStage {
 // Issues the copies of group g of the half with tiles [t0, t1) into st
 // (one j atom per lane); returns the lane's slot word. Lanes past the end
 // take the pad slot (never occupied, q = 0) with an empty mask.
-__device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, const float4 *shift, int t0, int t1, int g,
+__device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, int t0, int t1, int g,
                                            int lane) {
     const int tile = t0 + 4 * g + (lane >> 3);
     int v = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
@@ -101,7 +82,6 @@ __device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, const
     const int slot = v & 0x07ffffff;
     cp_async16(&st.xj[lane], p.xq + slot);
     cp_async4(&st.tj[lane], p.tsort + slot);
-    cp_async16(&st.S[lane], shift + ((unsigned)v >> 27));
     return v;
 }
 
@@ -120,6 +100,8 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     constexpr int kWarps = THREADS / 32;
     extern __shared__ float4 s_lj[];
     __shared__ VtStage s_st[kWarps][2];
+    __shared__ float4 s_shift[kWarps][27];  // the warp's copy of its system's shift vectors
+    int shift_sys = -1;
     __shared__ float4 s_xi[kWarps][4];
     __shared__ int s_tr[kWarps][4];
     const int nt2 = p.ntype * p.ntype;
@@ -159,9 +141,12 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         if (w >= nwork) break;
         const int t0 = p.half_start[2 * ci + h], t1 = t0 + p.half_len[2 * ci + h];
         if (t1 <= t0) continue;
-        const float4 *shift = p.sys_shift + 27 * csys;
+        if (csys != shift_sys) {
+            if (lane < 27) s_shift[warp][lane] = p.sys_shift[27 * csys + lane];
+            shift_sys = csys;
+        }
         const int ibase = ci * NB_CLUSTER + 4 * h;
-        int v = stage_group(p, s_st[warp][0], shift, t0, t1, 0, lane);
+        int v = stage_group(p, s_st[warp][0], t0, t1, 0, lane);
         if (lane < 4) {
             const float4 x = p.xq[ibase + lane];
             s_xi[warp][lane] = make_float4(x.x, x.y, x.z, x.w * NB_COULOMB_F);
@@ -184,7 +169,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         for (int g = 0; g < ngroups; ++g) {
             VtStage &cs = s_st[warp][g & 1];
             const float4 xj = cs.xj[lane];
-            const float4 S = cs.S[lane];
+            const float4 S = s_shift[warp][(unsigned)v >> 27];
             const int tj = cs.tj[lane];
             const unsigned mrow = cs.m[lane] >> (lane & 7);
             const int slot = v & 0x07ffffff;
@@ -193,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
-                    vn = stage_group(p, s_st[warp][(g + 1) & 1], shift, t0, t1, g + 1, lane);
+                    vn = stage_group(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xi = xr[a];
                 const int c1 = nb_pair<true, ENERGY>(xi, xi.w, xj, s_lj[trr[a] + tj], S.x, S.y, S.z,
                                                      ((mrow >> (8 * a)) & 1u) != 0u, p.cc, fi[a], fj, ec, elj);
@@ -214,7 +199,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             r[4 * a + 2] = fi[a].z;
             r[4 * a + 3] = 0.0f;
         }
-        reduce_scatter16(r, lane);
+        reduce_scatter<16>(r, lane);
         // lane 8a holds row a's x; its y and z sit 2 and 4 lanes up
         const float ry = __shfl_down_sync(0xffffffffu, r[0], 2);
         const float rz = __shfl_down_sync(0xffffffffu, r[0], 4);

@@ -166,6 +166,8 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
 cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, bool hist_ready, cudaStream_t s);
 // Clears the list-length histogram ahead of a prune that fills it.
 cudaError_t nb_clear_len_hist(nb_pairlist *pl, cudaStream_t s);
+cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
+                                  float stale_prune2, cudaStream_t s);
 cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
                                double *energies, float stale_prune2, cudaStream_t s);
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,

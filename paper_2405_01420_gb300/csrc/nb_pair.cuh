@@ -161,3 +161,58 @@ __device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const 
     }
     return in ? 1 : 0;
 }
+
+// One pair of the adjoint of nb_pair (same distance contract, same pair
+// terms), for g = dL/dF with u = g_a - g_b:
+//   dL/dx_a += s u + (s'/r)(u.d) d,  dL/dx_b -= the same
+//   dL/dq_a += f q_b B (u.d),        dL/dq_b += f q_a B (u.d)
+//   dL/dC6 = -6 r^-8 (u.d),          dL/dC12 = 12 r^-14 (u.d)
+// bi/bj accumulate (dL/dx, dL/dq); d6/d12 return the pair's dL/dC6 and
+// dL/dC12 (0 when the pair does not count). k2 = 2 (2 beta/sqrt(pi)) beta^2.
+template <bool SHIFT>
+__device__ __forceinline__ void nb_pair_adj(const float4 xi, const float qi_f, const float4 gi, const float4 xj,
+                                            const float qj_f, const float4 gj, const float4 lj, const float Sx,
+                                            const float Sy, const float Sz, const bool in_mask, const nb_coul &cc,
+                                            const float k2, float4 &bi, float4 &bj, float &d6, float &d12) {
+    float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y), dz = __fsub_rn(xi.z, xj.z);
+    if (SHIFT) {
+        dx = __fadd_rn(dx, Sx);
+        dy = __fadd_rn(dy, Sy);
+        dz = __fadd_rn(dz, Sz);
+    }
+    const float r2 = nb_r2(dx, dy, dz);
+    const bool in = in_mask && (r2 < cc.rc2);
+    const float y0 = nb_rsqrt(r2);
+    const float rinv = fmaf(0.5f * y0, fmaf(-(r2 * y0), y0, 1.0f), y0);
+    const float rinv2 = rinv * rinv;
+    const float rinv6 = rinv2 * rinv2 * rinv2;
+    const float v6 = lj.x * rinv6, v12 = lj.y * rinv6 * rinv6;
+    const float slj = fmaf(12.0f, v12, -6.0f * v6) * rinv2;
+    const float r = r2 * rinv;
+    const float ex = nb_exp2(cc.kexp * r2);
+    const float a = ex * nb_erfcx(cc.beta * r) * rinv;  // erfc(beta r)/r
+    const float Bc = fmaf(cc.c2b, ex, a) * rinv2;        // B
+    const float qq = qi_f * xj.w;                          // f q_a q_b
+    const float sC = qq * Bc;
+    const float s = sC + slj;
+    const float spr = rinv2 * fmaf(rinv2, fmaf(48.0f, v6, -168.0f * v12), fmaf(-3.0f, sC, -k2 * qq * ex));
+    const float ux = gi.x - gj.x, uy = gi.y - gj.y, uz = gi.z - gj.z;
+    const float ud = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
+    // Pairs that do not count can carry inf/NaN in their pair terms (r2 = 0
+    // on a masked diagonal): select, never multiply by a zero factor.
+    const float sm = in ? s : 0.0f;
+    const float t = in ? spr * ud : 0.0f;
+    const float vx = fmaf(sm, ux, t * dx), vy = fmaf(sm, uy, t * dy), vz = fmaf(sm, uz, t * dz);
+    bi.x += vx;
+    bi.y += vy;
+    bi.z += vz;
+    bj.x -= vx;
+    bj.y -= vy;
+    bj.z -= vz;
+    const float bud = in ? Bc * ud : 0.0f;
+    bi.w = fmaf(qj_f, bud, bi.w);
+    bj.w = fmaf(qi_f, bud, bj.w);
+    const float r8ud = rinv6 * rinv2 * ud;
+    d6 = in ? -6.0f * r8ud : 0.0f;
+    d12 = in ? 12.0f * rinv6 * r8ud : 0.0f;
+}

@@ -44,7 +44,9 @@ def diffbox():
     return b, p, lj
 
 
-def test_backward_matches_oracle_adjoint(nb, diffbox):
+@pytest.mark.parametrize("cluster_tiles", [False, True])
+def test_backward_matches_oracle_adjoint(nb, diffbox, cluster_tiles):
+    """After a prune: the gathered-tile adjoint (default) and the 8 x 8 cluster-tile one."""
     b, p, lj = diffbox
     rc = 1.0
     beta = synth.ewald_beta(rc)
@@ -52,7 +54,7 @@ def test_backward_matches_oracle_adjoint(nb, diffbox):
     d = to_dev(b)
     rng = np.random.default_rng(3)
     g = rng.normal(size=(b.n_atoms, 3)).astype(np.float32)
-    pl = nb.Pairlist(b.n_atoms)
+    pl = nb.Pairlist(b.n_atoms, cluster_tiles=cluster_tiles)
     pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
     pl.prune(d["coords"], 1.04)
     gx, gq, glj = pl.backward(d["coords"], torch.from_numpy(q).cuda(), torch.from_numpy(p["type"]).cuda(),
@@ -65,6 +67,35 @@ def test_backward_matches_oracle_adjoint(nb, diffbox):
     # translation invariance of g.F
     s = gx.double().sum(0).abs().max().item()
     assert s <= 1e-5 * gx.abs().max().item() * np.sqrt(b.n_atoms)
+    pl.close()
+
+
+@pytest.mark.parametrize("ntype", [1, 2])
+def test_backward_water_types(nb, ntype):
+    """Water with 2 types (LJ on O only) and with 1 type (every atom O-like):
+    the gathered-tile adjoint's one- and two-type forms against the oracle."""
+    b = synth.water_box(3000, 21)
+    rc = 1.0
+    beta = synth.ewald_beta(rc)
+    if ntype == 2:
+        typ, lj = b.type, b.ljparams
+    else:
+        typ = np.zeros(b.n_atoms, np.int32)
+        lj = b.ljparams.reshape(-1, 2)[:1].reshape(1, 1, 2).astype(np.float32)
+    d = to_dev(b)
+    rng = np.random.default_rng(ntype)
+    g = rng.normal(size=(b.n_atoms, 3)).astype(np.float32)
+    pl = nb.Pairlist(b.n_atoms)
+    pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
+    pl.prune(d["coords"], 1.04)
+    gx, gq, glj = pl.backward(d["coords"], d["q"], torch.from_numpy(typ).cuda(), torch.from_numpy(lj).cuda(), rc,
+                              beta, torch.from_numpy(g).cuda())
+    assert pl.status() == 0
+    ox, oq, olj = oracle.force_vjp(b.coords, b.q, typ, lj, b.box, rc, beta, g, b.excl_off, b.excl_idx)
+    assert per_atom_err(gx.cpu().numpy(), ox) <= GX_TOL
+    assert per_atom_err(gq.cpu().numpy(), oq) <= GQ_TOL
+    nz = np.abs(olj) > 0
+    np.testing.assert_allclose(glj.cpu().numpy()[nz], olj[nz], rtol=GLJ_TOL)
     pl.close()
 
 
