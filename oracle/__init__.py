@@ -77,6 +77,10 @@ def _load():
             lib.oracle_image_f32.restype = None
             lib.oracle_force_vjp.argtypes = [I, P, P, P, I, P, P, D, D, P, P, P, P, P, P]
             lib.oracle_force_vjp.restype = I
+            lib.oracle_energy_forces_coul.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, D, I, P, P, P]
+            lib.oracle_energy_forces_coul.restype = I
+            lib.oracle_force_vjp_coul.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, D, I, P, P, P, P]
+            lib.oracle_force_vjp_coul.restype = I
             _lib = lib
     return _lib
 
@@ -232,3 +236,64 @@ def force_matching(x, q, type_, lj, box, rc, beta, target, excl_off=None, excl_i
     g = 2.0 * diff / (3 * n)
     gx, gq, glj = force_vjp(x, q, type_, lj, box, rc, beta, g, excl_off, excl_idx)
     return L, gx, gq, glj, F
+
+
+COUL_KINDS = {"ewald": 0, "rf": 1}
+COUL_SHIFT = 0x1
+COUL_EXCL_CORR = 0x2
+
+
+def _coul_flags(shift: bool, excl_corr: bool) -> int:
+    return (COUL_SHIFT if shift else 0) | (COUL_EXCL_CORR if excl_corr else 0)
+
+
+def energy_forces_coul(x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None, kind="ewald",
+                       eps_rf=0.0, shift=False, excl_corr=False):
+    """FP64 energies and forces with the Coulomb options (reaction field,
+    Ewald potential shift, excluded-pair correction).
+
+    Returns ``(F [N,3], E_lj, E_coul, npairs)``; E_coul includes the
+    excluded-pair corrections, npairs counts non-excluded pairs within rc.
+    ``eps_rf`` = 0 means an infinite reaction-field permittivity.
+    """
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    n = x.shape[0]
+    lj = _f64(lj)
+    F = np.zeros((n, 3))
+    E = np.zeros(2)
+    npairs = ctypes.c_longlong(0)
+    rcode = lib.oracle_energy_forces_coul(n, _p(x), _p(_f64(q)), _p(_i32(type_)), lj.shape[0], _p(lj),
+                                          _p(_f64(box)), float(rc), float(beta), _p(_i32(excl_off)),
+                                          _p(_i32(excl_idx)), COUL_KINDS[kind], float(eps_rf),
+                                          _coul_flags(shift, excl_corr), _p(F), _p(E), ctypes.byref(npairs))
+    if rcode != 0:
+        raise ValueError(f"oracle_energy_forces_coul failed with code {rcode}")
+    return F, float(E[0]), float(E[1]), int(npairs.value)
+
+
+def force_vjp_coul(x, q, type_, lj, box, rc, beta, g, excl_off=None, excl_idx=None, kind="ewald", eps_rf=0.0,
+                   excl_corr=False):
+    """Adjoint of energy_forces_coul's forces for g = dL/dF: (gx [N,3], gq [N], glj [nt,nt,2]).
+    O(N^2); for small systems."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    n = x.shape[0]
+    lj = _f64(lj)
+    nt = lj.shape[0]
+    g = _f64(g).reshape(-1, 3)
+    gx = np.zeros((n, 3))
+    gq = np.zeros(n)
+    glj = np.zeros((nt, nt, 2))
+    rcode = lib.oracle_force_vjp_coul(n, _p(x), _p(_f64(q)), _p(_i32(type_)), nt, _p(lj), _p(_f64(box)), float(rc),
+                                      float(beta), _p(_i32(excl_off)), _p(_i32(excl_idx)), COUL_KINDS[kind],
+                                      float(eps_rf), _coul_flags(False, excl_corr), _p(g), _p(gx), _p(gq), _p(glj))
+    if rcode != 0:
+        raise ValueError(f"oracle_force_vjp_coul failed with code {rcode}")
+    return gx, gq, glj
+
+
+def rf_constants(rc: float, eps_rf: float) -> tuple[float, float]:
+    """(k_rf, c_rf) of the reaction field; eps_rf = 0 means infinity."""
+    k = 1.0 / (2.0 * rc ** 3) if eps_rf == 0.0 else (eps_rf - 1.0) / ((2.0 * eps_rf + 1.0) * rc ** 3)
+    return k, 1.0 / rc + k * rc * rc

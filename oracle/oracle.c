@@ -20,6 +20,10 @@
  * (§III-A names it "short-range non-bonded forces" with Ewald-type and
  * Lennard-Jones flavours); this is textbook LJ + Ewald real-space physics.
  *
+ * oracle_energy_forces_coul / oracle_force_vjp_coul (end of this file) add
+ * the reaction-field flavour, the Ewald potential shift and the
+ * excluded-pair correction.
+ *
  * Pins (tests, CPU only): Coulomb's law at beta = 0, tabulated erfc values,
  * the LJ force zero at 2^(1/6) sigma and energy zero at sigma, continuity at
  * rc, sum of forces = 0, translation and permutation invariance, length
@@ -594,5 +598,243 @@ int oracle_force_vjp(int n, const double *x, const double *q, const int *type, i
     free(cell_start);
     free(cell_atoms);
     free(atom_cell);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Coulomb options: the reaction-field flavour, the Ewald potential shift
+ * and the exclusion correction (the paper's benchmark systems come in
+ * Ewald "PME" and reaction-field "RF" flavours, §II; GROMACS's NBNXM kernels
+ * have both). Per pair at distance r, per unit f q_i q_j, with
+ *   E_C = f q_i q_j phi(r),  F_i += f q_i q_j B(r) d,  B = -(1/r) dphi/dr,
+ *   D = (1/r) dB/dr (what the adjoint needs):
+ *
+ *   Ewald:            phi = erfc(beta r)/r - shift,
+ *                     B = [erfc(beta r)/r + (2 beta/sqrt(pi)) exp(-beta^2 r^2)] / r^2,
+ *                     D = [-3 B - 2 (2 beta/sqrt(pi)) beta^2 exp(-beta^2 r^2)] / r^2,
+ *                     shift = erfc(beta rc)/rc with ORACLE_COUL_SHIFT, else 0;
+ *   Ewald, excluded:  phi = -erf(beta r)/r (= erfc(beta r)/r - 1/r),
+ *                     B = B_Ewald - 1/r^3, D = D_Ewald + 3/r^5;
+ *   reaction field:   phi = 1/r + k_rf r^2 - c_rf,  B = 1/r^3 - 2 k_rf,  D = -3/r^5;
+ *   RF, excluded:     phi = k_rf r^2 - c_rf,  B = -2 k_rf,  D = 0;
+ *
+ * with k_rf = (eps_rf - 1) / ((2 eps_rf + 1) rc^3), eps_rf = 0 meaning
+ * infinity (k_rf = 1 / (2 rc^3)), relative permittivity 1 inside the
+ * cutoff, and c_rf = 1/rc + k_rf rc^2 (phi_RF(rc) = 0). Excluded pairs
+ * (from the exclusion lists, r < rc) contribute only with
+ * ORACLE_COUL_EXCL_CORR, and never LJ. The self terms (i = i) are
+ * constants a caller adds; they are not here.
+ * ------------------------------------------------------------------------ */
+
+#define ORACLE_COUL_EWALD 0
+#define ORACLE_COUL_RF 1
+#define ORACLE_COUL_SHIFT 0x1
+#define ORACLE_COUL_EXCL_CORR 0x2
+
+static void rf_constants(double rc, double eps_rf, double *k_rf, double *c_rf) {
+    if (eps_rf == 0.0)
+        *k_rf = 1.0 / (2.0 * rc * rc * rc);
+    else
+        *k_rf = (eps_rf - 1.0) / ((2.0 * eps_rf + 1.0) * rc * rc * rc);
+    *c_rf = 1.0 / rc + *k_rf * rc * rc;
+}
+
+static void coul_radial(int kind, int excluded, double r, double beta, double k_rf, double c_rf,
+                        double shift, double *phi, double *B, double *D) {
+    double r2 = r * r, rinv2 = 1.0 / r2;
+    if (kind == ORACLE_COUL_RF) {
+        if (excluded) {
+            *phi = k_rf * r2 - c_rf;
+            *B = -2.0 * k_rf;
+            *D = 0.0;
+        } else {
+            *phi = 1.0 / r + k_rf * r2 - c_rf;
+            *B = rinv2 / r - 2.0 * k_rf;
+            *D = -3.0 * rinv2 * rinv2 / r;
+        }
+        return;
+    }
+    double cb = 2.0 * beta / sqrt(M_PI);
+    double e = exp(-beta * beta * r2);
+    double A = erfc(beta * r) / r;
+    double Be = (A + cb * e) * rinv2;
+    double De = (-3.0 * Be - 2.0 * cb * beta * beta * e) * rinv2;
+    if (excluded) {
+        *phi = -erf(beta * r) / r;
+        *B = Be - rinv2 / r;
+        *D = De + 3.0 * rinv2 * rinv2 / r;
+    } else {
+        *phi = A - shift;
+        *B = Be;
+        *D = De;
+    }
+}
+
+/* Energies and forces with Coulomb options; E[0] = E_LJ, E[1] = E_C
+   (including excluded-pair corrections), *npairs = non-excluded pairs
+   within rc. O(N^2) over i < j (cell list when n > 4096 and the box allows). */
+int oracle_energy_forces_coul(int n, const double *x, const double *q, const int *type, int ntype,
+                              const double *lj, const double *box, double rc, double beta,
+                              const int *excl_off, const int *excl_idx, int kind, double eps_rf,
+                              int flags, double *F, double *E, long long *npairs) {
+    for (int k = 0; k < 3; ++k)
+        if (!(rc < 0.5 * box[k])) return -1;
+    if (kind != ORACLE_COUL_EWALD && kind != ORACLE_COUL_RF) return -3;
+    int nc[3];
+    int use_cells = cell_grid(box, rc, nc) && n > 4096;
+    double k_rf = 0.0, c_rf = 0.0;
+    if (kind == ORACLE_COUL_RF) rf_constants(rc, eps_rf, &k_rf, &c_rf);
+    double shift = (kind == ORACLE_COUL_EWALD && (flags & ORACLE_COUL_SHIFT)) ? erfc(beta * rc) / rc : 0.0;
+    int corr = (flags & ORACLE_COUL_EXCL_CORR) != 0;
+    double rc6 = pow(rc, -6.0), rc12 = rc6 * rc6;
+    int nt = oracle_nthreads();
+    double *Ft = (double *)calloc((size_t)nt * 3 * (size_t)n, sizeof(double));
+    double *Elj = (double *)calloc((size_t)nt, sizeof(double));
+    double *Ec = (double *)calloc((size_t)nt, sizeof(double));
+    long long *Np = (long long *)calloc((size_t)nt, sizeof(long long));
+    int *cell_start = NULL, *cell_atoms = NULL, *atom_cell = NULL;
+    if (use_cells) {
+        int ncell = nc[0] * nc[1] * nc[2];
+        cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
+        cell_atoms = (int *)malloc(sizeof(int) * (size_t)n);
+        atom_cell = (int *)malloc(sizeof(int) * (size_t)n);
+        build_cells(n, x, box, nc, cell_start, cell_atoms, atom_cell);
+    }
+    const double rc2 = rc * rc;
+#pragma omp parallel
+    {
+        int tid = oracle_tid();
+        double *Fl = Ft + (size_t)tid * 3 * (size_t)n;
+        double elj_sum = 0.0, ec_sum = 0.0;
+        long long np = 0;
+        int nb[27];
+#pragma omp for schedule(static)
+        for (int i = 0; i < n; ++i) {
+            int ncc = use_cells ? 27 : 1;
+            if (use_cells) neighbour_cells(atom_cell[i], nc, nb);
+            for (int cc = 0; cc < ncc; ++cc) {
+                int j0 = use_cells ? cell_start[nb[cc]] : i + 1;
+                int j1 = use_cells ? cell_start[nb[cc] + 1] : n;
+                for (int jj = j0; jj < j1; ++jj) {
+                    int j = use_cells ? cell_atoms[jj] : jj;
+                    if (j <= i) continue;
+                    double d[3];
+                    min_image(x + 3 * i, x + 3 * j, box, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!(r2 < rc2)) continue;
+                    int excl = is_excluded(i, j, excl_off, excl_idx);
+                    if (excl && !corr) continue;
+                    double r = sqrt(r2), phi, B, D;
+                    coul_radial(kind, excl, r, beta, k_rf, c_rf, shift, &phi, &B, &D);
+                    double K = ORACLE_COULOMB_F * q[i] * q[j];
+                    double s = K * B;
+                    ec_sum += K * phi;
+                    if (!excl) {
+                        const double *p = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+                        double rinv2 = 1.0 / r2, rinv6 = rinv2 * rinv2 * rinv2;
+                        elj_sum += p[1] * rinv6 * rinv6 - p[0] * rinv6 - (p[1] * rc12 - p[0] * rc6);
+                        s += (12.0 * p[1] * rinv6 * rinv6 - 6.0 * p[0] * rinv6) * rinv2;
+                        np++;
+                    }
+                    for (int k = 0; k < 3; ++k) {
+                        Fl[3 * i + k] += s * d[k];
+                        Fl[3 * j + k] -= s * d[k];
+                    }
+                }
+            }
+        }
+        Elj[tid] = elj_sum;
+        Ec[tid] = ec_sum;
+        Np[tid] = np;
+    }
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) {
+        double v = 0.0;
+        for (int t = 0; t < nt; ++t) v += Ft[(size_t)t * 3 * (size_t)n + k];
+        F[k] = v;
+    }
+    double el = 0.0, ecs = 0.0;
+    long long npt = 0;
+    for (int t = 0; t < nt; ++t) {
+        el += Elj[t];
+        ecs += Ec[t];
+        npt += Np[t];
+    }
+    E[0] = el;
+    E[1] = ecs;
+    if (npairs) *npairs = npt;
+    free(Ft);
+    free(Elj);
+    free(Ec);
+    free(Np);
+    free(cell_start);
+    free(cell_atoms);
+    free(atom_cell);
+    return 0;
+}
+
+/* Adjoint of oracle_energy_forces_coul for g = dL/dF: per pair with
+   u = g_i - g_j and s = f q_i q_j B + s_LJ,
+     dL/dx_i += s u + (s'/r)(u.d) d,  dL/dx_j -= the same,
+     s'/r = f q_i q_j D + (48 C6 / r^10 - 168 C12 / r^16),
+     dL/dq_i += f q_j B (u.d),  dL/dq_j += f q_i B (u.d),
+     dL/dC6 += -6 (u.d) / r^8,  dL/dC12 += 12 (u.d) / r^14 (non-excluded pairs),
+   the LJ gradient split evenly between (t_i, t_j) and (t_j, t_i). */
+int oracle_force_vjp_coul(int n, const double *x, const double *q, const int *type, int ntype,
+                          const double *lj, const double *box, double rc, double beta,
+                          const int *excl_off, const int *excl_idx, int kind, double eps_rf, int flags,
+                          const double *g, double *gx, double *gq, double *glj) {
+    for (int k = 0; k < 3; ++k)
+        if (!(rc < 0.5 * box[k])) return -1;
+    if (kind != ORACLE_COUL_EWALD && kind != ORACLE_COUL_RF) return -3;
+    double k_rf = 0.0, c_rf = 0.0;
+    if (kind == ORACLE_COUL_RF) rf_constants(rc, eps_rf, &k_rf, &c_rf);
+    int corr = (flags & ORACLE_COUL_EXCL_CORR) != 0;
+    size_t nlj = (size_t)ntype * ntype * 2;
+    memset(gx, 0, sizeof(double) * 3 * (size_t)n);
+    memset(gq, 0, sizeof(double) * (size_t)n);
+    memset(glj, 0, sizeof(double) * nlj);
+    const double rc2 = rc * rc;
+    /* plain O(N^2) double loop: the adjoint tests use small systems */
+    for (int i = 0; i < n; ++i) {
+        for (int j = i + 1; j < n; ++j) {
+            double d[3];
+            min_image(x + 3 * i, x + 3 * j, box, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rc2)) continue;
+            int excl = is_excluded(i, j, excl_off, excl_idx);
+            if (excl && !corr) continue;
+            double r = sqrt(r2), phi, B, D;
+            coul_radial(kind, excl, r, beta, k_rf, c_rf, 0.0, &phi, &B, &D);
+            double K = ORACLE_COULOMB_F * q[i] * q[j];
+            double s = K * B, spr = K * D;
+            double rinv2 = 1.0 / r2, rinv6 = rinv2 * rinv2 * rinv2;
+            const double *p = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+            if (!excl) {
+                s += (12.0 * p[1] * rinv6 * rinv6 - 6.0 * p[0] * rinv6) * rinv2;
+                spr += (48.0 * p[0] * rinv6 - 168.0 * p[1] * rinv6 * rinv6) * rinv2 * rinv2;
+            }
+            double u[3], ud = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                u[k] = g[3 * i + k] - g[3 * j + k];
+                ud += u[k] * d[k];
+            }
+            for (int k = 0; k < 3; ++k) {
+                double v = s * u[k] + spr * ud * d[k];
+                gx[3 * i + k] += v;
+                gx[3 * j + k] -= v;
+            }
+            gq[i] += ORACLE_COULOMB_F * q[j] * B * ud;
+            gq[j] += ORACLE_COULOMB_F * q[i] * B * ud;
+            if (!excl) {
+                double d6 = -6.0 * rinv6 * rinv2 * ud, d12 = 12.0 * rinv6 * rinv6 * rinv2 * ud;
+                size_t ab = 2 * ((size_t)type[i] * ntype + type[j]);
+                size_t ba = 2 * ((size_t)type[j] * ntype + type[i]);
+                glj[ab] += 0.5 * d6;
+                glj[ab + 1] += 0.5 * d12;
+                glj[ba] += 0.5 * d6;
+                glj[ba + 1] += 0.5 * d12;
+            }
+        }
+    }
     return 0;
 }

@@ -38,10 +38,27 @@ ADJOINT_MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(ADJOINT_MUTATIONS))
+# mistakes in the Coulomb options (reaction field, shift, exclusion
+# correction), caught by tests/test_oracle_coul.py
+COUL_MUTATIONS = {
+    "rf_quadratic_term_sign": ("*phi = 1.0 / r + k_rf * r2 - c_rf;", "*phi = 1.0 / r - k_rf * r2 - c_rf;"),
+    "rf_force_constant_halved": ("*B = rinv2 / r - 2.0 * k_rf;", "*B = rinv2 / r - k_rf;"),
+    "rf_conducting_constant": ("*k_rf = 1.0 / (2.0 * rc * rc * rc);", "*k_rf = 1.0 / (rc * rc * rc);"),
+    "rf_adjoint_sign": ("*D = -3.0 * rinv2 * rinv2 / r;", "*D = 3.0 * rinv2 * rinv2 / r;"),
+    "excluded_energy_sign": ("*phi = -erf(beta * r) / r;", "*phi = erf(beta * r) / r;"),
+    "excluded_force_keeps_bare_term": ("*B = Be - rinv2 / r;", "*B = Be;"),
+    "ewald_shift_sign": ("*phi = A - shift;", "*phi = A + shift;"),
+}
+
+PIN_FILES = {**{k: "test_oracle_pins.py" for k in MUTATIONS},
+             **{k: "test_oracle_adjoint.py" for k in ADJOINT_MUTATIONS},
+             **{k: "test_oracle_coul.py" for k in COUL_MUTATIONS}}
+
+
+@pytest.mark.parametrize("name", sorted(PIN_FILES))
 def test_pins_catch_mutation(name, tmp_path):
-    old, new = MUTATIONS[name] if name in MUTATIONS else ADJOINT_MUTATIONS[name]
-    pins = "test_oracle_pins.py" if name in MUTATIONS else "test_oracle_adjoint.py"
+    old, new = {**MUTATIONS, **ADJOINT_MUTATIONS, **COUL_MUTATIONS}[name]
+    pins = PIN_FILES[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
     mutated = tmp_path / "oracle_mut.c"
