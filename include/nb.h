@@ -61,7 +61,8 @@ extern "C" {
 #define NB_DEV_NONFINITE 0x04u       /* a coordinate was NaN or infinite */
 #define NB_DEV_STALE_SEARCH 0x08u    /* atoms moved more than (rlist - r)/2 since the search */
 #define NB_DEV_STALE_PRUNE 0x10u     /* atoms moved more than (r_inner - rc)/2 since the prune */
-#define NB_DEV_EXCL_OVERFLOW 0x20u   /* >256 exclusions in one 8-atom cluster, or an index outside [0, n) */
+#define NB_DEV_EXCL_OVERFLOW 0x20u   /* >256 exclusions in one 8-atom cluster, an index outside [0, n),
+                                        or more than 8 excluded pairs per atom on average */
 #define NB_DEV_CLUSTER_OVERFLOW 0x40u /* more than 512 list entries for one i-cluster */
 #define NB_DEV_BAD_TYPE 0x80u         /* an LJ type outside [0, ntype) (treated as type 0) */
 
@@ -276,6 +277,34 @@ int nb_pairlist_export_tiles(nb_pairlist *pl, int *half_id, int *slots, unsigned
  * The events are caller-owned (cudaEvent_t passed as void*).
  */
 int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
+
+/* Coulomb flavours (nb_set_coulomb). The paper's benchmark systems come in
+   Ewald ("PME") and reaction-field ("RF") flavours (§II). */
+#define NB_COUL_EWALD 0 /* real-space Ewald: f qi qj erfc(beta r)/r (default) */
+#define NB_COUL_RF 1    /* reaction field: f qi qj (1/r + k_rf r^2 - c_rf) */
+/* nb_set_coulomb flags */
+#define NB_COUL_SHIFT 0x1u     /* Ewald only: subtract f qi qj erfc(beta rc)/rc from each pair energy */
+#define NB_COUL_EXCL_CORR 0x2u /* add the excluded pairs within rc: Ewald -f qi qj erf(beta r)/r,
+                                  RF f qi qj (k_rf r^2 - c_rf), with their forces */
+
+/*
+ * Coulomb flavour of later nb_forces / nb_backward calls on this pair list
+ * (the default is NB_COUL_EWALD with no flags).
+ *   kind    NB_COUL_EWALD or NB_COUL_RF. For RF, beta in nb_forces is
+ *           ignored; k_rf = (eps_rf - 1) / ((2 eps_rf + 1) rc^3) and
+ *           c_rf = 1/rc + k_rf rc^2 (permittivity 1 inside the cutoff), so
+ *           the pair energy is 0 at rc.
+ *   eps_rf  reaction-field permittivity: 0 means infinity (k_rf = 1/(2 rc^3)),
+ *           otherwise >= 1. Ignored for Ewald.
+ *   flags   NB_COUL_SHIFT (Ewald only) | NB_COUL_EXCL_CORR. The correction
+ *           covers the excluded pairs of the exclusion lists given to the
+ *           last nb_search (the search keeps them as its own slot pairs, up
+ *           to 8 per atom; beyond that NB_DEV_EXCL_OVERFLOW). Excluded pairs
+ *           carry no LJ. The self terms (i = i) are constants the caller adds.
+ * Energies: the corrections are part of E_coul. Errors: NB_ERR_ARG for an
+ * unknown kind or flag, eps_rf in (0, 1), or NB_COUL_SHIFT with RF.
+ */
+int nb_set_coulomb(nb_pairlist *pl, int kind, float eps_rf, unsigned flags);
 
 /*
  * Launch shape of the force kernel for later nb_forces calls on this pair

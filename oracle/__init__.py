@@ -81,6 +81,8 @@ def _load():
             lib.oracle_energy_forces_coul.restype = I
             lib.oracle_force_vjp_coul.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, D, I, P, P, P, P]
             lib.oracle_force_vjp_coul.restype = I
+            lib.oracle_energy_forces_coul_list.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, D, I, P, LL, P, P]
+            lib.oracle_energy_forces_coul_list.restype = I
             _lib = lib
     return _lib
 
@@ -297,3 +299,24 @@ def rf_constants(rc: float, eps_rf: float) -> tuple[float, float]:
     """(k_rf, c_rf) of the reaction field; eps_rf = 0 means infinity."""
     k = 1.0 / (2.0 * rc ** 3) if eps_rf == 0.0 else (eps_rf - 1.0) / ((2.0 * eps_rf + 1.0) * rc ** 3)
     return k, 1.0 / rc + k * rc * rc
+
+
+def energy_forces_coul_pairs(x, q, type_, lj, box, rc, beta, pairs, excl_off=None, excl_idx=None, kind="ewald",
+                             eps_rf=0.0, shift=False, excl_corr=False):
+    """energy_forces_coul over an explicit set of non-excluded pairs ``pairs``
+    [P, 2] (i < j), e.g. the FP32-contract set of ``pairs_f32``; returns
+    ``(F [N,3], E_lj, E_coul)``."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    n = x.shape[0]
+    lj = _f64(lj)
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+    F = np.zeros((n, 3))
+    E = np.zeros(2)
+    rcode = lib.oracle_energy_forces_coul_list(n, _p(x), _p(_f64(q)), _p(_i32(type_)), lj.shape[0], _p(lj),
+                                               _p(_f64(box)), float(rc), float(beta), _p(_i32(excl_off)),
+                                               _p(_i32(excl_idx)), COUL_KINDS[kind], float(eps_rf),
+                                               _coul_flags(shift, excl_corr), _p(pr), pr.shape[0], _p(F), _p(E))
+    if rcode != 0:
+        raise ValueError(f"oracle_energy_forces_coul_list failed with code {rcode}")
+    return F, float(E[0]), float(E[1])

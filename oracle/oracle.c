@@ -838,3 +838,65 @@ int oracle_force_vjp_coul(int n, const double *x, const double *q, const int *ty
     }
     return 0;
 }
+
+/* As oracle_energy_forces_coul, with the set of non-excluded pairs given
+   explicitly (pairs[2k], pairs[2k+1], i < j, npairs of them) instead of
+   decided by r < rc in FP64: a caller that decides the in/out question in
+   another precision (the FP32 contract) passes that set here. Excluded
+   pairs (ORACLE_COUL_EXCL_CORR) still come from the exclusion lists with
+   r < rc. Everything else is FP64 as above. */
+int oracle_energy_forces_coul_list(int n, const double *x, const double *q, const int *type, int ntype,
+                                   const double *lj, const double *box, double rc, double beta,
+                                   const int *excl_off, const int *excl_idx, int kind, double eps_rf,
+                                   int flags, const long long *pairs, long long npairs, double *F,
+                                   double *E) {
+    if (kind != ORACLE_COUL_EWALD && kind != ORACLE_COUL_RF) return -3;
+    double k_rf = 0.0, c_rf = 0.0;
+    if (kind == ORACLE_COUL_RF) rf_constants(rc, eps_rf, &k_rf, &c_rf);
+    double shift = (kind == ORACLE_COUL_EWALD && (flags & ORACLE_COUL_SHIFT)) ? erfc(beta * rc) / rc : 0.0;
+    double rc6 = pow(rc, -6.0), rc12 = rc6 * rc6;
+    memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    double elj = 0.0, ec = 0.0;
+    for (long long k = 0; k < npairs; ++k) {
+        int i = (int)pairs[2 * k], j = (int)pairs[2 * k + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j) return -4;
+        double d[3];
+        min_image(x + 3 * i, x + 3 * j, box, d);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double r = sqrt(r2), phi, B, D;
+        coul_radial(kind, 0, r, beta, k_rf, c_rf, shift, &phi, &B, &D);
+        double K = ORACLE_COULOMB_F * q[i] * q[j];
+        const double *p = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+        double rinv2 = 1.0 / r2, rinv6 = rinv2 * rinv2 * rinv2;
+        double s = K * B + (12.0 * p[1] * rinv6 * rinv6 - 6.0 * p[0] * rinv6) * rinv2;
+        ec += K * phi;
+        elj += p[1] * rinv6 * rinv6 - p[0] * rinv6 - (p[1] * rc12 - p[0] * rc6);
+        for (int c = 0; c < 3; ++c) {
+            F[3 * i + c] += s * d[c];
+            F[3 * j + c] -= s * d[c];
+        }
+    }
+    if ((flags & ORACLE_COUL_EXCL_CORR) && excl_off) {
+        for (int i = 0; i < n; ++i) {
+            for (int e = excl_off[i]; e < excl_off[i + 1]; ++e) {
+                int j = excl_idx[e];
+                if (j <= i || j >= n) continue;
+                double d[3];
+                min_image(x + 3 * i, x + 3 * j, box, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(r2 < rc * rc)) continue;
+                double phi, B, D;
+                coul_radial(kind, 1, sqrt(r2), beta, k_rf, c_rf, 0.0, &phi, &B, &D);
+                double K = ORACLE_COULOMB_F * q[i] * q[j];
+                ec += K * phi;
+                for (int c = 0; c < 3; ++c) {
+                    F[3 * i + c] += K * B * d[c];
+                    F[3 * j + c] -= K * B * d[c];
+                }
+            }
+        }
+    }
+    E[0] = elj;
+    E[1] = ec;
+    return 0;
+}

@@ -55,7 +55,7 @@ void free_buffers(nb_pairlist *pl) {
                     pl->ci_len_inner, pl->gsort,   pl->bsort,          pl->glj_acc,        pl->sys,
                     pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys,       pl->len_hist,
                     pl->len_offsets, pl->len_cursor, pl->ci_order,     pl->vt_slot,        pl->vt_mask,
-                    pl->half_start, pl->half_len,  pl->len_key};
+                    pl->half_start, pl->half_len,  pl->len_key,      pl->excl_pairs};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -117,6 +117,7 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
     size_t cap = (cfg && cfg->capacity_entries) ? cfg->capacity_entries : (size_t)nclus * 200 + 65536;
     if (cap >= (size_t)1 << 31) return fail(NB_ERR_ARG, "%s: capacity_entries %zu >= 2^31", who, cap);
     pl->cap = cap;
+    pl->excl_cap = 8 * (size_t)n + 64;  // excluded pairs (i < j): 8 per atom
     pl->flags = cfg ? cfg->flags : 0u;
     // one extra cluster of slots past the last cluster: slot 8 nc_max pads
     // the last gathered tile of a half and never holds an atom
@@ -139,6 +140,7 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
                 alloc(&pl->len_hist, NB_LEN_BINS, &total) && alloc(&pl->len_offsets, NB_LEN_BINS, &total) &&
                 alloc(&pl->len_cursor, NB_LEN_BINS, &total) && alloc(&pl->ci_order, pl->nc_max, &total) &&
                 alloc(&pl->len_key, pl->nc_max, &total) &&
+                alloc(&pl->excl_pairs, pl->excl_cap, &total) &&
                 alloc(&pl->half_start, 2 * (size_t)pl->nc_max, &total) &&
                 alloc(&pl->half_len, 2 * (size_t)pl->nc_max, &total);
     // gathered tiles pack a slot in 27 bits and index tiles with 32-bit ints;
@@ -318,6 +320,11 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
     const float rl_col = (float)(rle + 1e-3);
     NB_CUDA(nb_launch_search(pl, excl_off, excl_idx, rl2, rl_col, s));
+    // the excluded pairs, kept as slot pairs for the excluded-pair correction
+    // (the caller's lists are read only during this call)
+    NB_CUDA(cudaMemsetAsync(&pl->st->excl_count, 0, sizeof(unsigned), s));
+    if (excl_off) NB_CUDA(nb_launch_excl_list(pl, excl_off, excl_idx, s));
+    pl->has_excl = excl_off != nullptr;
     pl->sorted = 0;
     if (!(pl->flags & NB_FLAG_NO_LIST_SORT)) {
         NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_outer, false, s));
@@ -364,8 +371,10 @@ extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, c
     const float rmax = pl->has_inner ? pl->r_inner : pl->rlist;
     if (!(rc > 0.0f) || !(rc <= rmax))
         return fail(NB_ERR_ARG, "nb_forces: rc = %g must be in (0, %g] (list radius)", rc, rmax);
-    if (!(beta >= 0.0f) || !((double)beta * rc <= 3.2))
+    if (pl->coul_kind == NB_COUL_EWALD && (!(beta >= 0.0f) || !((double)beta * rc <= 3.2)))
         return fail(NB_ERR_ARG, "nb_forces: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
+    if ((pl->coul_flags & NB_COUL_EXCL_CORR) && !pl->has_excl)
+        return fail(NB_ERR_STATE, "nb_forces: NB_COUL_EXCL_CORR needs exclusion lists at the search");
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, energies, s));
@@ -376,6 +385,7 @@ extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, c
         NB_CUDA(nb_launch_force(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->rlist, rc),
                                 stale_bound2(pl->r_inner, rc), s));
     if (pl->ev_stop) NB_CUDA(cudaEventRecord(pl->ev_stop, s));
+    if (pl->coul_flags & NB_COUL_EXCL_CORR) NB_CUDA(nb_launch_excl_corr(pl, rc, beta, energies, s));
     NB_CUDA(nb_launch_scatter(pl, forces, s));
     return ok();
 }
@@ -391,8 +401,10 @@ extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q,
     const float rmax = pl->has_inner ? pl->r_inner : pl->rlist;
     if (!(rc > 0.0f) || !(rc <= rmax))
         return fail(NB_ERR_ARG, "nb_backward: rc = %g must be in (0, %g] (list radius)", rc, rmax);
-    if (!(beta >= 0.0f) || !((double)beta * rc <= 3.2))
+    if (pl->coul_kind == NB_COUL_EWALD && (!(beta >= 0.0f) || !((double)beta * rc <= 3.2)))
         return fail(NB_ERR_ARG, "nb_backward: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
+    if ((pl->coul_flags & NB_COUL_EXCL_CORR) && !pl->has_excl)
+        return fail(NB_ERR_STATE, "nb_backward: NB_COUL_EXCL_CORR needs exclusion lists at the search");
     DeviceGuard gd(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, nullptr, s));
@@ -538,5 +550,19 @@ extern "C" int nb_pairlist_export_tiles(nb_pairlist *pl, int *half_id, int *slot
     NB_CUDA(cudaStreamSynchronize(s));
     *n_out = k;
     if (k > cap) return fail(NB_ERR_CAPACITY, "nb_pairlist_export_tiles: %zu tiles > cap %zu", k, cap);
+    return ok();
+}
+
+extern "C" int nb_set_coulomb(nb_pairlist *pl, int kind, float eps_rf, unsigned flags) {
+    if (!pl) return fail(NB_ERR_ARG, "nb_set_coulomb: NULL pair list");
+    if (kind != NB_COUL_EWALD && kind != NB_COUL_RF) return fail(NB_ERR_ARG, "nb_set_coulomb: kind = %d", kind);
+    if (flags & ~(NB_COUL_SHIFT | NB_COUL_EXCL_CORR)) return fail(NB_ERR_ARG, "nb_set_coulomb: flags = 0x%x", flags);
+    if (kind == NB_COUL_RF && (flags & NB_COUL_SHIFT))
+        return fail(NB_ERR_ARG, "nb_set_coulomb: NB_COUL_SHIFT is for Ewald (the reaction field is 0 at rc)");
+    if (kind == NB_COUL_RF && !(eps_rf == 0.0f || (eps_rf >= 1.0f && std::isfinite(eps_rf))))
+        return fail(NB_ERR_ARG, "nb_set_coulomb: eps_rf = %g must be 0 (infinity) or >= 1", eps_rf);
+    pl->coul_kind = kind;
+    pl->eps_rf = kind == NB_COUL_RF ? eps_rf : 0.0f;
+    pl->coul_flags = flags;
     return ok();
 }

@@ -75,7 +75,7 @@ __device__ __forceinline__ void add_onehot(float (&acc)[NT][2], const int tj, co
     }
 }
 
-template <int NT>
+template <int NT, int COUL>
 __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdParams p) {
     extern __shared__ float4 s_lj[];
     __shared__ int4 s_ent[kBwdWarps][kChunk];
@@ -149,19 +149,19 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdParams p) {
                 float d6, d12;
                 if (mlo) {
                     if (e.y == NB_SHIFT_CENTER)
-                        nb_pair_adj<false>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
+                        nb_pair_adj<false, COUL>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
                                            (mlo & lanebit) != 0u, p.cc, p.k2, bi1, bj, d6, d12);
                     else
-                        nb_pair_adj<true>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], S.x, S.y, S.z,
+                        nb_pair_adj<true, COUL>(xi1, qi1, gi1, xj, qj_f, gj, s_lj[tr1 + tj], S.x, S.y, S.z,
                                           (mlo & lanebit) != 0u, p.cc, p.k2, bi1, bj, d6, d12);
                     add_onehot<NT>(acc1, tj, d6, d12);
                 }
                 if (mhi) {
                     if (e.y == NB_SHIFT_CENTER)
-                        nb_pair_adj<false>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
+                        nb_pair_adj<false, COUL>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
                                            (mhi & lanebit) != 0u, p.cc, p.k2, bi2, bj, d6, d12);
                     else
-                        nb_pair_adj<true>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], S.x, S.y, S.z,
+                        nb_pair_adj<true, COUL>(xi2, qi2, gi2, xj, qj_f, gj, s_lj[tr2 + tj], S.x, S.y, S.z,
                                           (mhi & lanebit) != 0u, p.cc, p.k2, bi2, bj, d6, d12);
                     add_onehot<NT>(acc2, tj, d6, d12);
                 }
@@ -234,19 +234,26 @@ __global__ void k_bwd_scatter(int n, const int *__restrict__ pos, const float4 *
     grad_q[i] = v.w;
 }
 
-template <int NT>
+template <int NT, int COUL>
 cudaError_t launch_bwd(nb_pairlist *pl, const BwdParams &p, cudaStream_t s) {
     const size_t smem = sizeof(float4) * (size_t)p.ntype * p.ntype;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<NT>, kBwdThreads,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<NT, COUL>, kBwdThreads,
                                                                       sizeof(float4) * 16);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
     int blocks = min(pl->num_sms * per_sm, (pl->nc_max + kBwdWarps - 1) / kBwdWarps);
-    k_backward<NT><<<max(blocks, 1), kBwdThreads, smem, s>>>(p);
+    k_backward<NT, COUL><<<max(blocks, 1), kBwdThreads, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int COUL>
+cudaError_t launch_bwd_nt(nb_pairlist *pl, const BwdParams &p, cudaStream_t s) {
+    if (p.ntype == 1) return launch_bwd<1, COUL>(pl, p, s);
+    if (p.ntype == 2) return launch_bwd<2, COUL>(pl, p, s);
+    return launch_bwd<4, COUL>(pl, p, s);
 }
 
 }  // namespace
@@ -273,10 +280,7 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
     p.sys_shift = pl->sys_shift;
     p.clus_sys = pl->clus_sys;
     p.ntype = ntype;
-    p.cc.rc2 = rc * rc;
-    p.cc.beta = beta;
-    p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
-    p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    const int coul = nb_fill_coul(p.cc, rc, beta, pl->coul_kind, pl->eps_rf, pl->coul_flags);
     p.k2 = (float)(2.0 * (2.0 * beta / 1.7724538509055159) * (double)beta * beta);
     p.stale_search2 = stale_search2;
     p.stale_prune2 = stale_prune2;
@@ -284,13 +288,15 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
     cudaError_t e;
     if (pl->has_vtiles && !(pl->flags & NB_FLAG_CLUSTER_TILES))  // gathered tiles after a prune
         e = nb_launch_backward_vt(pl, ntype, ljparams, rc, beta, stale_prune2, s);
-    else if (ntype == 1)
-        e = launch_bwd<1>(pl, p, s);
-    else if (ntype == 2)
-        e = launch_bwd<2>(pl, p, s);
+    else if (coul == NB_COULK_RF)  // the Ewald shift does not change forces
+        e = launch_bwd_nt<NB_COULK_RF>(pl, p, s);
     else
-        e = launch_bwd<4>(pl, p, s);
+        e = launch_bwd_nt<NB_COULK_EWALD>(pl, p, s);
     if (e != cudaSuccess) return e;
+    if ((pl->coul_flags & NB_COUL_EXCL_CORR) && pl->has_excl) {
+        e = nb_launch_excl_corr_adj(pl, rc, beta, s);
+        if (e != cudaSuccess) return e;
+    }
     k_bwd_final<<<1, 32, 0, s>>>(ntype, pl->glj_acc, grad_lj);
     const int n = pl->n_atoms;
     k_bwd_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, pl->pos, pl->bsort, grad_x, grad_q);

@@ -68,7 +68,7 @@ __device__ __forceinline__ int stage_adj(const BvtParams &p, BvtStage &st, int t
     return v;
 }
 
-template <int NT>
+template <int NT, int COUL>
 __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
     extern __shared__ float4 s_lj[];  // (C6, C12, 0, 0)
     __shared__ BvtStage s_st[kBvtWarps][2];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
                     vn = stage_adj(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xi = s_xi[warp][a];
                 float d6, d12;
-                nb_pair_adj<true>(xi, xi.w, s_gi[warp][a], xj, qj_f, gj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
+                nb_pair_adj<true, COUL>(xi, xi.w, s_gi[warp][a], xj, qj_f, gj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
                                   ((mrow >> (8 * a)) & 1u) != 0u, p.cc, p.k2, bi[a], bj, d6, d12);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {  // one-hot by the j atom's type
@@ -197,18 +197,18 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
     }
 }
 
-template <int NT>
+template <int NT, int COUL>
 cudaError_t launch_bvt(nb_pairlist *pl, const BvtParams &p, cudaStream_t s) {
     const size_t smem = sizeof(float4) * (size_t)p.ntype * p.ntype;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_vt<NT>, kBvtThreads,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_vt<NT, COUL>, kBvtThreads,
                                                                       sizeof(float4) * 16);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
     const int blocks = min(pl->num_sms * per_sm, (2 * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
-    k_backward_vt<NT><<<max(blocks, 1), kBvtThreads, smem, s>>>(p);
+    k_backward_vt<NT, COUL><<<max(blocks, 1), kBvtThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -232,14 +232,16 @@ cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljpar
     p.sys_shift = pl->sys_shift;
     p.clus_sys = pl->clus_sys;
     p.ntype = ntype;
-    p.cc.rc2 = rc * rc;
-    p.cc.beta = beta;
-    p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
-    p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    const int coul = nb_fill_coul(p.cc, rc, beta, pl->coul_kind, pl->eps_rf, pl->coul_flags);
     p.k2 = (float)(2.0 * (2.0 * beta / 1.7724538509055159) * (double)beta * beta);
     p.stale_prune2 = stale_prune2;
     p.pad_slot = pl->nc_max * NB_CLUSTER;
-    if (ntype == 1) return launch_bvt<1>(pl, p, s);
-    if (ntype == 2) return launch_bvt<2>(pl, p, s);
-    return launch_bvt<4>(pl, p, s);
+    if (coul == NB_COULK_RF) {  // the Ewald shift does not change forces
+        if (ntype == 1) return launch_bvt<1, NB_COULK_RF>(pl, p, s);
+        if (ntype == 2) return launch_bvt<2, NB_COULK_RF>(pl, p, s);
+        return launch_bvt<4, NB_COULK_RF>(pl, p, s);
+    }
+    if (ntype == 1) return launch_bvt<1, NB_COULK_EWALD>(pl, p, s);
+    if (ntype == 2) return launch_bvt<2, NB_COULK_EWALD>(pl, p, s);
+    return launch_bvt<4, NB_COULK_EWALD>(pl, p, s);
 }

@@ -142,7 +142,7 @@ __device__ __forceinline__ void flush_energies(double ec, double elj, int lane, 
 // THREADS per block and CHUNK list entries staged per warp are launch
 // shapes the autotuner chooses among (nb_set_force_shape); both keep the
 // register cap at 64 (4 blocks of 256 or 8 of 128 threads per SM).
-template <bool ENERGY, bool COUNT, int THREADS, int CHUNK>
+template <bool ENERGY, bool COUNT, int THREADS, int CHUNK, int COUL>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p) {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ float4 s_lj[];  // ntype^2 entries (C6, C12, E shift, 0)
@@ -226,15 +226,15 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
                 float ect = 0.0f, eljt = 0.0f;
                 int c1 = 0, c2 = 0;
                 if (sidx == NB_SHIFT_CENTER) {
-                    if (mlo) c1 = nb_pair<false, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
+                    if (mlo) c1 = nb_pair<false, ENERGY, COUL>(xi1, qi1, xj, s_lj[tr1 + tj], 0.f, 0.f, 0.f,
                                                          (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
-                    if (mhi) c2 = nb_pair<false, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
+                    if (mhi) c2 = nb_pair<false, ENERGY, COUL>(xi2, qi2, xj, s_lj[tr2 + tj], 0.f, 0.f, 0.f,
                                                          (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
                 } else {
                     const float4 S = shift[sidx];
-                    if (mlo) c1 = nb_pair<true, ENERGY>(xi1, qi1, xj, s_lj[tr1 + tj], S.x, S.y, S.z,
+                    if (mlo) c1 = nb_pair<true, ENERGY, COUL>(xi1, qi1, xj, s_lj[tr1 + tj], S.x, S.y, S.z,
                                                         (mlo & lanebit) != 0u, p.cc, fi1, fj, ect, eljt);
-                    if (mhi) c2 = nb_pair<true, ENERGY>(xi2, qi2, xj, s_lj[tr2 + tj], S.x, S.y, S.z,
+                    if (mhi) c2 = nb_pair<true, ENERGY, COUL>(xi2, qi2, xj, s_lj[tr2 + tj], S.x, S.y, S.z,
                                                         (mhi & lanebit) != 0u, p.cc, fi2, fj, ect, eljt);
                 }
                 if (COUNT) cnt += c1 + c2;
@@ -303,13 +303,20 @@ __global__ void k_scatter(int n, const int *__restrict__ pos, const float4 *__re
 
 // kernel variants: [energy][count][threads 128/256][chunk 8/16]
 using ForceFn = void (*)(ForceParams);
-template <bool E, bool C>
-ForceFn pick(int threads, int chunk) {
-    if (threads == 128) return chunk == 8 ? k_force<E, C, 128, 8> : k_force<E, C, 128, 16>;
-    return chunk == 8 ? k_force<E, C, 256, 8> : k_force<E, C, 256, 16>;
+template <bool E, bool C, int K>
+ForceFn pick_shape(int threads, int chunk) {
+    if (threads == 128) return chunk == 8 ? k_force<E, C, 128, 8, K> : k_force<E, C, 128, 16, K>;
+    return chunk == 8 ? k_force<E, C, 256, 8, K> : k_force<E, C, 256, 16, K>;
 }
 
-int g_blocks_per_sm[2][2][2][2] = {};
+template <bool E, bool C>
+ForceFn pick(int threads, int chunk, int coul) {
+    if (coul == NB_COULK_RF) return pick_shape<E, C, NB_COULK_RF>(threads, chunk);
+    if (coul == NB_COULK_EWALD_SHIFT) return pick_shape<E, C, NB_COULK_EWALD_SHIFT>(threads, chunk);
+    return pick_shape<E, C, NB_COULK_EWALD>(threads, chunk);
+}
+
+int g_blocks_per_sm[3][2][2][2][2] = {};
 
 }  // namespace
 
@@ -358,10 +365,7 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     const double rc6 = 1.0 / ((double)rc * rc * rc * rc * rc * rc);
     p.rc6inv = (float)rc6;
     p.rc12inv = (float)(rc6 * rc6);
-    p.cc.rc2 = rc * rc;
-    p.cc.beta = beta;
-    p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
-    p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    const int coul = nb_fill_coul(p.cc, rc, beta, pl->coul_kind, pl->eps_rf, pl->coul_flags);
     p.stale_search2 = stale_search2;
     p.stale_prune2 = stale_prune2;
     p.has_inner = pl->has_inner;
@@ -369,10 +373,10 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     const int c = (pl->flags & NB_FLAG_COUNT_PAIRS) ? 1 : 0;
     const int threads = pl->force_threads == 128 ? 128 : 256;
     const int chunk = pl->force_chunk == 8 ? 8 : 16;
-    ForceFn fn = e ? (c ? pick<true, true>(threads, chunk) : pick<true, false>(threads, chunk))
-                   : (c ? pick<false, true>(threads, chunk) : pick<false, false>(threads, chunk));
+    ForceFn fn = e ? (c ? pick<true, true>(threads, chunk, coul) : pick<true, false>(threads, chunk, coul))
+                   : (c ? pick<false, true>(threads, chunk, coul) : pick<false, false>(threads, chunk, coul));
     const size_t smem = sizeof(float4) * (size_t)ntype * ntype;
-    int &per_sm = g_blocks_per_sm[e][c][threads == 128][chunk == 8];
+    int &per_sm = g_blocks_per_sm[coul][e][c][threads == 128][chunk == 8];
     if (per_sm == 0) {
         // occupancy at the largest LJ table, so that the grid never exceeds residency
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -95,7 +95,7 @@ __device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, int t
 // while group g is computed.
 // 768 / THREADS resident CTAs per SM leave 80 registers per thread: enough
 // to keep the 4 rows' positions, LJ rows and forces in registers.
-template <bool ENERGY, bool COUNT, int THREADS>
+template <bool ENERGY, bool COUNT, int THREADS, int COUL>
 __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p) {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ float4 s_lj[];
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
                 if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
                     vn = stage_group(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xi = xr[a];
-                const int c1 = nb_pair<true, ENERGY>(xi, xi.w, xj, s_lj[trr[a] + tj], S.x, S.y, S.z,
+                const int c1 = nb_pair<true, ENERGY, COUL>(xi, xi.w, xj, s_lj[trr[a] + tj], S.x, S.y, S.z,
                                                      ((mrow >> (8 * a)) & 1u) != 0u, p.cc, fi[a], fj, ec, elj);
                 if (COUNT) cnt += c1;
             }
@@ -219,16 +219,23 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
 }
 
 using VtFn = void (*)(VtParams);
+template <bool E, bool C, int K>
+VtFn pick_vt_shape(int threads) {
+    return threads == 128 ? k_force_vt<E, C, 128, K> : k_force_vt<E, C, 256, K>;
+}
+
 template <bool E, bool C>
-VtFn pick_vt(int threads) {
-    return threads == 128 ? k_force_vt<E, C, 128> : k_force_vt<E, C, 256>;
+VtFn pick_vt(int threads, int coul) {
+    if (coul == NB_COULK_RF) return pick_vt_shape<E, C, NB_COULK_RF>(threads);
+    if (coul == NB_COULK_EWALD_SHIFT) return pick_vt_shape<E, C, NB_COULK_EWALD_SHIFT>(threads);
+    return pick_vt_shape<E, C, NB_COULK_EWALD>(threads);
 }
 
 struct Occ {
     size_t smem;
     int per_sm;
 };
-Occ g_vt_occ[2][2][2] = {};
+Occ g_vt_occ[3][2][2][2] = {};
 
 }  // namespace
 
@@ -252,19 +259,16 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     const double rc6 = 1.0 / ((double)rc * rc * rc * rc * rc * rc);
     p.rc6inv = (float)rc6;
     p.rc12inv = (float)(rc6 * rc6);
-    p.cc.rc2 = rc * rc;
-    p.cc.beta = beta;
-    p.cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
-    p.cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    const int coul = nb_fill_coul(p.cc, rc, beta, pl->coul_kind, pl->eps_rf, pl->coul_flags);
     p.stale_prune2 = stale_prune2;
     p.pad_slot = pl->nc_max * NB_CLUSTER;
     const int e = energies ? 1 : 0;
     const int c = (pl->flags & NB_FLAG_COUNT_PAIRS) ? 1 : 0;
     const int threads = pl->force_threads == 128 ? 128 : 256;
-    VtFn fn = e ? (c ? pick_vt<true, true>(threads) : pick_vt<true, false>(threads))
-                : (c ? pick_vt<false, true>(threads) : pick_vt<false, false>(threads));
+    VtFn fn = e ? (c ? pick_vt<true, true>(threads, coul) : pick_vt<true, false>(threads, coul))
+                : (c ? pick_vt<false, true>(threads, coul) : pick_vt<false, false>(threads, coul));
     const size_t smem = sizeof(float4) * (size_t)ntype * ntype;
-    Occ &occ = g_vt_occ[e][c][threads == 128];
+    Occ &occ = g_vt_occ[coul][e][c][threads == 128];
     if (occ.per_sm == 0 || occ.smem != smem) {  // resident CTAs for this LJ table size
         int n = 0;
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)fn, threads, smem);

@@ -29,6 +29,7 @@ struct nb_dev_state {
     unsigned last_d2_search;       // the same values of the last completed call
     unsigned last_d2_prune;
     unsigned long long npairs;     // in-range pairs counted by the last force call
+    unsigned excl_count;           // excluded pairs recorded by the last search
 };
 
 // Per-system parameters (one entry per independent box). A single-system
@@ -61,6 +62,10 @@ struct nb_pairlist {
     float r_inner;
     int ncx, ncy, ncol;
     unsigned flags;                 // nb_config.flags given at creation
+    int coul_kind;                  // NB_COUL_EWALD / NB_COUL_RF (nb_set_coulomb)
+    float eps_rf;
+    unsigned coul_flags;            // NB_COUL_SHIFT | NB_COUL_EXCL_CORR
+    int has_excl;                   // the last search had exclusion lists
     int force_threads;              // force kernel launch shape (0 = default), see nb_set_force_shape
     int force_chunk;
     int force_blocks_per_sm;
@@ -107,6 +112,8 @@ struct nb_pairlist {
     unsigned *vt_mask;    // [2 cap] 4 x 8 in-range bits per gathered tile
     int *half_start;      // [2 nc_max] first gathered tile of each half i-cluster
     int *half_len;        // [2 nc_max]
+    int2 *excl_pairs;     // [excl_cap] excluded pairs (slot_i, slot_j), i < j, of the last search
+    size_t excl_cap;
     int has_vtiles;       // the last prune built gathered tiles
     float4 *gsort;        // [8 nc_max] dL/dF in cluster order (adjoint)
     float4 *bsort;        // [8 nc_max] adjoint accumulators (dL/dx, dL/dq)
@@ -166,6 +173,12 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
 cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, bool hist_ready, cudaStream_t s);
 // Clears the list-length histogram ahead of a prune that fills it.
 cudaError_t nb_clear_len_hist(nb_pairlist *pl, cudaStream_t s);
+// Records the excluded pairs of the caller's exclusion lists as slot pairs
+// (after the grid sort, during the search call).
+cudaError_t nb_launch_excl_list(nb_pairlist *pl, const int *excl_off, const int *excl_idx, cudaStream_t s);
+// Excluded-pair correction (NB_COUL_EXCL_CORR): forces and E_coul, and its adjoint.
+cudaError_t nb_launch_excl_corr(nb_pairlist *pl, float rc, float beta, double *energies, cudaStream_t s);
+cudaError_t nb_launch_excl_corr_adj(nb_pairlist *pl, float rc, float beta, cudaStream_t s);
 cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
                                   float stale_prune2, cudaStream_t s);
 cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,

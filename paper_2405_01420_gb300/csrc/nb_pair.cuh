@@ -17,6 +17,8 @@
 // factor free of approximation bias beyond FP32 rounding.
 #pragma once
 
+#include <cmath>
+
 #include "nb_internal.cuh"
 
 #define NB_ERFCX_P1 8.430113792e-01f
@@ -104,18 +106,53 @@ __device__ __forceinline__ float nb_erfcx(float x) {
     return p * nb_recip(q);
 }
 
+// Coulomb flavour of the pair kernels (their COUL template parameter):
+//   NB_COULK_EWALD        f qi qj erfc(beta r)/r
+//   NB_COULK_EWALD_SHIFT  the same minus f qi qj erfc(beta rc)/rc (energies only)
+//   NB_COULK_RF           reaction field f qi qj (1/r + k_rf r^2 - c_rf)
+#define NB_COULK_EWALD 0
+#define NB_COULK_EWALD_SHIFT 1
+#define NB_COULK_RF 2
+
 // Constants of one force call, shared by all pairs.
 struct nb_coul {
     float rc2;   // fl(rc * rc): a pair counts iff r2 < rc2
     float beta;  // Ewald splitting parameter
     float kexp;  // -beta^2 log2(e): exp(-beta^2 r^2) = 2^(kexp r^2)
     float c2b;   // 2 beta / sqrt(pi)
+    float sh;    // erfc(beta rc)/rc (Ewald shift)
+    float krf;   // k_rf (reaction field)
+    float crf;   // c_rf = 1/rc + k_rf rc^2
+    // k_rf - krf and c_rf - crf: the energy adds these residuals, since
+    // f sum q q c_rf cancels to ~1/60 of itself in water and the FP32
+    // rounding of the constants alone biases E_coul by ~1e-6
+    float krf_lo, crf_lo;
 };
+
+// Fills the constants for cutoff rc, Ewald beta and the pair list's
+// Coulomb setting (kind NB_COUL_*, eps_rf with 0 meaning infinity, flags
+// NB_COUL_SHIFT / NB_COUL_EXCL_CORR); returns the NB_COULK_* mode.
+inline int nb_fill_coul(nb_coul &cc, float rc, float beta, int kind, float eps_rf, unsigned flags) {
+    cc.rc2 = rc * rc;
+    cc.beta = beta;
+    cc.kexp = (float)(-(double)beta * beta * 1.4426950408889634);
+    cc.c2b = (float)(2.0 * beta / 1.7724538509055159);
+    cc.sh = (float)(std::erfc((double)beta * rc) / rc);
+    const double rc3 = (double)rc * rc * rc;
+    const double krf = eps_rf == 0.0f ? 1.0 / (2.0 * rc3) : ((double)eps_rf - 1.0) / ((2.0 * eps_rf + 1.0) * rc3);
+    const double crf = 1.0 / rc + krf * (double)rc * rc;
+    cc.krf = (float)krf;
+    cc.crf = (float)crf;
+    cc.krf_lo = (float)(krf - (double)cc.krf);
+    cc.crf_lo = (float)(crf - (double)cc.crf);
+    if (kind == NB_COUL_RF) return NB_COULK_RF;
+    return (flags & NB_COUL_SHIFT) ? NB_COULK_EWALD_SHIFT : NB_COULK_EWALD;
+}
 
 // Accumulates one pair into fi (+) and fj (-). in_mask: the list mask bit.
 // SHIFT: add the periodic shift S to (y_a - y_b). ENERGY: also accumulate
 // the pair energies. Returns 1 if the pair was within rc and counted.
-template <bool SHIFT, bool ENERGY>
+template <bool SHIFT, bool ENERGY, int COUL = NB_COULK_EWALD>
 __device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const float4 xj,
                                        const float4 lj, const float Sx, const float Sy,
                                        const float Sz, const bool in_mask, const nb_coul &cc,
@@ -141,11 +178,18 @@ __device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const 
     const float v6 = lj.x * rinv6;           // C6 / r^6
     const float v12 = lj.y * rinv6 * rinv6;  // C12 / r^12
     const float slj = fmaf(12.0f, v12, -6.0f * v6) * rinv2;
-    const float r = r2 * rinv;
-    const float ex = nb_exp2(cc.kexp * r2);          // exp(-beta^2 r^2)
-    const float a = ex * nb_erfcx(cc.beta * r) * rinv;  // erfc(beta r) / r
-    const float qq = qi_f * xj.w;                    // f q_i q_j
-    float s = fmaf(qq * fmaf(cc.c2b, ex, a), rinv2, slj);
+    float s, a = 0.0f, qq;  // qq = f q_i q_j
+    if (COUL == NB_COULK_RF) {
+        // f q q (1/r + k_rf r^2 - c_rf); s = f q q (1/r^3 - 2 k_rf)
+        qq = qi_f * xj.w;
+        s = fmaf(qq, fmaf(rinv, rinv2, -2.0f * cc.krf), slj);
+    } else {
+        const float r = r2 * rinv;
+        const float ex = nb_exp2(cc.kexp * r2);  // exp(-beta^2 r^2)
+        a = ex * nb_erfcx(cc.beta * r) * rinv;   // erfc(beta r) / r
+        qq = qi_f * xj.w;
+        s = fmaf(qq * fmaf(cc.c2b, ex, a), rinv2, slj);
+    }
     s = in ? s : 0.0f;
     fi.x = fmaf(s, dx, fi.x);
     fi.y = fmaf(s, dy, fi.y);
@@ -154,7 +198,11 @@ __device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const 
     fj.y = fmaf(-s, dy, fj.y);
     fj.z = fmaf(-s, dz, fj.z);
     if (ENERGY) {
-        const float e_c = qq * a;
+        // RF: the residual term enters through the FMA's addend, against the
+        // unrounded product (added to a rounded sum it would be absorbed)
+        const float e_c = COUL == NB_COULK_RF
+                              ? fmaf(qq, rinv + fmaf(cc.krf, r2, -cc.crf), qq * fmaf(cc.krf_lo, r2, -cc.crf_lo))
+                          : COUL == NB_COULK_EWALD_SHIFT ? qq * (a - cc.sh) : qq * a;
         const float e_lj = v12 - v6 - lj.z;
         ec += in ? e_c : 0.0f;
         elj += in ? e_lj : 0.0f;
@@ -169,7 +217,7 @@ __device__ __forceinline__ int nb_pair(const float4 xi, const float qi_f, const 
 //   dL/dC6 = -6 r^-8 (u.d),          dL/dC12 = 12 r^-14 (u.d)
 // bi/bj accumulate (dL/dx, dL/dq); d6/d12 return the pair's dL/dC6 and
 // dL/dC12 (0 when the pair does not count). k2 = 2 (2 beta/sqrt(pi)) beta^2.
-template <bool SHIFT>
+template <bool SHIFT, int COUL = NB_COULK_EWALD>
 __device__ __forceinline__ void nb_pair_adj(const float4 xi, const float qi_f, const float4 gi, const float4 xj,
                                             const float qj_f, const float4 gj, const float4 lj, const float Sx,
                                             const float Sy, const float Sz, const bool in_mask, const nb_coul &cc,
@@ -188,14 +236,22 @@ __device__ __forceinline__ void nb_pair_adj(const float4 xi, const float qi_f, c
     const float rinv6 = rinv2 * rinv2 * rinv2;
     const float v6 = lj.x * rinv6, v12 = lj.y * rinv6 * rinv6;
     const float slj = fmaf(12.0f, v12, -6.0f * v6) * rinv2;
-    const float r = r2 * rinv;
-    const float ex = nb_exp2(cc.kexp * r2);
-    const float a = ex * nb_erfcx(cc.beta * r) * rinv;  // erfc(beta r)/r
-    const float Bc = fmaf(cc.c2b, ex, a) * rinv2;        // B
     const float qq = qi_f * xj.w;                          // f q_a q_b
+    float Bc, cpr;  // B, and r^2 (1/r) dB/dr times f q_a q_b
+    if (COUL == NB_COULK_RF) {
+        const float rinv3 = rinv * rinv2;
+        Bc = rinv3 - 2.0f * cc.krf;  // 1/r^3 - 2 k_rf
+        cpr = -3.0f * qq * rinv3;    // (1/r) dB/dr = -3/r^5
+    } else {
+        const float r = r2 * rinv;
+        const float ex = nb_exp2(cc.kexp * r2);
+        const float a = ex * nb_erfcx(cc.beta * r) * rinv;  // erfc(beta r)/r
+        Bc = fmaf(cc.c2b, ex, a) * rinv2;
+        cpr = fmaf(-3.0f, qq * Bc, -k2 * qq * ex);
+    }
     const float sC = qq * Bc;
     const float s = sC + slj;
-    const float spr = rinv2 * fmaf(rinv2, fmaf(48.0f, v6, -168.0f * v12), fmaf(-3.0f, sC, -k2 * qq * ex));
+    const float spr = rinv2 * fmaf(rinv2, fmaf(48.0f, v6, -168.0f * v12), cpr);
     const float ux = gi.x - gj.x, uy = gi.y - gj.y, uz = gi.z - gj.z;
     const float ud = fmaf(ux, dx, fmaf(uy, dy, uz * dz));
     // Pairs that do not count can carry inf/NaN in their pair terms (r2 = 0

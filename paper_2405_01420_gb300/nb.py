@@ -41,6 +41,10 @@ NB_LIST_INNER = 1
 NB_FLAG_COUNT_PAIRS = 0x1
 NB_FLAG_NO_LIST_SORT = 0x2
 NB_FLAG_CLUSTER_TILES = 0x4
+NB_COUL_EWALD = 0
+NB_COUL_RF = 1
+NB_COUL_SHIFT = 0x1
+NB_COUL_EXCL_CORR = 0x2
 
 
 class NBError(RuntimeError):
@@ -98,6 +102,7 @@ SIGNATURES = {
     "nb_set_timing_events": (_I, [_P, _P, _P]),
     "nb_set_force_shape": (_I, [_P, _I, _I, _I]),
     "nb_pairlist_export_tiles": (_I, [_P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P]),
+    "nb_set_coulomb": (_I, [_P, _I, ctypes.c_float, ctypes.c_uint]),
     "nb_backward": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P, _P]),
     "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
                                ctypes.POINTER(ctypes.c_uint), _P]),
@@ -295,6 +300,11 @@ def nb_pairlist_export_tiles(pl, stream=None) -> dict:
     return {"half_id": hid[:k], "slots": slots[:k], "masks": masks[:k]}
 
 
+def nb_set_coulomb(pl, kind: int = NB_COUL_EWALD, eps_rf: float = 0.0, flags: int = 0) -> None:
+    """Coulomb flavour of later nb_forces / nb_backward calls (NB_COUL_EWALD or NB_COUL_RF)."""
+    _check(load_library().nb_set_coulomb(pl, int(kind), float(eps_rf), int(flags)))
+
+
 def nb_set_force_shape(pl, threads: int = 0, chunk: int = 0, blocks_per_sm: int = 0) -> None:
     _check(load_library().nb_set_force_shape(pl, int(threads), int(chunk), int(blocks_per_sm)))
 
@@ -355,6 +365,13 @@ class Pairlist:
 
     def export_tiles(self, stream=None) -> dict:
         return nb_pairlist_export_tiles(self.handle, stream)
+
+    def set_coulomb(self, kind: str = "ewald", eps_rf: float = 0.0, shift: bool = False,
+                    excl_corr: bool = False) -> None:
+        """kind "ewald" or "rf" (reaction field, eps_rf = 0 meaning infinity);
+        shift (Ewald) and excl_corr (excluded-pair correction) as in nb.h."""
+        flags = (NB_COUL_SHIFT if shift else 0) | (NB_COUL_EXCL_CORR if excl_corr else 0)
+        nb_set_coulomb(self.handle, {"ewald": NB_COUL_EWALD, "rf": NB_COUL_RF}[kind], eps_rf, flags)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

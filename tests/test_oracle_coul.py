@@ -92,6 +92,21 @@ def test_rf_at_eps_one_is_shifted_bare_coulomb(box):
     assert np.abs(Fr - Fe).max() <= 1e-9 * np.abs(Fe).max()
 
 
+@pytest.mark.parametrize("opts", [dict(kind="rf", eps_rf=78.5, excl_corr=True), dict(kind="ewald", shift=True),
+                                  dict(kind="ewald", excl_corr=True)])
+def test_explicit_pair_set_equals_the_cutoff_form(box, opts):
+    """Given the FP64 brute-force pair set, the explicit-set form equals the cutoff form."""
+    b = box
+    pairs = oracle.pairs_f64(b.coords, b.box, 0.9, b.excl_off, b.excl_idx)
+    F1, el1, ec1, n1 = run(b, **dict(opts))
+    F2, el2, ec2 = oracle.energy_forces_coul_pairs(b.coords, b.q, b.type, b.ljparams, b.box, 0.9, 3.47, pairs,
+                                                   b.excl_off, b.excl_idx, **opts)
+    assert len(pairs) == n1
+    assert el2 == pytest.approx(el1, rel=1e-12)
+    assert ec2 == pytest.approx(ec1, rel=1e-11)
+    assert np.abs(F2 - F1).max() <= 1e-9 * np.abs(F1).max()
+
+
 # ---------------------------------------------------------------- reaction field at the cutoff
 
 @pytest.mark.parametrize("eps_rf", [0.0, 78.5, 4.0])
