@@ -435,7 +435,7 @@ def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
     assert counter.status() == 0
     counter.close()
 
-    from paper_2405_01420_gb300.tune import tune_batch_prune, tune_force_shape
+    from paper_2405_01420_gb300.tune import tune_batch_prune, tune_force_shape, tune_tile_form
     pl = nb.Pairlist.batch(off, bx)
     F = torch.empty((pl.n_atoms, 3), dtype=torch.float32, device=dev)
     E = torch.empty(2 * pl.n_systems, dtype=torch.float64, device=dev)
@@ -447,6 +447,11 @@ def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
     use_prune, prune_times = tune_batch_prune(lambda: pl.search(xd, None, rlist, eod, eid),
                                               lambda: pl.prune(xd, rc),
                                               lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
+    tile_form, tile_times = "cluster", None
+    if use_prune:  # the tile form matters only after a prune
+        pl.search(xd, None, rlist, eod, eid)
+        pl.prune(xd, rc)
+        tile_form, tile_times = tune_tile_form(pl, lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
@@ -513,7 +518,7 @@ def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
             "plain_launches_p50_ms": p50, "plain_launches_p99_ms": p99, "plain_pairs_per_s": pairs / (p50 / 1e3),
             "speedup_p50": p50 / g50, "graph_reps": reps, "plain_reps": plain_reps,
             "tuned": {"force_shape": list(shape), "prune_before_forces": bool(use_prune),
-                      "prune_choice_ms": prune_times}}
+                      "prune_choice_ms": prune_times, "tile_form": tile_form, "tile_form_ms": tile_times}}
 
 
 def run_ours(args, rank, world, local):
@@ -569,12 +574,13 @@ def run_ours(args, rank, world, local):
     counter.close()
     pairs_per_step = float(sum(pairs))
 
-    # autotune the force kernel's launch shape on this workload (untimed)
-    from paper_2405_01420_gb300.tune import tune_force_shape
+    # autotune the force kernel's launch shape and tile form on this workload (untimed)
+    from paper_2405_01420_gb300.tune import tune_force_shape, tune_tile_form
     restart()
     eng.compute(frames_d[0], q, typ, lj, forces, energies[0])
-    shape, shape_times = tune_force_shape(
-        eng.pl, lambda: nb.nb_forces(eng.pl.handle, frames_d[0], q, typ, lj, RC, beta, forces, energies[0]))
+    force_call = lambda: nb.nb_forces(eng.pl.handle, frames_d[0], q, typ, lj, RC, beta, forces, energies[0])
+    shape, shape_times = tune_force_shape(eng.pl, force_call)
+    tile_form, tile_times = tune_tile_form(eng.pl, force_call)
 
     for _ in range(args.warmup):
         one_step(lambda i: frames_d[i])
@@ -682,7 +688,8 @@ def run_ours(args, rank, world, local):
         "us_per_eval": 1e3 * ms_step / args.evals,
         "pairs_per_eval": pairs_per_eval,
         "searches_per_step": searches, "prunes_per_step": prunes,
-        "force_shape": {"threads": shape[0], "chunk": shape[1], "blocks_per_sm": shape[2], "tuned_ms": shape_times},
+        "force_shape": {"threads": shape[0], "chunk": shape[1], "blocks_per_sm": shape[2], "tuned_ms": shape_times,
+                        "tile_form": tile_form, "tile_form_ms": tile_times},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

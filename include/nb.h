@@ -278,6 +278,15 @@ int nb_pairlist_export_tiles(nb_pairlist *pl, int *half_id, int *slots, unsigned
  */
 int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
 
+/*
+ * Replace the pair list's NB_FLAG_* flags (set at creation through
+ * nb_config.flags). Each flag takes effect at the next call that reads it:
+ * NB_FLAG_COUNT_PAIRS and NB_FLAG_CLUSTER_TILES at nb_forces / nb_backward,
+ * NB_FLAG_NO_LIST_SORT at nb_search / nb_prune. Used by the autotuner to
+ * choose the tile form. Errors: NB_ERR_ARG for an unknown flag.
+ */
+int nb_set_flags(nb_pairlist *pl, unsigned flags);
+
 /* Coulomb flavours (nb_set_coulomb). The paper's benchmark systems come in
    Ewald ("PME") and reaction-field ("RF") flavours (§II). */
 #define NB_COUL_EWALD 0 /* real-space Ewald: f qi qj erfc(beta r)/r (default) */

@@ -566,3 +566,11 @@ extern "C" int nb_set_coulomb(nb_pairlist *pl, int kind, float eps_rf, unsigned 
     pl->coul_flags = flags;
     return ok();
 }
+
+extern "C" int nb_set_flags(nb_pairlist *pl, unsigned flags) {
+    if (!pl) return fail(NB_ERR_ARG, "nb_set_flags: NULL pair list");
+    if (flags & ~(unsigned)(NB_FLAG_COUNT_PAIRS | NB_FLAG_NO_LIST_SORT | NB_FLAG_CLUSTER_TILES))
+        return fail(NB_ERR_ARG, "nb_set_flags: unknown flags 0x%x", flags);
+    pl->flags = flags;
+    return ok();
+}

@@ -36,24 +36,27 @@ struct PruneParams {
     float stale_search2;
 };
 
-constexpr int kStage = 512;  // ring of staged j atoms per warp and half (>= 32 * 8 + 8)
+constexpr int kStage = 256;  // ring of staged j atoms per warp and half (>= 31 + 16 * 8)
 
-// Rows (a = 0..3) of column b of a 4 x 8 mask (bit a*8 + b) as 4 bits.
-__device__ __forceinline__ unsigned column_rows(unsigned m, int b) {
-    return ((m >> b) & 1u) | ((m >> (7 + b)) & 2u) | ((m >> (14 + b)) & 4u) | ((m >> (21 + b)) & 8u);
-}
-
-// Writes one gathered tile from the 8 staged atoms at ring position head.
-__device__ __forceinline__ void flush_tile(const int *ring_slot, const unsigned char *ring_rows, int head, int vt,
-                                           int lane, const PruneParams &p) {
-    const int idx = (head + (lane & 7)) & (kStage - 1);
+// Writes ntiles (<= 4) gathered tiles from the 8 ntiles staged atoms at ring
+// position head: lane l takes atom l, i.e. column p = l & 7 of tile l >> 3.
+// Each staged atom keeps its entry's 4 x 8 mask word of the half; its column
+// b in that word is the low 3 bits of its slot, so its rows (bits b, 8 + b,
+// 16 + b, 24 + b) shifted to column p are its part of the tile's mask, and
+// the 8 lanes of a tile OR theirs together.
+__device__ __forceinline__ void flush_tiles(const int *ring_slot, const unsigned *ring_mask, int head, int vt,
+                                            int ntiles, int lane, const PruneParams &p) {
+    const int idx = (head + lane) & (kStage - 1);
     const int v = ring_slot[idx];
-    const unsigned r = lane < 8 ? ring_rows[idx] : 0u;
-    if (lane < 8) p.vt_slot[8 * (size_t)vt + lane] = v;
-    unsigned m = 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) m |= (__ballot_sync(0xffffffffu, (r >> a) & 1u) & 0xffu) << (8 * a);
-    if (lane == 0) p.vt_mask[vt] = m;
+    const int pcol = lane & 7, t = lane >> 3;
+    unsigned c = ((ring_mask[idx] >> ((unsigned)v & 7u)) & 0x01010101u) << pcol;
+    c |= __shfl_xor_sync(0xffffffffu, c, 1);
+    c |= __shfl_xor_sync(0xffffffffu, c, 2);
+    c |= __shfl_xor_sync(0xffffffffu, c, 4);
+    if (t < ntiles) {
+        p.vt_slot[8 * (size_t)vt + lane] = v;
+        if (pcol == 0) p.vt_mask[vt + t] = c;
+    }
 }
 
 template <bool SHIFT>
@@ -94,7 +97,7 @@ template <bool TILES>
 __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
     __shared__ int4 s_ent[kPruneThreads / 32][32];
     __shared__ int s_rslot[kPruneThreads / 32][2][kStage];
-    __shared__ unsigned char s_rrows[kPruneThreads / 32][2][kStage];
+    __shared__ unsigned s_rmask[kPruneThreads / 32][2][kStage];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // displacement since the search must leave the outer list complete at r_inner
         const unsigned ds = p.st->cur_d2_search;
@@ -151,47 +154,61 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
             // Gather, per half, the j atoms in range of any of its 4 rows.
 #pragma unroll
             for (int h = 0; h < (TILES ? 2 : 0); ++h) {
-                const unsigned m = lane < cnt ? (h ? mine.y : mine.x) : 0u;
-                unsigned col = (m | (m >> 8) | (m >> 16) | (m >> 24)) & 0xffu;
-                const int c = __popc(col);
-                int incl = c;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
+                // in entry order (atoms of one entry stay together, so a tile
+                // draws on few clusters), 16 entries at a time: an exclusive
+                // scan of the per-entry counts places each lane's atoms; once
+                // 32 atoms are staged, 4 full tiles leave together
+                const unsigned mh = lane < cnt ? (h ? mine.y : mine.x) : 0u;
+                const unsigned colh = (mh | (mh >> 8) | (mh >> 16) | (mh >> 24)) & 0xffu;
+                const unsigned sbase = (unsigned)(e.x * NB_CLUSTER) | ((unsigned)e.y << 27);
+#pragma unroll
+                for (int sp = 0; sp < 2; ++sp) {
+                    const unsigned col = (lane >> 4) == sp ? colh : 0u;
+                    const int c = __popc(col);
+                    int incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    if (total == 0) continue;
+                    const int pos0 = head[h] + fill[h] + incl - c;
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        if ((col >> bb) & 1u) {
+                            const int idx = (pos0 + __popc(col & ((1u << bb) - 1u))) & (kStage - 1);
+                            s_rslot[warp][h][idx] = (int)(sbase + (unsigned)bb);
+                            s_rmask[warp][h][idx] = mh;
+                        }
+                    }
+                    fill[h] += total;
+                    __syncwarp();
+                    while (fill[h] >= 32) {
+                        flush_tiles(s_rslot[warp][h], s_rmask[warp][h], head[h], 2 * k0 + h * n + ntile[h], 4, lane,
+                                    p);
+                        __syncwarp();
+                        head[h] += 32;
+                        fill[h] -= 32;
+                        ntile[h] += 4;
+                    }
                 }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                int pos = head[h] + fill[h] + incl - c;
-                while (col) {
-                    const int bb = __ffs(col) - 1;
-                    col &= col - 1u;
-                    const int idx = pos & (kStage - 1);
-                    s_rslot[warp][h][idx] = (int)((unsigned)(e.x * NB_CLUSTER + bb) | ((unsigned)e.y << 27));
-                    s_rrows[warp][h][idx] = (unsigned char)column_rows(m, bb);
-                    ++pos;
-                }
-                fill[h] += total;
-                __syncwarp();
-                while (fill[h] >= 8) {
-                    flush_tile(s_rslot[warp][h], s_rrows[warp][h], head[h], 2 * k0 + h * n + ntile[h], lane, p);
-                    head[h] += 8;
-                    fill[h] -= 8;
-                    ++ntile[h];
-                }
-                __syncwarp();
             }
         }
-        // last partial tile of each half, padded with a slot that holds no atom
+        // the rest of each half: its full tiles and a last one padded with a
+        // slot that holds no atom
 #pragma unroll
         for (int h = 0; h < (TILES ? 2 : 0); ++h) {
             if (fill[h] > 0) {
-                if (lane >= fill[h] && lane < 8) {
+                const int nt = (fill[h] + 7) >> 3;
+                if (lane >= fill[h] && lane < 8 * nt) {
                     const int idx = (head[h] + lane) & (kStage - 1);
                     s_rslot[warp][h][idx] = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-                    s_rrows[warp][h][idx] = 0;
+                    s_rmask[warp][h][idx] = 0u;
                 }
                 __syncwarp();
-                flush_tile(s_rslot[warp][h], s_rrows[warp][h], head[h], 2 * k0 + h * n + ntile[h], lane, p);
-                ++ntile[h];
+                flush_tiles(s_rslot[warp][h], s_rmask[warp][h], head[h], 2 * k0 + h * n + ntile[h], nt, lane, p);
+                ntile[h] += nt;
             }
             if (lane == 0) {
                 p.half_start[2 * ci + h] = 2 * k0 + h * n;

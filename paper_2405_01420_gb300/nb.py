@@ -103,6 +103,7 @@ SIGNATURES = {
     "nb_set_force_shape": (_I, [_P, _I, _I, _I]),
     "nb_pairlist_export_tiles": (_I, [_P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P]),
     "nb_set_coulomb": (_I, [_P, _I, ctypes.c_float, ctypes.c_uint]),
+    "nb_set_flags": (_I, [_P, ctypes.c_uint]),
     "nb_backward": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P, _P]),
     "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
                                ctypes.POINTER(ctypes.c_uint), _P]),
@@ -305,6 +306,11 @@ def nb_set_coulomb(pl, kind: int = NB_COUL_EWALD, eps_rf: float = 0.0, flags: in
     _check(load_library().nb_set_coulomb(pl, int(kind), float(eps_rf), int(flags)))
 
 
+def nb_set_flags(pl, flags: int) -> None:
+    """Replace the pair list's NB_FLAG_* flags (see nb.h)."""
+    _check(load_library().nb_set_flags(pl, int(flags)))
+
+
 def nb_set_force_shape(pl, threads: int = 0, chunk: int = 0, blocks_per_sm: int = 0) -> None:
     _check(load_library().nb_set_force_shape(pl, int(threads), int(chunk), int(blocks_per_sm)))
 
@@ -365,6 +371,9 @@ class Pairlist:
 
     def export_tiles(self, stream=None) -> dict:
         return nb_pairlist_export_tiles(self.handle, stream)
+
+    def set_flags(self, count_pairs: bool = False, sort_lists: bool = True, cluster_tiles: bool = False) -> None:
+        nb_set_flags(self.handle, self._flags(count_pairs, sort_lists, cluster_tiles))
 
     def set_coulomb(self, kind: str = "ewald", eps_rf: float = 0.0, shift: bool = False,
                     excl_corr: bool = False) -> None:

@@ -4,6 +4,8 @@ What it tunes, by timing the caller's own workload on the GPU:
 
 * the force kernel's launch shape (threads per CTA, list entries staged per
   warp, CTAs per SM; ``nb_set_force_shape``);
+* after a prune, the tile form: gathered 4 x 8 tiles computed 32 j atoms at a
+  time, or 8 x 8 cluster-pair tiles (``nb_set_flags``);
 * for one-shot batches (search + forces), whether to prune the outer list to
   the cutoff before the force call;
 * for trajectories, the prune interval and the inner-list margin
@@ -108,6 +110,21 @@ def tune_force_shape(pairlist, call: Callable[[], None], reps: int = 7, shapes=F
     nb.nb_set_force_shape(pairlist.handle, *best)
     if cache is not None and signature is not None:
         cache.put(_device_name(), "force_shape|" + signature, {"shape": list(best), "times": times})
+    return best, times
+
+
+def tune_tile_form(pairlist, call: Callable[[], None], reps: int = 7, count_pairs: bool = False,
+                   sort_lists: bool = True):
+    """After a prune: the gathered 4 x 8 tiles or the 8 x 8 cluster-pair tiles,
+    whichever makes ``call`` (an nb_forces on ``pairlist``) faster. Leaves the
+    pair list set to it and returns ("gathered" | "cluster", times)."""
+    def measure(form):
+        pairlist.set_flags(count_pairs=count_pairs, sort_lists=sort_lists, cluster_tiles=(form == "cluster"))
+        call()
+        return _median_ms(call, reps)
+
+    best, times = select_best(["gathered", "cluster"], measure)
+    pairlist.set_flags(count_pairs=count_pairs, sort_lists=sort_lists, cluster_tiles=(best == "cluster"))
     return best, times
 
 

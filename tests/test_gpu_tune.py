@@ -59,3 +59,27 @@ def test_autotuner_selects_a_shape(setup):
     pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta, F, E)
     compare_forces(F.cpu().numpy(), Fo)
     nb.nb_set_force_shape(pl.handle, 0, 0, 0)
+
+
+def test_tile_form_tuner_after_prune(setup):
+    """Both tile forms meet the oracle bar; the tuner leaves the pair list on one of them."""
+    from paper_2405_01420_gb300.tune import tune_tile_form
+    nb, b, d, pl, rc, beta, Fo, elj, ec = setup
+    q = nb.Pairlist(b.n_atoms)
+    q.search(d["coords"], b.box, rc + 0.1, d["excl_off"], d["excl_idx"])
+    q.prune(d["coords"], rc + 0.04)
+    F = torch.empty((b.n_atoms, 3), dtype=torch.float32, device="cuda")
+    E = torch.empty(2, dtype=torch.float64, device="cuda")
+    call = lambda: q.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta, F, E)
+    for form in ("gathered", "cluster"):
+        q.set_flags(cluster_tiles=(form == "cluster"))
+        call()
+        torch.cuda.synchronize()
+        compare_forces(F.cpu().numpy(), Fo)
+    best, times = tune_tile_form(q, call, reps=3)
+    assert best in ("gathered", "cluster") and all(t > 0 for t in times.values())
+    call()
+    compare_forces(F.cpu().numpy(), Fo)
+    with pytest.raises(nb.NBError):
+        nb.nb_set_flags(q.handle, 0x80)
+    q.close()
