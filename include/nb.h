@@ -287,6 +287,39 @@ int nb_set_timing_events(nb_pairlist *pl, void *start, void *stop);
  */
 int nb_set_flags(nb_pairlist *pl, unsigned flags);
 
+/*
+ * Local / non-local split (the domain-decomposition form of the kernel,
+ * §III-A: local work runs while the halo coordinates are still arriving).
+ * Atoms [0, n_home) are home atoms and [n_home, n) halo atoms; the default
+ * n_home = n means no halo. A pair is local when both atoms are home and
+ * non-local otherwise. Takes effect at the next nb_search; single-system
+ * pair lists only. Reserves the second region of gathered tiles (the pair
+ * list's tile buffers double), so call it before any graph capture.
+ * Errors: NB_ERR_ARG (n_home outside [1, n], a batch), NB_ERR_NOMEM.
+ */
+int nb_set_home(nb_pairlist *pl, int n_home);
+
+/* nb_forces_part parts */
+#define NB_PART_ALL 0      /* every pair (= nb_forces) */
+#define NB_PART_LOCAL 1    /* pairs of two home atoms */
+#define NB_PART_NONLOCAL 2 /* pairs with a halo atom */
+
+/*
+ * One part of nb_forces. NB_PART_LOCAL reads the home atoms' coordinates,
+ * charges and types, zeroes the force accumulators and energies[], and
+ * computes the local pairs; it writes nothing to forces (which may be NULL).
+ * NB_PART_NONLOCAL, issued after NB_PART_LOCAL on the same stream (or one
+ * that waits for it), reads the halo atoms' inputs, computes the non-local
+ * pairs, adds their energies to energies[] and writes the total forces of
+ * all atoms to forces. Between the two calls the caller may update the halo
+ * atoms' coordinates (e.g. the copy of a halo exchange on another stream):
+ * the local part never reads them. Without a halo, NB_PART_LOCAL computes
+ * every pair and NB_PART_NONLOCAL only writes the forces. Arguments and
+ * errors as nb_forces; NB_ERR_ARG for an unknown part.
+ */
+int nb_forces_part(nb_pairlist *pl, int part, const float *coords, const float *q, const int *type, int ntype,
+                   const float *ljparams, float rc, float beta, float *forces, double *energies, void *stream);
+
 /* Coulomb flavours (nb_set_coulomb). The paper's benchmark systems come in
    Ewald ("PME") and reaction-field ("RF") flavours (§II). */
 #define NB_COUL_EWALD 0 /* real-space Ewald: f qi qj erfc(beta r)/r (default) */

@@ -55,7 +55,7 @@ void free_buffers(nb_pairlist *pl) {
                     pl->ci_len_inner, pl->gsort,   pl->bsort,          pl->glj_acc,        pl->sys,
                     pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys,       pl->len_hist,
                     pl->len_offsets, pl->len_cursor, pl->ci_order,     pl->vt_slot,        pl->vt_mask,
-                    pl->half_start, pl->half_len,  pl->len_key,      pl->excl_pairs};
+                    pl->half_start, pl->half_len,  pl->len_key,      pl->excl_pairs,  pl->clus_home};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -118,6 +118,8 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
     if (cap >= (size_t)1 << 31) return fail(NB_ERR_ARG, "%s: capacity_entries %zu >= 2^31", who, cap);
     pl->cap = cap;
     pl->excl_cap = 8 * (size_t)n + 64;  // excluded pairs (i < j): 8 per atom
+    pl->n_home = n;                     // no halo until nb_set_home
+    pl->vt_parts = 1;
     pl->flags = cfg ? cfg->flags : 0u;
     // one extra cluster of slots past the last cluster: slot 8 nc_max pads
     // the last gathered tile of a half and never holds an atom
@@ -141,8 +143,9 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
                 alloc(&pl->len_cursor, NB_LEN_BINS, &total) && alloc(&pl->ci_order, pl->nc_max, &total) &&
                 alloc(&pl->len_key, pl->nc_max, &total) &&
                 alloc(&pl->excl_pairs, pl->excl_cap, &total) &&
-                alloc(&pl->half_start, 2 * (size_t)pl->nc_max, &total) &&
-                alloc(&pl->half_len, 2 * (size_t)pl->nc_max, &total);
+                alloc(&pl->half_start, 4 * (size_t)pl->nc_max, &total) &&
+                alloc(&pl->half_len, 4 * (size_t)pl->nc_max, &total) &&
+                alloc(&pl->clus_home, (size_t)pl->nc_max, &total);
     // gathered tiles pack a slot in 27 bits and index tiles with 32-bit ints;
     // beyond that the force kernel stays on the cluster-pair tiles
     if (good && nslot < ((size_t)1 << 27) && 2 * cap < ((size_t)1 << 31))
@@ -320,6 +323,7 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
     const float rl_col = (float)(rle + 1e-3);
     NB_CUDA(nb_launch_search(pl, excl_off, excl_idx, rl2, rl_col, s));
+    if (pl->vt_parts == 2) NB_CUDA(nb_launch_clus_home(pl, s));  // home bits of the clusters (a halo)
     // the excluded pairs, kept as slot pairs for the excluded-pair correction
     // (the caller's lists are read only during this call)
     NB_CUDA(cudaMemsetAsync(&pl->st->excl_count, 0, sizeof(unsigned), s));
@@ -345,7 +349,7 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
         return fail(NB_ERR_ARG, "nb_prune: r_inner = %g must be in (0, rlist = %g]", r_inner, pl->rlist);
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
-    NB_CUDA(nb_launch_gather(pl, coords, nullptr, nullptr, 1, 1, nullptr, s));
+    NB_CUDA(nb_launch_gather(pl, coords, nullptr, nullptr, 1, 1, nullptr, NB_PART_ALL, s));
     const float r2cut = r_inner * r_inner;
     const bool sort = !(pl->flags & NB_FLAG_NO_LIST_SORT);
     if (sort) NB_CUDA(nb_clear_len_hist(pl, s));
@@ -361,10 +365,12 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
     return ok();
 }
 
-extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
-                         const float *ljparams, float rc, float beta, float *forces, double *energies,
-                         void *stream) {
-    if (!pl || !coords || !q || !type || !ljparams || !forces)
+extern "C" int nb_forces_part(nb_pairlist *pl, int part, const float *coords, const float *q, const int *type,
+                              int ntype, const float *ljparams, float rc, float beta, float *forces, double *energies,
+                              void *stream) {
+    if (part != NB_PART_ALL && part != NB_PART_LOCAL && part != NB_PART_NONLOCAL)
+        return fail(NB_ERR_ARG, "nb_forces: part = %d", part);
+    if (!pl || !coords || !q || !type || !ljparams || (!forces && part != NB_PART_LOCAL))
         return fail(NB_ERR_ARG, "nb_forces: NULL argument");
     if (!pl->searched) return fail(NB_ERR_STATE, "nb_forces: no search yet");
     if (ntype < 1 || ntype > NB_MAX_TYPES) return fail(NB_ERR_ARG, "nb_forces: ntype = %d not in [1, %d]", ntype, NB_MAX_TYPES);
@@ -377,17 +383,35 @@ extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, c
         return fail(NB_ERR_STATE, "nb_forces: NB_COUL_EXCL_CORR needs exclusion lists at the search");
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
-    NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, energies, s));
-    if (pl->ev_start) NB_CUDA(cudaEventRecord(pl->ev_start, s));
-    if (pl->has_vtiles && !(pl->flags & NB_FLAG_CLUSTER_TILES))
-        NB_CUDA(nb_launch_force_vt(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->r_inner, rc), s));
-    else
-        NB_CUDA(nb_launch_force(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->rlist, rc),
-                                stale_bound2(pl->r_inner, rc), s));
-    if (pl->ev_stop) NB_CUDA(cudaEventRecord(pl->ev_stop, s));
-    if (pl->coul_flags & NB_COUL_EXCL_CORR) NB_CUDA(nb_launch_excl_corr(pl, rc, beta, energies, s));
-    NB_CUDA(nb_launch_scatter(pl, forces, s));
+    // Without a halo the local part is the whole computation and the
+    // non-local part only writes the forces.
+    const bool split = pl->vt_parts == 2;
+    const bool compute = split || part != NB_PART_NONLOCAL;
+    const int kpart = split ? part : NB_PART_ALL;
+    const bool last = part != NB_PART_LOCAL;  // this call ends the evaluation
+    if (compute) {
+        NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, energies, kpart, s));
+        if (pl->ev_start) NB_CUDA(cudaEventRecord(pl->ev_start, s));
+        const int fpart = (!split && part == NB_PART_LOCAL) ? NB_PART_ALL : kpart;
+        if (pl->has_vtiles && !(pl->flags & NB_FLAG_CLUSTER_TILES))
+            NB_CUDA(nb_launch_force_vt(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->r_inner, rc), fpart,
+                                       s));
+        else
+            NB_CUDA(nb_launch_force(pl, ntype, ljparams, rc, beta, energies, stale_bound2(pl->rlist, rc),
+                                    stale_bound2(pl->r_inner, rc), fpart, s));
+        if (pl->ev_stop) NB_CUDA(cudaEventRecord(pl->ev_stop, s));
+    }
+    if (last) {
+        if (pl->coul_flags & NB_COUL_EXCL_CORR) NB_CUDA(nb_launch_excl_corr(pl, rc, beta, energies, s));
+        NB_CUDA(nb_launch_scatter(pl, forces, s));
+    }
     return ok();
+}
+
+extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
+                         const float *ljparams, float rc, float beta, float *forces, double *energies,
+                         void *stream) {
+    return nb_forces_part(pl, NB_PART_ALL, coords, q, type, ntype, ljparams, rc, beta, forces, energies, stream);
 }
 
 extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
@@ -407,7 +431,7 @@ extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q,
         return fail(NB_ERR_STATE, "nb_backward: NB_COUL_EXCL_CORR needs exclusion lists at the search");
     DeviceGuard gd(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
-    NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, nullptr, s));
+    NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, nullptr, NB_PART_ALL, s));
     NB_CUDA(nb_launch_backward(pl, ntype, ljparams, rc, beta, g, grad_x, grad_q, grad_lj,
                                stale_bound2(pl->rlist, rc), stale_bound2(pl->r_inner, rc), s));
     return ok();
@@ -530,18 +554,23 @@ extern "C" int nb_pairlist_export_tiles(nb_pairlist *pl, int *half_id, int *slot
     nb_dev_state st;
     NB_CUDA(cudaMemcpyAsync(&st, pl->st, sizeof(st), cudaMemcpyDeviceToHost, s));
     NB_CUDA(cudaStreamSynchronize(s));
-    const int nh = 2 * st.nc;
-    std::vector<int> start(nh), len(nh);
-    NB_CUDA(cudaMemcpyAsync(start.data(), pl->half_start, sizeof(int) * nh, cudaMemcpyDeviceToHost, s));
-    NB_CUDA(cudaMemcpyAsync(len.data(), pl->half_len, sizeof(int) * nh, cudaMemcpyDeviceToHost, s));
+    const int nh = 2 * st.nc, nreg = pl->vt_parts == 2 ? 2 : 1;
+    std::vector<int> start(nh * nreg), len(nh * nreg);
+    for (int r = 0; r < nreg; ++r) {  // regions: local, non-local (with a halo)
+        NB_CUDA(cudaMemcpyAsync(start.data() + r * nh, pl->half_start + (size_t)r * 2 * pl->nc_max, sizeof(int) * nh,
+                                cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaMemcpyAsync(len.data() + r * nh, pl->half_len + (size_t)r * 2 * pl->nc_max, sizeof(int) * nh,
+                                cudaMemcpyDeviceToHost, s));
+    }
     NB_CUDA(cudaStreamSynchronize(s));
     size_t k = 0;
-    for (int hh = 0; hh < nh; ++hh) {
-        const size_t m = (size_t)len[hh];
+    for (int rh = 0; rh < nh * nreg; ++rh) {
+        const int hh = rh % nh;
+        const size_t m = (size_t)len[rh];
         if (m > 0 && k + m <= cap) {  // one copy per half: its tiles are contiguous
-            NB_CUDA(cudaMemcpyAsync(slots + 8 * k, pl->vt_slot + 8 * (size_t)start[hh], sizeof(int) * 8 * m,
+            NB_CUDA(cudaMemcpyAsync(slots + 8 * k, pl->vt_slot + 8 * (size_t)start[rh], sizeof(int) * 8 * m,
                                     cudaMemcpyDeviceToHost, s));
-            NB_CUDA(cudaMemcpyAsync(masks + k, pl->vt_mask + start[hh], sizeof(unsigned) * m,
+            NB_CUDA(cudaMemcpyAsync(masks + k, pl->vt_mask + start[rh], sizeof(unsigned) * m,
                                     cudaMemcpyDeviceToHost, s));
             for (size_t t = 0; t < m; ++t) half_id[k + t] = hh;
         }
@@ -572,5 +601,38 @@ extern "C" int nb_set_flags(nb_pairlist *pl, unsigned flags) {
     if (flags & ~(unsigned)(NB_FLAG_COUNT_PAIRS | NB_FLAG_NO_LIST_SORT | NB_FLAG_CLUSTER_TILES))
         return fail(NB_ERR_ARG, "nb_set_flags: unknown flags 0x%x", flags);
     pl->flags = flags;
+    return ok();
+}
+
+extern "C" int nb_set_home(nb_pairlist *pl, int n_home) {
+    if (!pl) return fail(NB_ERR_ARG, "nb_set_home: NULL pair list");
+    if (pl->batch) return fail(NB_ERR_ARG, "nb_set_home: not for a batch of systems");
+    if (n_home < 1 || n_home > pl->n_atoms)
+        return fail(NB_ERR_ARG, "nb_set_home: n_home = %d not in [1, %d]", n_home, pl->n_atoms);
+    const int parts = n_home < pl->n_atoms ? 2 : 1;
+    if (parts == 2 && pl->vt_slot && pl->vt_parts != 2) {
+        // the second region of gathered tiles (non-local): twice the buffers
+        if (4 * pl->cap >= ((size_t)1 << 31))
+            return fail(NB_ERR_CAPACITY, "nb_set_home: list capacity %zu too large for two tile regions", pl->cap);
+        DeviceGuard g(pl->device);
+        NB_CUDA(cudaDeviceSynchronize());
+        int *slot2 = nullptr;
+        unsigned *mask2 = nullptr;
+        if (cudaMalloc(&slot2, sizeof(int) * 32 * pl->cap) != cudaSuccess ||
+            cudaMalloc(&mask2, sizeof(unsigned) * 4 * pl->cap) != cudaSuccess) {
+            cudaFree(slot2);
+            cudaGetLastError();
+            return fail(NB_ERR_NOMEM, "nb_set_home: no memory for the non-local tile region");
+        }
+        cudaFree(pl->vt_slot);
+        cudaFree(pl->vt_mask);
+        pl->vt_slot = slot2;
+        pl->vt_mask = mask2;
+    }
+    pl->n_home = n_home;
+    pl->vt_parts = parts;
+    pl->searched = 0;  // the next nb_search builds the split lists
+    pl->has_inner = 0;
+    pl->has_vtiles = 0;
     return ok();
 }

@@ -41,6 +41,8 @@ struct BvtParams {
     float k2;  // 2 (2 beta/sqrt(pi)) beta^2
     float stale_prune2;
     int pad_slot;  // never holds an atom: far away, q = 0, type 0
+    int nreg;      // regions of gathered tiles (2 with a halo: local, non-local)
+    int reg_stride;  // 2 nc_max
 };
 
 struct BvtStage {
@@ -90,7 +92,8 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned nwork = 2u * (unsigned)p.st->nc;
+    const unsigned nhalf = 2u * (unsigned)p.st->nc;
+    const unsigned nwork = nhalf * (unsigned)p.nreg;
     int shift_sys = -1;
 
     for (;;) {
@@ -98,9 +101,11 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= nwork) break;
-        const int ci = p.order ? p.order[w >> 1] : (int)(w >> 1);
-        const int h = (int)(w & 1u);
-        const int t0 = p.half_start[2 * ci + h], t1 = t0 + p.half_len[2 * ci + h];
+        const unsigned reg = w / nhalf, hw = w - reg * nhalf;
+        const int ci = p.order ? p.order[hw >> 1] : (int)(hw >> 1);
+        const int h = (int)(hw & 1u);
+        const size_t hidx = (size_t)reg * p.reg_stride + 2 * ci + h;
+        const int t0 = p.half_start[hidx], t1 = t0 + p.half_len[hidx];
         if (t1 <= t0) continue;
         const int csys = p.clus_sys[ci];
         if (csys != shift_sys) {
@@ -207,7 +212,7 @@ cudaError_t launch_bvt(nb_pairlist *pl, const BvtParams &p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    const int blocks = min(pl->num_sms * per_sm, (2 * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
+    const int blocks = min(pl->num_sms * per_sm, (2 * p.nreg * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
     k_backward_vt<NT, COUL><<<max(blocks, 1), kBvtThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -236,6 +241,8 @@ cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljpar
     p.k2 = (float)(2.0 * (2.0 * beta / 1.7724538509055159) * (double)beta * beta);
     p.stale_prune2 = stale_prune2;
     p.pad_slot = pl->nc_max * NB_CLUSTER;
+    p.nreg = pl->vt_parts == 2 ? 2 : 1;
+    p.reg_stride = 2 * pl->nc_max;
     if (coul == NB_COULK_RF) {  // the Ewald shift does not change forces
         if (ntype == 1) return launch_bvt<1, NB_COULK_RF>(pl, p, s);
         if (ntype == 2) return launch_bvt<2, NB_COULK_RF>(pl, p, s);

@@ -40,6 +40,8 @@ struct GatherParams {
     int nsys;
     int snapshot;
     int ntype;
+    int part;    // NB_PART_ALL / NB_PART_LOCAL (home atoms) / NB_PART_NONLOCAL (halo atoms)
+    int n_home;  // atoms [0, n_home) are home atoms
 };
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -52,8 +54,9 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
     float d2s_max = 0.0f, d2p_max = 0.0f;
     for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nslot; slot += gridDim.x * blockDim.x) {
         const int atom = p.perm[slot];
-        p.fsort[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (p.part != NB_PART_NONLOCAL) p.fsort[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (atom < 0) continue;
+        if (p.part == NB_PART_LOCAL ? atom >= p.n_home : (p.part == NB_PART_NONLOCAL && atom < p.n_home)) continue;
         const float4 r = p.xref[slot];
         const float4 L = p.sys[p.atom_sys[atom]].box;
         float x = p.coords[3 * atom + 0], y = p.coords[3 * atom + 1], z = p.coords[3 * atom + 2];
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
                 p.st->inner_count = 0ull;
             }
         }
-        if (p.energies)
+        if (p.energies && p.part != NB_PART_NONLOCAL)
             for (int k = threadIdx.x; k < 2 * p.nsys; k += blockDim.x) p.energies[k] = 0.0;
     }
 }
@@ -124,6 +127,9 @@ struct ForceParams {
     nb_coul cc;
     float stale_search2, stale_prune2;
     int has_inner;
+    int part;                        // NB_PART_*: ALL computes every pair
+    const unsigned char *clus_home;  // with a part: bit b = slot b of the cluster holds a home atom
+    int finalize;                    // move the displacement maxima of this evaluation to last_*
 };
 
 
@@ -149,6 +155,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
     __shared__ int4 s_ent[kWarps][CHUNK];
     __shared__ float4 s_xj[kWarps][CHUNK * NB_CLUSTER];
     __shared__ int s_tj[kWarps][CHUNK * NB_CLUSTER];
+    __shared__ unsigned char s_hj[kWarps][CHUNK];  // home bits of the staged j clusters
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -158,10 +165,12 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
         // The gather of this call has finished; record its displacements and
         // check them against the list buffers.
         const unsigned ds = p.st->cur_d2_search, dp = p.st->cur_d2_prune;
-        p.st->last_d2_search = ds;
-        p.st->last_d2_prune = dp;
-        p.st->cur_d2_search = 0u;
-        p.st->cur_d2_prune = 0u;
+        if (p.finalize) {
+            p.st->last_d2_search = ds;
+            p.st->last_d2_prune = dp;
+            p.st->cur_d2_search = 0u;
+            p.st->cur_d2_prune = 0u;
+        }
         if (!p.has_inner && __uint_as_float(ds) > p.stale_search2) atomicOr(&p.st->err, NB_DEV_STALE_SEARCH);
         if (p.has_inner && __uint_as_float(dp) > p.stale_prune2) atomicOr(&p.st->err, NB_DEV_STALE_PRUNE);
     }
@@ -199,6 +208,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
         const float qi1 = xi1.w * NB_COULOMB_F, qi2 = xi2.w * NB_COULOMB_F;
         const int tr1 = p.tsort[ci * NB_CLUSTER + a1] * p.ntype;
         const int tr2 = p.tsort[ci * NB_CLUSTER + a2] * p.ntype;
+        const unsigned hci = p.part != NB_PART_ALL ? p.clus_home[ci] : 0u;
+        const bool hi1 = (hci >> a1) & 1u, hi2 = (hci >> a2) & 1u;
         float3 fi1 = make_float3(0.0f, 0.0f, 0.0f), fi2 = make_float3(0.0f, 0.0f, 0.0f);
         float ec = 0.0f, ecomp = 0.0f, elj = 0.0f, eljcomp = 0.0f;
 
@@ -208,7 +219,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
             // chain per tile.
             const int nch = min(CHUNK, k1 - base);
             __syncwarp();
-            if (lane < nch) ent[lane] = p.list[base + lane];
+            if (lane < nch) {
+                ent[lane] = p.list[base + lane];
+                if (p.part != NB_PART_ALL) s_hj[warp][lane] = p.clus_home[ent[lane].x];
+            }
             __syncwarp();
             for (int idx = lane; idx < nch * NB_CLUSTER; idx += 32) {
                 const int slot = ent[idx >> 3].x * NB_CLUSTER + (idx & 7);
@@ -221,7 +235,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
                 const float4 xj = sxj[t * NB_CLUSTER + b];
                 const int tj = stj[t * NB_CLUSTER + b];
                 const int sidx = e.y;
-                const unsigned mlo = (unsigned)e.z, mhi = (unsigned)e.w;
+                unsigned mlo = (unsigned)e.z, mhi = (unsigned)e.w;
+                if (p.part != NB_PART_ALL) {  // keep the pairs of this part: both atoms home, or not
+                    const bool hj = (s_hj[warp][t] >> b) & 1u;
+                    const unsigned l1 = __ballot_sync(0xffffffffu, hi1 && hj);
+                    const unsigned l2 = __ballot_sync(0xffffffffu, hi2 && hj);
+                    mlo &= p.part == NB_PART_LOCAL ? l1 : ~l1;
+                    mhi &= p.part == NB_PART_LOCAL ? l2 : ~l2;
+                }
                 float3 fj = make_float3(0.0f, 0.0f, 0.0f);
                 float ect = 0.0f, eljt = 0.0f;
                 int c1 = 0, c2 = 0;
@@ -291,6 +312,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
     }
 }
 
+__global__ void k_clus_home(int nc_max, const int *__restrict__ perm, int n_home,
+                            unsigned char *__restrict__ clus_home, const nb_dev_state *st) {
+    const int nc = st->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc_max; c += gridDim.x * blockDim.x) {
+        unsigned bits = 0u;
+        if (c < nc)
+            for (int b = 0; b < NB_CLUSTER; ++b) {
+                const int atom = perm[c * NB_CLUSTER + b];
+                bits |= (atom >= 0 && atom < n_home ? 1u : 0u) << b;
+            }
+        clus_home[c] = (unsigned char)bits;
+    }
+}
+
 __global__ void k_scatter(int n, const int *__restrict__ pos, const float4 *__restrict__ fsort,
                           float *__restrict__ forces) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -321,8 +356,10 @@ int g_blocks_per_sm[3][2][2][2][2] = {};
 }  // namespace
 
 cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
-                             int ntype, int snapshot, double *energies, cudaStream_t s) {
+                             int ntype, int snapshot, double *energies, int part, cudaStream_t s) {
     GatherParams p;
+    p.part = part;
+    p.n_home = pl->n_home;
     p.ntype = ntype;
     p.perm = pl->perm;
     p.coords = coords;
@@ -346,9 +383,12 @@ cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *
 }
 
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
-                            double *energies, float stale_search2, float stale_prune2,
+                            double *energies, float stale_search2, float stale_prune2, int part,
                             cudaStream_t s) {
     ForceParams p;
+    p.part = part;
+    p.clus_home = pl->clus_home;
+    p.finalize = part != NB_PART_LOCAL;
     p.xq = pl->xq;
     p.tsort = pl->tsort;
     p.fsort = reinterpret_cast<float *>(pl->fsort);
@@ -389,6 +429,12 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     blocks = min(blocks, (pl->nc_max + threads / 32 - 1) / (threads / 32));
     blocks = max(blocks, 1);
     fn<<<blocks, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t nb_launch_clus_home(nb_pairlist *pl, cudaStream_t s) {
+    const int blocks = max(1, min((pl->nc_max + 255) / 256, pl->num_sms * 8));
+    k_clus_home<<<blocks, 256, 0, s>>>(pl->nc_max, pl->perm, pl->n_home, pl->clus_home, pl->st);
     return cudaGetLastError();
 }
 

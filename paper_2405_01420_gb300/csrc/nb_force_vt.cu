@@ -46,6 +46,9 @@ struct VtParams {
     nb_coul cc;
     float stale_prune2;
     int pad_slot;             // never holds an atom: far away, q = 0, type 0
+    int reg0, nreg;           // regions of gathered tiles to compute (0 local or all, 1 non-local)
+    int reg_stride;           // 2 nc_max: halves per region in half_start / half_len
+    int finalize;             // move the displacement maxima of this evaluation to last_*
 };
 
 __device__ __forceinline__ void flush_energies_vt(double ec, double elj, int lane, double *out) {
@@ -111,16 +114,19 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned ds = p.st->cur_d2_search, dp = p.st->cur_d2_prune;
-        p.st->last_d2_search = ds;
-        p.st->last_d2_prune = dp;
-        p.st->cur_d2_search = 0u;
-        p.st->cur_d2_prune = 0u;
+        if (p.finalize) {
+            p.st->last_d2_search = ds;
+            p.st->last_d2_prune = dp;
+            p.st->cur_d2_search = 0u;
+            p.st->cur_d2_prune = 0u;
+        }
         if (__uint_as_float(dp) > p.stale_prune2) atomicOr(&p.st->err, NB_DEV_STALE_PRUNE);
     }
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned nwork = 2u * (unsigned)p.st->nc;
+    const unsigned nhalf = 2u * (unsigned)p.st->nc;  // halves per region
+    const unsigned nwork = nhalf * (unsigned)p.nreg;
     double ecd = 0.0, eljd = 0.0;
     int cur_sys = -1;
     unsigned cnt = 0;
@@ -129,8 +135,9 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        const int ci = (w < nwork && p.order) ? p.order[w >> 1] : (int)(w >> 1);
-        const int h = (int)(w & 1u);
+        const unsigned reg = w < nwork ? w / nhalf : 0u, hw = w - reg * nhalf;
+        const int ci = (w < nwork && p.order) ? p.order[hw >> 1] : (int)(hw >> 1);
+        const int h = (int)(hw & 1u);
         const int csys = (w < nwork) ? p.clus_sys[ci] : -1;
         if (ENERGY && csys != cur_sys) {
             if (cur_sys >= 0) flush_energies_vt(ecd, eljd, lane, p.energies + 2 * cur_sys);
@@ -139,7 +146,8 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             cur_sys = csys;
         }
         if (w >= nwork) break;
-        const int t0 = p.half_start[2 * ci + h], t1 = t0 + p.half_len[2 * ci + h];
+        const size_t hidx = (size_t)(p.reg0 + (int)reg) * p.reg_stride + 2 * ci + h;
+        const int t0 = p.half_start[hidx], t1 = t0 + p.half_len[hidx];
         if (t1 <= t0) continue;
         if (csys != shift_sys) {
             if (lane < 27) s_shift[warp][lane] = p.sys_shift[27 * csys + lane];
@@ -240,8 +248,13 @@ Occ g_vt_occ[3][2][2][2] = {};
 }  // namespace
 
 cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
-                               double *energies, float stale_prune2, cudaStream_t s) {
+                               double *energies, float stale_prune2, int part, cudaStream_t s) {
     VtParams p;
+    // regions: without a halo one (every pair); with one, 0 = local, 1 = non-local
+    p.reg0 = part == NB_PART_NONLOCAL ? 1 : 0;
+    p.nreg = (part == NB_PART_ALL && pl->vt_parts == 2) ? 2 : 1;
+    p.reg_stride = 2 * pl->nc_max;
+    p.finalize = part != NB_PART_LOCAL;
     p.xq = pl->xq;
     p.tsort = pl->tsort;
     p.fsort = reinterpret_cast<float *>(pl->fsort);
@@ -279,7 +292,7 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     const int per_sm = occ.per_sm;
     const int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
     int blocks = pl->num_sms * use;
-    blocks = min(blocks, (2 * pl->nc_max + threads / 32 - 1) / (threads / 32));
+    blocks = min(blocks, (2 * p.nreg * pl->nc_max + threads / 32 - 1) / (threads / 32));
     fn<<<max(blocks, 1), threads, smem, s>>>(p);
     return cudaGetLastError();
 }

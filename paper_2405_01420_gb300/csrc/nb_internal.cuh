@@ -110,8 +110,11 @@ struct nb_pairlist {
     int sorted;           // ci_order matches the list the forces will use
     int *vt_slot;         // [2 cap * 8] gathered tiles: j slot | shift << 27
     unsigned *vt_mask;    // [2 cap] 4 x 8 in-range bits per gathered tile
-    int *half_start;      // [2 nc_max] first gathered tile of each half i-cluster
-    int *half_len;        // [2 nc_max]
+    int *half_start;      // [2 parts][2 nc_max] first gathered tile of each half i-cluster
+    int *half_len;        // [2 parts][2 nc_max]
+    int n_home;           // atoms [0, n_home) are home atoms (nb_set_home); n_atoms = no halo
+    int vt_parts;         // regions of gathered tiles: 1, or 2 (local, non-local) with a halo
+    unsigned char *clus_home;  // [nc_max] bit b: slot b of the cluster holds a home atom (with a halo)
     int2 *excl_pairs;     // [excl_cap] excluded pairs (slot_i, slot_j), i < j, of the last search
     size_t excl_cap;
     int has_vtiles;       // the last prune built gathered tiles
@@ -165,8 +168,12 @@ cudaError_t nb_launch_set_system(nb_pairlist *pl, const nb_sys &one, cudaStream_
 cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream_t s);
 cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *excl_idx, float rl2,
                              float rl_col, cudaStream_t s);
+// part: NB_PART_ALL (every atom), NB_PART_LOCAL (home atoms; zeroes the
+// accumulators and energies), NB_PART_NONLOCAL (halo atoms only).
 cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
-                             int ntype, int snapshot, double *energies, cudaStream_t s);
+                             int ntype, int snapshot, double *energies, int part, cudaStream_t s);
+// clus_home[c] bit b = slot b of cluster c holds a home atom (after the grid sort of a search).
+cudaError_t nb_launch_clus_home(nb_pairlist *pl, cudaStream_t s);
 cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2, cudaStream_t s);
 // Orders i-clusters by decreasing ci_len. hist_ready: the histogram of
 // ci_len is already in len_hist (the prune computes it), else it is built here.
@@ -181,10 +188,13 @@ cudaError_t nb_launch_excl_corr(nb_pairlist *pl, float rc, float beta, double *e
 cudaError_t nb_launch_excl_corr_adj(nb_pairlist *pl, float rc, float beta, cudaStream_t s);
 cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
                                   float stale_prune2, cudaStream_t s);
+// Force kernels for one part (NB_PART_*). A local part leaves the
+// displacement tracker's running maxima for the non-local part, which ends
+// the evaluation.
 cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
-                               double *energies, float stale_prune2, cudaStream_t s);
+                               double *energies, float stale_prune2, int part, cudaStream_t s);
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
-                            double *energies, float stale_search2, float stale_prune2,
+                            double *energies, float stale_search2, float stale_prune2, int part,
                             cudaStream_t s);
 cudaError_t nb_launch_scatter(nb_pairlist *pl, float *forces, cudaStream_t s);
 cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,

@@ -176,8 +176,8 @@ extern "C" int nb_forces_noalloc(int n_atoms, const float *coords, const float *
     pl.searched = 1;
     pl.has_inner = 0;
     pl.rlist = rc;
-    if (e == cudaSuccess) e = nb_launch_gather(&pl, coords, q, type, ntype, 0, energies, s);
-    if (e == cudaSuccess) e = nb_launch_force(&pl, ntype, ljparams, rc, beta, energies, 0.0f, 0.0f, s);
+    if (e == cudaSuccess) e = nb_launch_gather(&pl, coords, q, type, ntype, 0, energies, NB_PART_ALL, s);
+    if (e == cudaSuccess) e = nb_launch_force(&pl, ntype, ljparams, rc, beta, energies, 0.0f, 0.0f, NB_PART_ALL, s);
     if (e == cudaSuccess) e = nb_launch_scatter(&pl, forces, s);
     if (e != cudaSuccess) return fail(NB_ERR_CUDA, cudaGetErrorString(e));
     if (error_word) {

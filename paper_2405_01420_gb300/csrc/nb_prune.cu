@@ -25,18 +25,27 @@ struct PruneParams {
     nb_dev_state *st;
     const float4 *sys_shift;  // [27 nsys]
     const int *clus_sys;
-    int *vt_slot;        // [2 cap * 8] gathered j slots (shift index in the top 5 bits)
-    unsigned *vt_mask;   // [2 cap] 4 x 8 in-range bits (bit a*8 + p)
-    int *half_start;     // [2 nc_max]
-    int *half_len;       // [2 nc_max]
+    int *vt_slot;        // [2 parts * 2 cap * 8] gathered j slots (shift index in the top 5 bits)
+    unsigned *vt_mask;   // [2 parts * 2 cap] 4 x 8 in-range bits (bit a*8 + p)
+    int *half_start;     // [2 parts][2 nc_max]
+    int *half_len;       // [2 parts][2 nc_max]
     int pad_slot;        // a slot that never holds an atom (far away, q = 0)
     int *len_key;        // [nc_max] work of each i-cluster for the force kernel
     int *len_hist;       // [NB_LEN_BINS] histogram of len_key, or NULL (no sorting)
+    const unsigned char *clus_home;  // with a halo: bit b = slot b of the cluster holds a home atom
+    int reg_stride;      // 2 nc_max: halves per region of half_start / half_len
     float r2cut;
     float stale_search2;
 };
 
-constexpr int kStage = 256;  // ring of staged j atoms per warp and half (>= 31 + 16 * 8)
+// Ring of staged j atoms per warp, half and part: it holds up to 31 atoms
+// left from full tiles plus one pass of kSub entries (8 atoms each).
+template <int NPART>
+struct Ring {
+    static constexpr int kSub = NPART == 1 ? 16 : 8;
+    static constexpr int kStage = NPART == 1 ? 256 : 128;
+    static_assert(kStage >= 31 + 8 * kSub, "ring too small");
+};
 
 // Writes ntiles (<= 4) gathered tiles from the 8 ntiles staged atoms at ring
 // position head: lane l takes atom l, i.e. column p = l & 7 of tile l >> 3.
@@ -44,9 +53,10 @@ constexpr int kStage = 256;  // ring of staged j atoms per warp and half (>= 31 
 // b in that word is the low 3 bits of its slot, so its rows (bits b, 8 + b,
 // 16 + b, 24 + b) shifted to column p are its part of the tile's mask, and
 // the 8 lanes of a tile OR theirs together.
+template <int STAGE>
 __device__ __forceinline__ void flush_tiles(const int *ring_slot, const unsigned *ring_mask, int head, int vt,
                                             int ntiles, int lane, const PruneParams &p) {
-    const int idx = (head + lane) & (kStage - 1);
+    const int idx = (head + lane) & (STAGE - 1);
     const int v = ring_slot[idx];
     const int pcol = lane & 7, t = lane >> 3;
     unsigned c = ((ring_mask[idx] >> ((unsigned)v & 7u)) & 0x01010101u) << pcol;
@@ -93,11 +103,14 @@ __device__ __forceinline__ uint2 prune_entry(const int4 e, const float4 xi1, con
 // iteration (independent loads for latency hiding); lane t keeps the new
 // masks of entry t, and the kept entries are written back compacted and
 // coalesced.
-template <bool TILES>
+// With a halo (NPART = 2) the tiles of each half are gathered in two sets:
+// pairs of two home atoms (region 0) and the rest (region 1).
+template <bool TILES, int NPART>
 __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
+    constexpr int kStage = Ring<NPART>::kStage, kSub = Ring<NPART>::kSub, kSets = 2 * NPART;
     __shared__ int4 s_ent[kPruneThreads / 32][32];
-    __shared__ int s_rslot[kPruneThreads / 32][2][kStage];
-    __shared__ unsigned s_rmask[kPruneThreads / 32][2][kStage];
+    __shared__ int s_rslot[kPruneThreads / 32][kSets][kStage];
+    __shared__ unsigned s_rmask[kPruneThreads / 32][kSets][kStage];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // displacement since the search must leave the outer list complete at r_inner
         const unsigned ds = p.st->cur_d2_search;
@@ -120,10 +133,22 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         const int ci = (int)w;
         const float4 *shift = p.sys_shift + 27 * p.clus_sys[ci];
         const int k0 = p.ci_start[ci], n = p.ci_len_outer[ci];
-        // tiles of half h go to [2 k0 + h n, 2 k0 + (h + 1) n): each entry adds at most 8 atoms
+        // tiles of set r (part r >> 1, half r & 1) go to [2 NPART k0 + r n, + n):
+        // each entry adds at most 8 atoms to a set
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
+        unsigned rows_lo = 0u, rows_hi = 0u;  // home rows of ci as byte masks (rows 0-3 / 4-7)
+        if (NPART == 2) {
+            const unsigned hci = p.clus_home[ci];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                rows_lo |= ((hci >> a) & 1u) ? 0xffu << (8 * a) : 0u;
+                rows_hi |= ((hci >> (a + 4)) & 1u) ? 0xffu << (8 * a) : 0u;
+            }
+        }
         int out = 0;
-        int head[2] = {0, 0}, fill[2] = {0, 0}, ntile[2] = {0, 0};
+        int head[kSets], fill[kSets], ntile[kSets];
+#pragma unroll
+        for (int r = 0; r < kSets; ++r) head[r] = fill[r] = ntile[r] = 0;
         for (int base = 0; base < n; base += 32) {
             const int cnt = min(32, n - base);
             __syncwarp();
@@ -151,19 +176,27 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
             if (keep)
                 p.inner[k0 + out + __popc(bal & (lanebit - 1u))] = make_int4(e.x, e.y, (int)mine.x, (int)mine.y);
             out += __popc(bal);
-            // Gather, per half, the j atoms in range of any of its 4 rows.
+            // Gather, per half (and part), the j atoms in range of any of its 4 rows.
+            unsigned loc_lo = 0xffffffffu, loc_hi = 0xffffffffu;  // local pairs of the lane's entry
+            if (NPART == 2) {
+                const unsigned hjw = (lane < cnt ? (unsigned)p.clus_home[e.x] : 0u) * 0x01010101u;
+                loc_lo = hjw & rows_lo;
+                loc_hi = hjw & rows_hi;
+            }
 #pragma unroll
-            for (int h = 0; h < (TILES ? 2 : 0); ++h) {
+            for (int r = 0; r < (TILES ? kSets : 0); ++r) {
                 // in entry order (atoms of one entry stay together, so a tile
-                // draws on few clusters), 16 entries at a time: an exclusive
+                // draws on few clusters), kSub entries at a time: an exclusive
                 // scan of the per-entry counts places each lane's atoms; once
                 // 32 atoms are staged, 4 full tiles leave together
-                const unsigned mh = lane < cnt ? (h ? mine.y : mine.x) : 0u;
+                const int h = r & 1, part = r >> 1;
+                unsigned mh = lane < cnt ? (h ? mine.y : mine.x) : 0u;
+                if (NPART == 2) mh &= part ? ~(h ? loc_hi : loc_lo) : (h ? loc_hi : loc_lo);
                 const unsigned colh = (mh | (mh >> 8) | (mh >> 16) | (mh >> 24)) & 0xffu;
                 const unsigned sbase = (unsigned)(e.x * NB_CLUSTER) | ((unsigned)e.y << 27);
 #pragma unroll
-                for (int sp = 0; sp < 2; ++sp) {
-                    const unsigned col = (lane >> 4) == sp ? colh : 0u;
+                for (int sp = 0; sp < 32 / kSub; ++sp) {
+                    const unsigned col = lane / kSub == sp ? colh : 0u;
                     const int c = __popc(col);
                     int incl = c;
 #pragma unroll
@@ -173,46 +206,48 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
                     }
                     const int total = __shfl_sync(0xffffffffu, incl, 31);
                     if (total == 0) continue;
-                    const int pos0 = head[h] + fill[h] + incl - c;
+                    const int pos0 = head[r] + fill[r] + incl - c;
 #pragma unroll
                     for (int bb = 0; bb < 8; ++bb) {
                         if ((col >> bb) & 1u) {
                             const int idx = (pos0 + __popc(col & ((1u << bb) - 1u))) & (kStage - 1);
-                            s_rslot[warp][h][idx] = (int)(sbase + (unsigned)bb);
-                            s_rmask[warp][h][idx] = mh;
+                            s_rslot[warp][r][idx] = (int)(sbase + (unsigned)bb);
+                            s_rmask[warp][r][idx] = mh;
                         }
                     }
-                    fill[h] += total;
+                    fill[r] += total;
                     __syncwarp();
-                    while (fill[h] >= 32) {
-                        flush_tiles(s_rslot[warp][h], s_rmask[warp][h], head[h], 2 * k0 + h * n + ntile[h], 4, lane,
-                                    p);
+                    while (fill[r] >= 32) {
+                        flush_tiles<kStage>(s_rslot[warp][r], s_rmask[warp][r], head[r],
+                                            2 * NPART * k0 + r * n + ntile[r], 4, lane, p);
                         __syncwarp();
-                        head[h] += 32;
-                        fill[h] -= 32;
-                        ntile[h] += 4;
+                        head[r] += 32;
+                        fill[r] -= 32;
+                        ntile[r] += 4;
                     }
                 }
             }
         }
-        // the rest of each half: its full tiles and a last one padded with a
+        // the rest of each set: its full tiles and a last one padded with a
         // slot that holds no atom
 #pragma unroll
-        for (int h = 0; h < (TILES ? 2 : 0); ++h) {
-            if (fill[h] > 0) {
-                const int nt = (fill[h] + 7) >> 3;
-                if (lane >= fill[h] && lane < 8 * nt) {
-                    const int idx = (head[h] + lane) & (kStage - 1);
-                    s_rslot[warp][h][idx] = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-                    s_rmask[warp][h][idx] = 0u;
+        for (int r = 0; r < (TILES ? kSets : 0); ++r) {
+            if (fill[r] > 0) {
+                const int nt = (fill[r] + 7) >> 3;
+                if (lane >= fill[r] && lane < 8 * nt) {
+                    const int idx = (head[r] + lane) & (kStage - 1);
+                    s_rslot[warp][r][idx] = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+                    s_rmask[warp][r][idx] = 0u;
                 }
                 __syncwarp();
-                flush_tiles(s_rslot[warp][h], s_rmask[warp][h], head[h], 2 * k0 + h * n + ntile[h], nt, lane, p);
-                ntile[h] += nt;
+                flush_tiles<kStage>(s_rslot[warp][r], s_rmask[warp][r], head[r], 2 * NPART * k0 + r * n + ntile[r], nt,
+                                    lane, p);
+                ntile[r] += nt;
             }
             if (lane == 0) {
-                p.half_start[2 * ci + h] = 2 * k0 + h * n;
-                p.half_len[2 * ci + h] = ntile[h];
+                const size_t hidx = (size_t)(r >> 1) * p.reg_stride + 2 * ci + (r & 1);
+                p.half_start[hidx] = 2 * NPART * k0 + r * n;
+                p.half_len[hidx] = ntile[r];
             }
         }
         __syncwarp();
@@ -220,7 +255,12 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
             p.ci_len_inner[ci] = out;
             atomicAdd(&p.st->inner_count, (unsigned long long)out);
             // post-prune sorting: the force kernel's work for ci and its histogram
-            const int key = TILES ? ntile[0] + ntile[1] : out;
+            int key = out;
+            if (TILES) {
+                key = 0;
+#pragma unroll
+                for (int r = 0; r < kSets; ++r) key += ntile[r];
+            }
             p.len_key[ci] = key;
             if (p.len_hist) atomicAdd(&p.len_hist[min(key, NB_LEN_BINS - 1)], 1);
         }
@@ -252,9 +292,13 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     // work_prune and inner_count were reset by the snapshot gather before this launch
     int blocks = pl->num_sms * 4;
     blocks = min(blocks, (pl->nc_max + kPruneThreads / 32 - 1) / (kPruneThreads / 32));
-    if (p.vt_slot)
-        k_prune<true><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
+    p.clus_home = pl->clus_home;
+    p.reg_stride = 2 * pl->nc_max;
+    if (!p.vt_slot)
+        k_prune<false, 1><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
+    else if (pl->vt_parts == 2)
+        k_prune<true, 2><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
     else
-        k_prune<false><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
+        k_prune<true, 1><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -41,6 +41,9 @@ NB_LIST_INNER = 1
 NB_FLAG_COUNT_PAIRS = 0x1
 NB_FLAG_NO_LIST_SORT = 0x2
 NB_FLAG_CLUSTER_TILES = 0x4
+NB_PART_ALL = 0
+NB_PART_LOCAL = 1
+NB_PART_NONLOCAL = 2
 NB_COUL_EWALD = 0
 NB_COUL_RF = 1
 NB_COUL_SHIFT = 0x1
@@ -104,6 +107,8 @@ SIGNATURES = {
     "nb_pairlist_export_tiles": (_I, [_P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P]),
     "nb_set_coulomb": (_I, [_P, _I, ctypes.c_float, ctypes.c_uint]),
     "nb_set_flags": (_I, [_P, ctypes.c_uint]),
+    "nb_set_home": (_I, [_P, _I]),
+    "nb_forces_part": (_I, [_P, _I, _P, _P, _P, _I, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
     "nb_backward": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P, _P]),
     "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
                                ctypes.POINTER(ctypes.c_uint), _P]),
@@ -212,6 +217,24 @@ def nb_forces(pl, coords, q, type_, ljparams, rc, beta, forces, energies=None, s
                                     float(beta), _dev(forces, torch.float32, 3 * n, "forces"),
                                     _dev(energies, torch.float64, 2 * n_systems, "energies", True),
                                     _stream(stream)))
+
+
+def nb_forces_part(pl, part, coords, q, type_, ljparams, rc, beta, forces=None, energies=None, stream=None,
+                   n_systems=1) -> None:
+    """One part (NB_PART_ALL / NB_PART_LOCAL / NB_PART_NONLOCAL) of nb_forces; see nb.h."""
+    n = coords.numel() // 3
+    ntype = int(ljparams.shape[0])
+    _check(load_library().nb_forces_part(pl, int(part), _dev(coords, torch.float32, 3 * n, "coords"),
+                                         _dev(q, torch.float32, n, "q"), _dev(type_, torch.int32, n, "type"), ntype,
+                                         _dev(ljparams, torch.float32, 2 * ntype * ntype, "ljparams"), float(rc),
+                                         float(beta), _dev(forces, torch.float32, 3 * n, "forces", True),
+                                         _dev(energies, torch.float64, 2 * n_systems, "energies", True),
+                                         _stream(stream)))
+
+
+def nb_set_home(pl, n_home: int) -> None:
+    """Atoms [0, n_home) are home atoms, the rest halo atoms (see nb.h)."""
+    _check(load_library().nb_set_home(pl, int(n_home)))
 
 
 def nb_backward(pl, coords, q, type_, ljparams, rc, beta, g, grad_x, grad_q, grad_lj, stream=None) -> None:
@@ -349,6 +372,17 @@ class Pairlist:
         if energies is None and want_energy:
             energies = torch.empty(2 * self.n_systems, dtype=torch.float64, device=coords.device)
         nb_forces(self.handle, coords, q, type_, ljparams, rc, beta, forces, energies, stream, self.n_systems)
+        return forces, energies
+
+    def set_home(self, n_home: int) -> None:
+        nb_set_home(self.handle, n_home)
+
+    def forces_part(self, part, coords, q, type_, ljparams, rc, beta, forces=None, energies=None, stream=None):
+        """nb_forces_part; returns (forces, energies) (forces is not written by the local part)."""
+        if forces is None and part != NB_PART_LOCAL:
+            forces = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=coords.device)
+        nb_forces_part(self.handle, part, coords, q, type_, ljparams, rc, beta, forces, energies, stream,
+                       self.n_systems)
         return forces, energies
 
     def backward(self, coords, q, type_, ljparams, rc, beta, g, stream=None):
