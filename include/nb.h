@@ -63,7 +63,7 @@ extern "C" {
 #define NB_DEV_STALE_PRUNE 0x10u     /* atoms moved more than (r_inner - rc)/2 since the prune */
 #define NB_DEV_EXCL_OVERFLOW 0x20u   /* >256 exclusions in one 8-atom cluster, an index outside [0, n),
                                         or more than 8 excluded pairs per atom on average */
-#define NB_DEV_CLUSTER_OVERFLOW 0x40u /* more than 512 list entries for one i-cluster */
+#define NB_DEV_CLUSTER_OVERFLOW 0x40u /* reserved (not raised: an i-cluster's list length is unbounded) */
 #define NB_DEV_BAD_TYPE 0x80u         /* an LJ type outside [0, ntype) (treated as type 0) */
 
 /* Which list nb_pairlist_export() copies. */
@@ -165,7 +165,7 @@ int nb_pairlist_destroy(nb_pairlist *pl);
  * duplicated. Mask bit a*8+b is atom a of ci with atom b of cj.
  * After the search the forces use the outer list until nb_prune runs.
  * Device errors: NB_DEV_LIST_OVERFLOW, NB_DEV_COLUMN_OVERFLOW,
- * NB_DEV_NONFINITE, NB_DEV_EXCL_OVERFLOW, NB_DEV_CLUSTER_OVERFLOW.
+ * NB_DEV_NONFINITE, NB_DEV_EXCL_OVERFLOW.
  */
 int nb_search(nb_pairlist *pl, const float *coords, const float *box, float rlist,
               const int *excl_off, const int *excl_idx, void *stream);

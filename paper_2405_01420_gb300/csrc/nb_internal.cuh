@@ -10,7 +10,6 @@
 #define NB_CLUSTER 8            // atoms per cluster (i and j)
 #define NB_MAX_COL_ATOMS 4096   // atoms per grid column the per-column sort can hold
 #define NB_MAX_TYPES 32         // LJ types (table of ntype^2 float4 in shared memory)
-#define NB_CI_ENTRY_BUF 512     // list entries one i-cluster may own
 #define NB_CI_EXCL_BUF 256      // exclusions within one i-cluster
 #define NB_SHIFT_CENTER 13      // shift index of S = (0, 0, 0)
 #define NB_LEN_BINS 512         // list-length histogram bins (lengths >= 511 share the last)

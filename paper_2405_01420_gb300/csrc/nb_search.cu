@@ -6,8 +6,8 @@
 // column tests the clusters cj >= ci, one per lane, by bounding-box distance.
 // Kept pairs get a shift index and a 64-bit mask (bit a*8+b: atom a of ci
 // with atom b of cj) of real, non-excluded, non-duplicated atom pairs. The
-// warp collects its entries in shared memory, reserves space in the list
-// with one atomic, and writes them out coalesced.
+// warp stages the kept pairs, reserves space in the list with one atomic,
+// and writes them out, coalesced.
 //
 // Half list: (ci, cj, S) and (cj, ci, -S) are the same interactions, so only
 // cj >= ci is kept; for cj == ci the shift S = 0 keeps b > a and of each
@@ -49,12 +49,134 @@ __device__ __forceinline__ unsigned long long row_mask(int n_real) {
 
 __device__ __forceinline__ int image_of(int ju, int n) { return ju < 0 ? -1 : (ju >= n ? 1 : 0); }
 
+constexpr int kExclTab = 64;  // clusters holding excluded partners of one i-cluster
+constexpr int kSearchBuf = 128;  // kept pairs of one i-cluster staged in shared memory
+
+// Per-warp shared state of the candidate walk.
+struct WalkShared {
+    int incl[32];   // inclusive prefix of the candidates of the batch's columns
+    int cs[32];     // first candidate cluster of each column
+    int len[32];    // candidate clusters per z image of each column
+    int zpack[32];  // kz + 1 of the column's z images, 2 bits each (up to 3)
+    int sbase[32];  // shift index without the z part: (1 - kx) * 9 + (1 - ky) * 3 + 1
+    float ox[32], oy[32];
+};
+
+// Walks the candidate clusters of ci: the grid columns within rl_col of its
+// bounding box (with periodic images), their z images, and in each the
+// clusters cj >= ci. A batch of 32 columns is read in parallel (one per
+// lane); a warp scan lays their candidates end to end, and the lanes then
+// test 32 candidates at a time (the column of a candidate found by binary
+// search over the scan). visit(c, sidx, m, r) is called by every lane that
+// keeps its pair (bounding boxes within rl2 and a non-empty mask m of real,
+// non-excluded, non-duplicated atom pairs), with its rank r among the kept
+// ones; the order is fixed, so two walks make the same calls.
+template <typename Visit>
+__device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, const float4 lo, const float4 hi, int ni,
+                                               const nb_sys &S, const int *tab_c, const unsigned long long *tab_m,
+                                               int ntab, WalkShared &ws, int lane, Visit visit) {
+    int nout = 0;
+    const int jx0 = max((int)floorf((lo.x - p.rl_col) * S.inv_sx), -S.ncx);
+    const int jx1 = min((int)floorf((hi.x + p.rl_col) * S.inv_sx), 2 * S.ncx - 1);
+    const int jy0 = max((int)floorf((lo.y - p.rl_col) * S.inv_sy), -S.ncy);
+    const int jy1 = min((int)floorf((hi.y + p.rl_col) * S.inv_sy), 2 * S.ncy - 1);
+    const int nyr = jy1 - jy0 + 1;
+    const int ncols = (jx1 - jx0 + 1) * nyr;
+    for (int kb = 0; kb < ncols; kb += 32) {
+        // this lane's column: its candidate range and z images
+        const int k = kb + lane;
+        int cs = 0, len = 0, zpack = 0, nz = 0, sbase = 0;
+        float ox = 0.0f, oy = 0.0f;
+        if (k < ncols) {
+            const int jxu = jx0 + k / nyr, jyu = jy0 + k % nyr;
+            const int kx = image_of(jxu, S.ncx), ky = image_of(jyu, S.ncy);
+            const int jx = jxu - kx * S.ncx, jy = jyu - ky * S.ncy;
+            ox = (float)kx * S.box.x;  // j image at x_b + ox, i.e. S_x = -ox
+            oy = (float)ky * S.box.y;
+            const int col = S.col_off + jx * S.ncy + jy;
+            const int c0 = p.col_clus_start[col], c1 = p.col_clus_start[col + 1];
+            cs = max(c0, ci);
+            len = max(c1 - cs, 0);
+            sbase = (1 - kx) * 9 + (1 - ky) * 3 + 1;
+            for (int kz = -1; kz <= 1; ++kz) {
+                const float oz = (float)kz * S.box.z;
+                if (lo.z - p.rl_col > oz + S.box.z || hi.z + p.rl_col < oz) continue;
+                zpack |= (kz + 1) << (2 * nz);
+                ++nz;
+            }
+        }
+        const int tot = len * nz;
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        ws.incl[lane] = incl;
+        ws.cs[lane] = cs;
+        ws.len[lane] = len;
+        ws.zpack[lane] = zpack;
+        ws.sbase[lane] = sbase;
+        ws.ox[lane] = ox;
+        ws.oy[lane] = oy;
+        __syncwarp();
+        for (int u0 = 0; u0 < total; u0 += 32) {
+            const int u = u0 + lane;
+            bool keep = false;
+            unsigned long long m = 0;
+            int c = 0, sidx = 0;
+            if (u < total) {
+                int o = 0;  // the column holding candidate u: columns with incl <= u come first
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (ws.incl[o + step - 1] <= u) o += step;
+                const int lo_u = ws.len[o];
+                const int first = (o == 0 ? 0 : ws.incl[o - 1]);
+                const int w = u - first;                         // index within the column's candidates
+                const int zi = (w >= lo_u) + (w >= 2 * lo_u);    // which z image (at most 3)
+                const int kz = ((ws.zpack[o] >> (2 * zi)) & 3) - 1;
+                c = ws.cs[o] + (w - zi * lo_u);
+                sidx = ws.sbase[o] - kz;
+                const float oxo = ws.ox[o], oyo = ws.oy[o], oz = (float)kz * S.box.z;
+                const float4 bl = p.bbox[2 * c], bh = p.bbox[2 * c + 1];
+                const float gx = fmaxf(0.0f, fmaxf((bl.x + oxo) - hi.x, lo.x - (bh.x + oxo)));
+                const float gy = fmaxf(0.0f, fmaxf((bl.y + oyo) - hi.y, lo.y - (bh.y + oyo)));
+                const float gz = fmaxf(0.0f, fmaxf((bl.z + oz) - hi.z, lo.z - (bh.z + oz)));
+                keep = gx * gx + gy * gy + gz * gz < p.rl2;
+                if (c == ci && sidx < NB_SHIFT_CENTER) keep = false;
+                if (keep) {
+                    const int nj = __float_as_int(bl.w);
+                    m = row_mask(ni) * (unsigned long long)((1u << nj) - 1u);
+                    if (c == ci) m &= (sidx == NB_SHIFT_CENTER) ? kUpperStrict : ~kDiagonal;
+                    for (int q = 0; q < ntab; ++q)
+                        if (tab_c[q] == c) m &= ~tab_m[q];
+                    keep = (m != 0ull);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) visit(c, sidx, m, nout + __popc(bal & ((1u << lane) - 1u)));
+            nout += __popc(bal);
+        }
+    }
+    return nout;
+}
+
+// One warp per i-cluster. The exclusions of ci's atoms are folded into a
+// table of (j cluster, 64-bit mask of excluded pairs). The walk stages the
+// kept pairs in shared memory, one atomic reserves exactly that many list
+// entries, and the warp copies them out coalesced; a list longer than the
+// stage is written by a second walk (the same decisions) instead.
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
-    extern __shared__ int4 s_entries[];  // kSearchWarps * NB_CI_ENTRY_BUF
     __shared__ int2 s_excl[kSearchWarps][NB_CI_EXCL_BUF];
     __shared__ int s_nexcl[kSearchWarps];
+    __shared__ int s_tab_c[kSearchWarps][kExclTab];
+    __shared__ unsigned long long s_tab_m[kSearchWarps][kExclTab];
+    __shared__ int s_ntab[kSearchWarps];
+    __shared__ WalkShared s_walk[kSearchWarps];
+    __shared__ int4 s_buf[kSearchWarps][kSearchBuf];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int4 *buf = s_entries + warp * NB_CI_ENTRY_BUF;
     const int nc = p.st->nc;
 
     for (int ci = blockIdx.x * kSearchWarps + warp; ci < nc; ci += gridDim.x * kSearchWarps) {
@@ -85,79 +207,62 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
             if (lane == 0) atomicOr(&p.st->err, NB_DEV_EXCL_OVERFLOW);
             nex = NB_CI_EXCL_BUF;
         }
-
-        int nout = 0;
-        int jx0 = max((int)floorf((lo.x - p.rl_col) * S.inv_sx), -S.ncx);
-        int jx1 = min((int)floorf((hi.x + p.rl_col) * S.inv_sx), 2 * S.ncx - 1);
-        int jy0 = max((int)floorf((lo.y - p.rl_col) * S.inv_sy), -S.ncy);
-        int jy1 = min((int)floorf((hi.y + p.rl_col) * S.inv_sy), 2 * S.ncy - 1);
-        for (int jxu = jx0; jxu <= jx1; ++jxu) {
-            const int kx = image_of(jxu, S.ncx);
-            const int jx = jxu - kx * S.ncx;
-            const float ox = (float)kx * S.box.x;  // j image at x_b + ox, i.e. S_x = -ox
-            for (int jyu = jy0; jyu <= jy1; ++jyu) {
-                const int ky = image_of(jyu, S.ncy);
-                const int jy = jyu - ky * S.ncy;
-                const float oy = (float)ky * S.box.y;
-                const int col = S.col_off + jx * S.ncy + jy;
-                const int c0 = p.col_clus_start[col], c1 = p.col_clus_start[col + 1];
-                if (c1 <= ci) continue;  // every cluster of this column precedes ci
-                const int cs = max(c0, ci);
-                for (int kz = -1; kz <= 1; ++kz) {
-                    const float oz = (float)kz * S.box.z;
-                    if (lo.z - p.rl_col > oz + S.box.z || hi.z + p.rl_col < oz) continue;
-                    const int sidx = (1 - kx) * 9 + (1 - ky) * 3 + (1 - kz);
-                    for (int cb = cs; cb < c1; cb += 32) {
-                        const int c = cb + lane;
-                        bool keep = false;
-                        unsigned long long m = 0;
-                        if (c < c1) {
-                            const float4 bl = p.bbox[2 * c], bh = p.bbox[2 * c + 1];
-                            float gx = fmaxf(0.0f, fmaxf((bl.x + ox) - hi.x, lo.x - (bh.x + ox)));
-                            float gy = fmaxf(0.0f, fmaxf((bl.y + oy) - hi.y, lo.y - (bh.y + oy)));
-                            float gz = fmaxf(0.0f, fmaxf((bl.z + oz) - hi.z, lo.z - (bh.z + oz)));
-                            keep = gx * gx + gy * gy + gz * gz < p.rl2;
-                            if (c == ci && sidx < NB_SHIFT_CENTER) keep = false;
-                            if (keep) {
-                                const int nj = __float_as_int(bl.w);
-                                m = row_mask(ni) * (unsigned long long)((1u << nj) - 1u);
-                                if (c == ci) m &= (sidx == NB_SHIFT_CENTER) ? kUpperStrict : ~kDiagonal;
-                                for (int e = 0; e < nex; ++e) {
-                                    const int2 ex = s_excl[warp][e];
-                                    if ((ex.y >> 3) == c) m &= ~(1ull << (ex.x * 8 + (ex.y & 7)));
-                                }
-                                keep = (m != 0ull);
-                            }
-                        }
-                        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                        if (keep) {
-                            const int r = nout + __popc(bal & ((1u << lane) - 1u));
-                            if (r < NB_CI_ENTRY_BUF)
-                                buf[r] = make_int4(c, sidx, (int)(unsigned)(m & 0xffffffffu),
-                                                   (int)(unsigned)(m >> 32));
-                        }
-                        nout += __popc(bal);
+        // fold them by j cluster (a handful of clusters per i-cluster)
+        if (lane == 0) {
+            int ntab = 0;
+            for (int e = 0; e < nex; ++e) {
+                const int2 ex = s_excl[warp][e];
+                const int cj = ex.y >> 3;
+                const unsigned long long bit = 1ull << (ex.x * 8 + (ex.y & 7));
+                int k = 0;
+                while (k < ntab && s_tab_c[warp][k] != cj) ++k;
+                if (k == ntab) {
+                    if (ntab == kExclTab) {
+                        atomicOr(&p.st->err, NB_DEV_EXCL_OVERFLOW);
+                        continue;
                     }
+                    s_tab_c[warp][k] = cj;
+                    s_tab_m[warp][k] = 0ull;
+                    ++ntab;
                 }
+                s_tab_m[warp][k] |= bit;
             }
-        }
-        if (nout > NB_CI_ENTRY_BUF) {
-            if (lane == 0) atomicOr(&p.st->err, NB_DEV_CLUSTER_OVERFLOW);
-            nout = NB_CI_ENTRY_BUF;
+            s_ntab[warp] = ntab;
         }
         __syncwarp();
+        const int ntab = s_ntab[warp];
+        const int *tab_c = s_tab_c[warp];
+        const unsigned long long *tab_m = s_tab_m[warp];
+
+        // first walk: kept pairs into the warp's buffer (while they fit)
+        int4 *buf = s_buf[warp];
+        const int nout = walk_candidates(p, ci, lo, hi, ni, S, tab_c, tab_m, ntab, s_walk[warp], lane,
+                                         [buf](int c, int sidx, unsigned long long m, int r) {
+                                             if (r < kSearchBuf)
+                                                 buf[r] = make_int4(c, sidx, (int)(unsigned)(m & 0xffffffffu),
+                                                                    (int)(unsigned)(m >> 32));
+                                         });
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&p.st->list_count, (unsigned long long)nout);
         base = __shfl_sync(0xffffffffu, base, 0);
+        int nkept = nout;
+        __syncwarp();
         if (base + (unsigned long long)nout > p.cap) {
             if (lane == 0) atomicOr(&p.st->err, NB_DEV_LIST_OVERFLOW);
-            nout = 0;
+            nkept = 0;
             base = 0;
+        } else if (nout <= kSearchBuf) {
+            for (int k = lane; k < nout; k += 32) p.outer[base + k] = buf[k];
+        } else {  // a long list: a second walk writes it directly
+            int4 *out = p.outer + base;
+            walk_candidates(p, ci, lo, hi, ni, S, tab_c, tab_m, ntab, s_walk[warp], lane,
+                            [out](int c, int sidx, unsigned long long m, int r) {
+                                out[r] = make_int4(c, sidx, (int)(unsigned)(m & 0xffffffffu), (int)(unsigned)(m >> 32));
+                            });
         }
-        for (int k = lane; k < nout; k += 32) p.outer[base + k] = buf[k];
         if (lane == 0) {
             p.ci_start[ci] = (int)base;
-            p.ci_len[ci] = nout;
+            p.ci_len[ci] = nkept;
             p.ci_len_inner[ci] = 0;
         }
         __syncwarp();
@@ -186,17 +291,8 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
     p.rl2 = rl2;
     p.rl_col = rl_col;
     p.cap = (unsigned long long)pl->cap;
-    const size_t smem = sizeof(int4) * kSearchWarps * NB_CI_ENTRY_BUF;
-    // once per device (outside any stream capture: the first search on a
-    // device must not be captured)
-    static bool attr_done[64] = {};
-    if (pl->device < 0 || pl->device >= 64 || !attr_done[pl->device]) {
-        cudaError_t e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (pl->device >= 0 && pl->device < 64) attr_done[pl->device] = true;
-    }
     int blocks = (pl->nc_max + kSearchWarps - 1) / kSearchWarps;
     blocks = min(blocks, pl->num_sms * 16);
-    k_search<<<blocks, kSearchWarps * 32, smem, s>>>(p);
+    k_search<<<blocks, kSearchWarps * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
