@@ -13,16 +13,23 @@
 // 1.04 nm about 60% of these pair slots are in range, against 40% for 8 x 8
 // cluster tiles with empty half-tiles skipped.
 //
+//  - The pair arithmetic runs on the packed two-wide FP32 instructions:
+//    rows (0, 1) and (2, 3) of the half are two row pairs, each evaluated
+//    against the lane's j atom by nb_pair_x2 (one packed operation for two
+//    pairs, same rounding per pair as nb_pair). The kernel is bound by
+//    instruction issue, and packing halves the issue slots of the FP32 work.
 //  - j data (coordinates and charge, type, mask word) of group g + 1 are
 //    copied into shared memory with cp.async while group g computes; the
-//    shift vectors come from a per-warp shared copy of the system's 27.
+//    shift vectors come from a per-warp shared copy of the system's 27; the
+//    row pairs' positions and charges and their LJ coefficients by j type
+//    sit in per-warp shared tables, already in packed order.
 //  - j forces stay in registers over the 4 rows and go out with one
 //    16-byte vector atomic per lane (fsort is float4 per slot).
 //  - i forces stay in registers over the whole half and are reduced across
 //    the warp at its end, one vector atomic per row.
 //  - Energies: FP32 per lane over a half, FP64 across halves, FP64 atomics
 //    per system when the warp moves to another system or finishes.
-#include "nb_pair.cuh"
+#include "nb_pair_x2.cuh"
 #include "nb_warp.cuh"
 
 namespace {
@@ -44,6 +51,7 @@ struct VtParams {
     int ntype;
     float rc6inv, rc12inv;
     nb_coul cc;
+    nb_coul2 cc2;             // the same constants in packed form
     float stale_prune2;
     int pad_slot;             // never holds an atom: far away, q = 0, type 0
     int reg0, nreg;           // regions of gathered tiles to compute (0 local or all, 1 non-local)
@@ -90,14 +98,17 @@ __device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, int t
 
 // j-stationary kernel over gathered tiles. A warp takes one half i-cluster
 // (4 i rows) at a time; its tiles are read in groups of 4 (32 j atoms, one
-// per lane), and each lane computes its j atom against the 4 rows. j forces
-// stay in registers for the 4 pairs and go out with one 16-byte vector
-// atomic per lane (fsort is float4 per slot);
-// i forces stay in registers for the whole half and are reduced across the
-// warp at its end. Group g + 1 is copied (cp.async) into the other buffer
-// while group g is computed.
-// 768 / THREADS resident CTAs per SM leave 80 registers per thread: enough
-// to keep the 4 rows' positions, LJ rows and forces in registers.
+// per lane), and each lane computes its j atom against the 4 rows, two row
+// pairs of packed arithmetic. j forces stay in registers for the 4 pairs
+// and go out with one 16-byte vector atomic per lane (fsort is float4 per
+// slot); i forces stay in registers for the whole half and are reduced
+// across the warp at its end. Group g + 1 is copied (cp.async) into the
+// other buffer while group g is computed.
+// Dynamic shared memory: the ntype x ntype LJ table, then per warp 3 float4
+// per j type (see s_lj2).
+// 768 / THREADS resident CTAs per SM leave 80 registers per thread: the 4
+// rows' forces and the j atom's data stay in registers; the rows' positions,
+// charges and LJ coefficients are read from the per-warp shared tables.
 template <bool ENERGY, bool COUNT, int THREADS, int COUL>
 __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p) {
     constexpr int kWarps = THREADS / 32;
@@ -107,6 +118,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     int shift_sys = -1;
     __shared__ float4 s_xi[kWarps][4];
     __shared__ int s_tr[kWarps][4];
+    __shared__ float4 s_xp[kWarps][2][2];  // row pair k: (x_a, x_b, y_a, y_b), (z_a, z_b, fq_a, fq_b)
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -125,6 +137,10 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per warp, for the current half, by j type t: (C6, C6, C12, C12) of
+    // row pairs (0, 1) and (2, 3) at [3t], [3t + 1], minus the 4 rows' LJ
+    // shifts at [3t + 2]
+    float4 *s_lj2 = s_lj + nt2 + 3 * p.ntype * warp;
     const unsigned nhalf = 2u * (unsigned)p.st->nc;  // halves per region
     const unsigned nwork = nhalf * (unsigned)p.nreg;
     double ecd = 0.0, eljd = 0.0;
@@ -160,40 +176,54 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             s_xi[warp][lane] = make_float4(x.x, x.y, x.z, x.w * NB_COULOMB_F);
             s_tr[warp][lane] = p.tsort[ibase + lane] * p.ntype;
         }
-        float3 fi[4];
+        float2 fix[2], fiy[2], fiz[2];  // row pair k: rows 2k (.x) and 2k + 1 (.y)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) fi[a] = make_float3(0.f, 0.f, 0.f);
-        float ec = 0.0f, elj = 0.0f;
+        for (int k = 0; k < 2; ++k) fix[k] = fiy[k] = fiz[k] = make_float2(0.f, 0.f);
+        float2 ec2 = make_float2(0.f, 0.f), elj2 = make_float2(0.f, 0.f);
         const int ngroups = (t1 - t0 + 3) >> 2;
         cp_async_wait_all();
         __syncwarp();
-        float4 xr[4];
-        int trr[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            xr[a] = s_xi[warp][a];
-            trr[a] = s_tr[warp][a];
+        if (lane < 2) {
+            const float4 a = s_xi[warp][2 * lane], b = s_xi[warp][2 * lane + 1];
+            s_xp[warp][lane][0] = make_float4(a.x, b.x, a.y, b.y);
+            s_xp[warp][lane][1] = make_float4(a.z, b.z, a.w, b.w);
         }
+        for (int t = lane; t < p.ntype; t += 32) {
+            const float4 c0 = s_lj[s_tr[warp][0] + t], c1 = s_lj[s_tr[warp][1] + t];
+            const float4 c2 = s_lj[s_tr[warp][2] + t], c3 = s_lj[s_tr[warp][3] + t];
+            s_lj2[3 * t + 0] = make_float4(c0.x, c1.x, c0.y, c1.y);
+            s_lj2[3 * t + 1] = make_float4(c2.x, c3.x, c2.y, c3.y);
+            s_lj2[3 * t + 2] = make_float4(-c0.z, -c1.z, -c2.z, -c3.z);
+        }
+        __syncwarp();
         for (int g = 0; g < ngroups; ++g) {
             VtStage &cs = s_st[warp][g & 1];
             const float4 xj = cs.xj[lane];
             const float4 S = s_shift[warp][(unsigned)v >> 27];
             const int tj = cs.tj[lane];
-            const unsigned mrow = cs.m[lane] >> (lane & 7);
+            const unsigned mrow = cs.m[lane] >> (lane & 7);  // bit 8a: row a
             const int slot = v & 0x07ffffff;
-            float3 fj = make_float3(0.f, 0.f, 0.f);
+            const float2 nxjx = nb_f2(-xj.x), nxjy = nb_f2(-xj.y), nxjz = nb_f2(-xj.z), qj = nb_f2(xj.w);
+            const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z);
+            const float4 nsh = s_lj2[3 * tj + 2];
+            float2 gjx = make_float2(0.f, 0.f), gjy = gjx, gjz = gjx;
             int vn = 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
+            for (int k = 0; k < 2; ++k) {
+                if (k == 1 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
                     vn = stage_group(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
-                const float4 xi = xr[a];
-                const int c1 = nb_pair<true, ENERGY, COUL>(xi, xi.w, xj, s_lj[trr[a] + tj], S.x, S.y, S.z,
-                                                     ((mrow >> (8 * a)) & 1u) != 0u, p.cc, fi[a], fj, ec, elj);
-                if (COUNT) cnt += c1;
+                const float4 xa = s_xp[warp][k][0], xb = s_xp[warp][k][1];
+                const int c2 = nb_pair_x2<ENERGY, COUL>(
+                    make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xb.x, xb.y),
+                    make_float2(xb.z, xb.w), nxjx, nxjy, nxjz, qj, Sx, Sy, Sz, s_lj2[3 * tj + k],
+                    k == 0 ? make_float2(nsh.x, nsh.y) : make_float2(nsh.z, nsh.w), ((mrow >> (16 * k)) & 1u) != 0u,
+                    ((mrow >> (16 * k + 8)) & 1u) != 0u, p.cc.rc2, p.cc2, fix[k], fiy[k], fiz[k], gjx, gjy, gjz, ec2,
+                    elj2);
+                if (COUNT) cnt += c2;
             }
             if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
-                atomicAdd(reinterpret_cast<float4 *>(p.fsort) + slot, make_float4(fj.x, fj.y, fj.z, 0.0f));
+                atomicAdd(reinterpret_cast<float4 *>(p.fsort) + slot,
+                          make_float4(-(gjx.x + gjx.y), -(gjy.x + gjy.y), -(gjz.x + gjz.y), 0.0f));
             v = vn;
             cp_async_wait_all();
             __syncwarp();
@@ -201,11 +231,15 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         // i forces: row a component c is value 4a + c; lanes 2k hold value k
         float r[16];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            r[4 * a + 0] = fi[a].x;
-            r[4 * a + 1] = fi[a].y;
-            r[4 * a + 2] = fi[a].z;
-            r[4 * a + 3] = 0.0f;
+        for (int k = 0; k < 2; ++k) {
+            r[8 * k + 0] = fix[k].x;
+            r[8 * k + 1] = fiy[k].x;
+            r[8 * k + 2] = fiz[k].x;
+            r[8 * k + 3] = 0.0f;
+            r[8 * k + 4] = fix[k].y;
+            r[8 * k + 5] = fiy[k].y;
+            r[8 * k + 6] = fiz[k].y;
+            r[8 * k + 7] = 0.0f;
         }
         reduce_scatter<16>(r, lane);
         // lane 8a holds row a's x; its y and z sit 2 and 4 lanes up
@@ -214,8 +248,8 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         if ((lane & 7) == 0)
             atomicAdd(reinterpret_cast<float4 *>(p.fsort) + ibase + (lane >> 3), make_float4(r[0], ry, rz, 0.0f));
         if (ENERGY) {
-            ecd += (double)ec;
-            eljd += (double)elj;
+            ecd += (double)(ec2.x + ec2.y);
+            eljd += (double)(elj2.x + elj2.y);
         }
         __syncwarp();
     }
@@ -273,6 +307,7 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     p.rc6inv = (float)rc6;
     p.rc12inv = (float)(rc6 * rc6);
     const int coul = nb_fill_coul(p.cc, rc, beta, pl->coul_kind, pl->eps_rf, pl->coul_flags);
+    p.cc2 = nb_pack_coul(p.cc);
     p.stale_prune2 = stale_prune2;
     p.pad_slot = pl->nc_max * NB_CLUSTER;
     const int e = energies ? 1 : 0;
@@ -280,7 +315,7 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     const int threads = pl->force_threads == 128 ? 128 : 256;
     VtFn fn = e ? (c ? pick_vt<true, true>(threads, coul) : pick_vt<true, false>(threads, coul))
                 : (c ? pick_vt<false, true>(threads, coul) : pick_vt<false, false>(threads, coul));
-    const size_t smem = sizeof(float4) * (size_t)ntype * ntype;
+    const size_t smem = sizeof(float4) * ((size_t)ntype * ntype + 3 * (size_t)ntype * (threads / 32));
     Occ &occ = g_vt_occ[coul][e][c][threads == 128];
     if (occ.per_sm == 0 || occ.smem != smem) {  // resident CTAs for this LJ table size
         int n = 0;
