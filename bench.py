@@ -44,6 +44,7 @@ N_WATERS = 32000
 RC, RLIST, R_INNER = 1.0, 1.1, 1.04
 PRUNE_INTERVAL = 10
 SIGMA = 0.001
+KERNEL_SAMPLE = 10  # the force kernel is timed on 1 evaluation in KERNEL_SAMPLE
 # FP32 operations per in-range pair in the force + energy formula as the
 # kernel evaluates it (FMA = 2): d 3, r^2 5, rsqrt 1, 1/r^2 and 1/r^6 3, C6/r^6 and
 # C12/r^12 3, LJ force scalar 4, r 1, beta r 1, exp 2, erfcx P/Q 18,
@@ -70,7 +71,7 @@ def workload_desc(evals: int) -> dict:
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--evals", type=int, default=100)
@@ -83,7 +84,7 @@ def parse_args():
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 50 ms while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -99,7 +100,7 @@ class ClockSampler:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -623,7 +624,7 @@ def run_ours(args, rank, world, local):
         restart()
         for i in range(args.evals):
             if kernel_events is not None:
-                nb.nb_set_timing_events(eng.pl.handle, *kernel_events[i])
+                nb.nb_set_timing_events(eng.pl.handle, *kernel_events.get(i, (None, None)))
             x = frame_src(i)
             eng.compute(x, q, typ, lj, forces, energies[i])
             if out_forces is not None:
@@ -654,8 +655,11 @@ def run_ours(args, rank, world, local):
         one_step(lambda i: frames_d[i])
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.evals)]
-    for a, b in ev:  # torch only times events it has recorded once; libnb re-records them at the kernel
+    # the force kernel is timed with an event pair on a sample of the evaluations (an event record costs
+    # about a microsecond of stream time), whose positions cycle through the prune interval
+    ev = {i: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for i in range(args.evals) if i % KERNEL_SAMPLE == (i // KERNEL_SAMPLE) % KERNEL_SAMPLE}
+    for a, b in ev.values():  # torch only times events it has recorded once; libnb re-records them at the kernel
         a.record(stream)
         b.record(stream)
     sampler = ClockSampler(local) if rank == 0 else None
@@ -674,7 +678,7 @@ def run_ours(args, rank, world, local):
         t1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(t0.elapsed_time(t1))
-        kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        kern_ms.append(statistics.mean(a.elapsed_time(b) for a, b in ev.values()))
         searches, prunes = eng.n_search, eng.n_prune
     clocks = sampler.stop() if sampler else None
     err = eng.check()
@@ -682,7 +686,7 @@ def run_ours(args, rank, world, local):
 
     ms_step = dist_max(statistics.mean(step_ms), world)
     value = replica_throughput(pairs_per_step * args.steps, sum(step_ms) / 1e3, world)
-    kern_ms_per_launch = statistics.mean(kern_ms) / args.evals
+    kern_ms_per_launch = statistics.mean(kern_ms)
     pairs_per_eval = pairs_per_step / args.evals
 
     # end to end through the public API: frames from pinned host memory each

@@ -240,6 +240,27 @@ int nb_status(nb_pairlist *pl, unsigned *error_word, int clear, void *stream);
 /* Fill *out with list sizes, counters and radii. Synchronises the stream. */
 int nb_pairlist_stats(nb_pairlist *pl, nb_stats *out, void *stream);
 
+/* The displacement tracker (§III-A's rolling prune needs to know when the
+   buffered list goes stale) and the error word, as of the last completed
+   call in stream order. Squared displacements, as FP32. */
+typedef struct {
+    unsigned error_word;    /* sticky device error bits (NB_DEV_*) */
+    float max_disp2_search; /* largest squared atom displacement since the search */
+    float max_disp2_prune;  /* the same since the last prune */
+} nb_tracker;
+
+/*
+ * Enqueue on `stream` a copy of the tracker into *out (12 bytes of host
+ * memory that the caller owns and keeps valid until the stream has passed
+ * the copy; page-locked memory keeps the copy asynchronous). Does not
+ * synchronise: the values are there once the stream reaches this point,
+ * e.g. after an event recorded right after this call. Lets a driver read
+ * the tracker a few calls late without draining the stream.
+ * Errors: NB_ERR_ARG for NULL arguments, NB_ERR_CUDA if the copy cannot be
+ * enqueued.
+ */
+int nb_tracker_enqueue(nb_pairlist *pl, nb_tracker *out, void *stream);
+
 /*
  * Copy a list to HOST arrays (for tests and inspection). Synchronises.
  *   which  NB_LIST_OUTER or NB_LIST_INNER.

@@ -1,6 +1,7 @@
 // C ABI of the nonbonded library (declared in include/nb.h): argument
 // checks, device buffer ownership, grid sizing and the order of launches.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -349,10 +350,10 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
         return fail(NB_ERR_ARG, "nb_prune: r_inner = %g must be in (0, rlist = %g]", r_inner, pl->rlist);
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
+    // the snapshot gather also clears the list-length histogram that the prune fills
     NB_CUDA(nb_launch_gather(pl, coords, nullptr, nullptr, 1, 1, nullptr, NB_PART_ALL, s));
     const float r2cut = r_inner * r_inner;
     const bool sort = !(pl->flags & NB_FLAG_NO_LIST_SORT);
-    if (sort) NB_CUDA(nb_clear_len_hist(pl, s));
     NB_CUDA(nb_launch_prune(pl, r2cut, stale_bound2(pl->rlist, r_inner), s));
     pl->sorted = 0;
     if (sort) {
@@ -473,6 +474,19 @@ extern "C" int nb_pairlist_stats(nb_pairlist *pl, nb_stats *out, void *stream) {
     out->max_disp_search = std::sqrt(ds);
     out->max_disp_prune = std::sqrt(dp);
     out->error_word = st.err;
+    return ok();
+}
+
+static_assert(sizeof(nb_tracker) == 3 * sizeof(unsigned), "nb_tracker is three 32-bit words");
+static_assert(offsetof(nb_dev_state, err) == offsetof(nb_tracker, error_word) &&
+                  offsetof(nb_dev_state, last_d2_search) == offsetof(nb_tracker, max_disp2_search) &&
+                  offsetof(nb_dev_state, last_d2_prune) == offsetof(nb_tracker, max_disp2_prune),
+              "nb_dev_state starts with the words of nb_tracker");
+
+extern "C" int nb_tracker_enqueue(nb_pairlist *pl, nb_tracker *out, void *stream) {
+    if (!pl || !out) return fail(NB_ERR_ARG, "nb_tracker_enqueue: NULL argument");
+    DeviceGuard g(pl->device);
+    NB_CUDA(cudaMemcpyAsync(out, pl->st, sizeof(nb_tracker), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     return ok();
 }
 

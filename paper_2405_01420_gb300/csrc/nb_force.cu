@@ -5,7 +5,9 @@
 // k_gather   coords/q/type (original order) -> xq (float4 y,q) / tsort in
 //            cluster order; y is the image nearest the search-frame
 //            position. Zeroes the force accumulators, tracks the largest
-//            displacement since the search and since the last prune.
+//            displacement since the search and since the last prune. The
+//            prune's gather (snapshot) records the positions of the prune
+//            and clears the list-length histogram the prune fills.
 // k_force    persistent grid, one warp per i-cluster taken from a work
 //            counter. List entries and their j-cluster data are staged in
 //            shared memory 16 at a time. Lane l owns j-atom b = l & 7 and i-atoms l >> 3 and
@@ -36,7 +38,8 @@ struct GatherParams {
     nb_dev_state *st;
     double *energies;  // [2 nsys] or NULL
     const nb_sys *sys;
-    const int *atom_sys;
+    const int *clus_sys;
+    int *len_hist;  // cleared here ahead of a prune that fills it, or NULL
     int nsys;
     int snapshot;
     int ntype;
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
         if (atom < 0) continue;
         if (p.part == NB_PART_LOCAL ? atom >= p.n_home : (p.part == NB_PART_NONLOCAL && atom < p.n_home)) continue;
         const float4 r = p.xref[slot];
-        const float4 L = p.sys[p.atom_sys[atom]].box;
+        const float4 L = p.sys[p.clus_sys[slot / NB_CLUSTER]].box;  // does not wait for perm
         float x = p.coords[3 * atom + 0], y = p.coords[3 * atom + 1], z = p.coords[3 * atom + 2];
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
             atomicOr(&p.st->err, NB_DEV_NONFINITE);
@@ -106,6 +109,8 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
         }
         if (p.energies && p.part != NB_PART_NONLOCAL)
             for (int k = threadIdx.x; k < 2 * p.nsys; k += blockDim.x) p.energies[k] = 0.0;
+        if (p.len_hist)
+            for (int k = threadIdx.x; k < NB_LEN_BINS; k += blockDim.x) p.len_hist[k] = 0;
     }
 }
 
@@ -373,7 +378,8 @@ cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *
     p.st = pl->st;
     p.energies = energies;
     p.sys = pl->sys;
-    p.atom_sys = pl->atom_sys;
+    p.clus_sys = pl->clus_sys;
+    p.len_hist = (snapshot && !(pl->flags & NB_FLAG_NO_LIST_SORT)) ? pl->len_hist : nullptr;
     p.nsys = pl->nsys;
     p.snapshot = snapshot;
     int blocks = (pl->nc_max * NB_CLUSTER + 255) / 256;

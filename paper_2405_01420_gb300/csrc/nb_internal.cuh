@@ -16,17 +16,19 @@
 #define NB_COULOMB_F 138.935458f
 
 // Device-side state of one pair list (one allocation, zeroed at creation).
+// The first three words are laid out as nb_tracker (nb.h), which
+// nb_tracker_enqueue copies to the host as they are.
 struct nb_dev_state {
     unsigned err;                  // sticky NB_DEV_* bits
+    unsigned last_d2_search;       // max |y - y_search|^2 (float bits) of the last completed call
+    unsigned last_d2_prune;        // max |y - y_prune|^2 (float bits) of the last completed call
     int nc;                        // clusters produced by the last search
     unsigned long long list_count; // outer entries allocated by the last search
     unsigned long long inner_count;// entries kept by the last prune
     unsigned work;                 // work counter of the force kernel
     unsigned work_prune;           // work counter of the prune kernel
-    unsigned cur_d2_search;        // max |y - y_search|^2 (float bits) of the running call
-    unsigned cur_d2_prune;         // max |y - y_prune|^2 (float bits) of the running call
-    unsigned last_d2_search;       // the same values of the last completed call
-    unsigned last_d2_prune;
+    unsigned cur_d2_search;        // the same maxima of the running call
+    unsigned cur_d2_prune;
     unsigned long long npairs;     // in-range pairs counted by the last force call
     unsigned excl_count;           // excluded pairs recorded by the last search
 };
@@ -169,6 +171,8 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
                              float rl_col, cudaStream_t s);
 // part: NB_PART_ALL (every atom), NB_PART_LOCAL (home atoms; zeroes the
 // accumulators and energies), NB_PART_NONLOCAL (halo atoms only).
+// snapshot: the gather of a prune (records the prune positions and, when
+// lists are sorted, clears the list-length histogram).
 cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *q, const int *type,
                              int ntype, int snapshot, double *energies, int part, cudaStream_t s);
 // clus_home[c] bit b = slot b of cluster c holds a home atom (after the grid sort of a search).

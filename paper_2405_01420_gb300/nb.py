@@ -100,6 +100,7 @@ SIGNATURES = {
     "nb_forces": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P]),
     "nb_status": (_I, [_P, ctypes.POINTER(ctypes.c_uint), _I, _P]),
     "nb_pairlist_stats": (_I, [_P, ctypes.POINTER(nb_stats), _P]),
+    "nb_tracker_enqueue": (_I, [_P, _P, _P]),
     "nb_pairlist_export": (_I, [_P, _I, _P, _P, _P, _P, _SZ, ctypes.POINTER(_SZ), _P, _SZ,
                                 ctypes.POINTER(_SZ), _P]),
     "nb_set_timing_events": (_I, [_P, _P, _P]),
@@ -261,6 +262,21 @@ def nb_pairlist_stats(pl, stream=None) -> dict:
     return {name: getattr(s, name) for name, _ in nb_stats._fields_}
 
 
+def nb_tracker_enqueue(pl, host_ptr: int, stream=None) -> None:
+    """Enqueue the 12-byte tracker copy (error word, squared displacement
+    maxima since the search and the prune) to host address host_ptr."""
+    _check(load_library().nb_tracker_enqueue(pl, ctypes.c_void_p(host_ptr), _stream(stream)))
+
+
+def decode_tracker(words) -> dict:
+    """The three 32-bit words of an nb_tracker (e.g. an int32 tensor or
+    array of 3) as error_word, max_disp_search, max_disp_prune (nm)."""
+    w = np.asarray(words, dtype=np.int32)[:3].copy()
+    d2 = w[1:3].view(np.float32).astype(np.float64)
+    return {"error_word": int(np.uint32(w[0])), "max_disp_search": float(np.sqrt(d2[0])),
+            "max_disp_prune": float(np.sqrt(d2[1]))}
+
+
 def nb_pairlist_export(pl, which: int = NB_LIST_OUTER, stream=None) -> dict:
     """Copy a list to host numpy arrays: ci, cj, shift, mask (uint64), perm."""
     st = nb_pairlist_stats(pl, stream)
@@ -399,6 +415,14 @@ class Pairlist:
 
     def stats(self, stream=None) -> dict:
         return nb_pairlist_stats(self.handle, stream)
+
+    def tracker_enqueue(self, host_words, stream=None) -> None:
+        """Enqueue the tracker copy into host_words, a page-locked int32
+        tensor of 3 or more elements; decode_tracker reads it once the
+        stream has passed this point."""
+        if host_words.dtype != torch.int32 or host_words.numel() < 3 or host_words.device.type != "cpu":
+            raise ValueError("host_words: a host int32 tensor of at least 3 elements")
+        nb_tracker_enqueue(self.handle, host_words.data_ptr(), stream)
 
     def export(self, which=NB_LIST_OUTER, stream=None) -> dict:
         return nb_pairlist_export(self.handle, which, stream)
