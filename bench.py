@@ -239,8 +239,8 @@ def load_traffic():
         return None
     rec = json.load(open(path))
     h = hashlib.sha256()
-    for f in ("nb_force_vt.cu", "nb_pair.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2405_01420_gb300", "csrc", f), "rb").read())
+    for f in rec.get("source_files", []):  # the kernel's sources, relative to the repository root
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     if rec.get("source_sha256") != h.hexdigest():
         return None
     return rec.get("bytes_per_launch_96k")
