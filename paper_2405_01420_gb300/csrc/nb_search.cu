@@ -54,20 +54,36 @@ constexpr int kSearchBuf = 128;  // kept pairs of one i-cluster staged in shared
 
 // Per-warp shared state of the candidate walk.
 struct WalkShared {
-    int incl[32];   // inclusive prefix of the candidates of the batch's columns
-    int cs[32];     // first candidate cluster of each column
-    int len[32];    // candidate clusters per z image of each column
-    int zpack[32];  // kz + 1 of the column's z images, 2 bits each (up to 3)
-    int sbase[32];  // shift index without the z part: (1 - kx) * 9 + (1 - ky) * 3 + 1
-    float ox[32], oy[32];
+    int incl[32];     // inclusive prefix of the candidates of the batch's columns
+    int cs[3][32];    // first candidate cluster of each z image of each column
+    int len01[32];    // candidates of the column's first two z images (16 bits each)
+    int zpack[32];    // kz + 1 of the column's z images, 2 bits each (up to 3)
+    int sbase[32];    // shift index without the z part: (1 - kx) * 9 + (1 - ky) * 3 + 1
 };
+
+// First cluster c in [a, b) with bbox[2c + hi].z >= z (hi = 1) or > z
+// (hi = 0, strict), for z-sorted clusters of one column: their lower and
+// upper z bounds are both non-decreasing in c (the column's atoms are
+// sorted by z and a cluster holds consecutive ones).
+__device__ __forceinline__ int z_bound(const float4 *bbox, int a, int b, int hi, float z) {
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        const float v = bbox[2 * m + hi].z;
+        if (hi ? v >= z : v > z)
+            b = m;
+        else
+            a = m + 1;
+    }
+    return a;
+}
 
 // Walks the candidate clusters of ci: the grid columns within rl_col of its
 // bounding box (with periodic images), their z images, and in each the
-// clusters cj >= ci. A batch of 32 columns is read in parallel (one per
-// lane); a warp scan lays their candidates end to end, and the lanes then
-// test 32 candidates at a time (the column of a candidate found by binary
-// search over the scan). visit(c, sidx, m, r) is called by every lane that
+// clusters cj >= ci whose z extent comes within rl_col of ci's (two binary
+// searches per column and image; a column spans the whole box in z). A
+// batch of 32 columns is read in parallel (one per lane); a warp scan lays
+// their candidates end to end, and the lanes then test 32 candidates at a
+// time (the column of a candidate found by binary search over the scan). visit(c, sidx, m, r) is called by every lane that
 // keeps its pair (bounding boxes within rl2 and a non-empty mask m of real,
 // non-excluded, non-duplicated atom pairs), with its rank r among the kept
 // ones; the order is fixed, so two walks make the same calls.
@@ -85,27 +101,37 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
     for (int kb = 0; kb < ncols; kb += 32) {
         // this lane's column: its candidate range and z images
         const int k = kb + lane;
-        int cs = 0, len = 0, zpack = 0, nz = 0, sbase = 0;
-        float ox = 0.0f, oy = 0.0f;
+        int cs0 = 0, cs1 = 0, cs2 = 0, len0 = 0, len1 = 0, len2 = 0;
+        int zpack = 0, nz = 0, sbase = 0;
         if (k < ncols) {
             const int jxu = jx0 + k / nyr, jyu = jy0 + k % nyr;
             const int kx = image_of(jxu, S.ncx), ky = image_of(jyu, S.ncy);
             const int jx = jxu - kx * S.ncx, jy = jyu - ky * S.ncy;
-            ox = (float)kx * S.box.x;  // j image at x_b + ox, i.e. S_x = -ox
-            oy = (float)ky * S.box.y;
             const int col = S.col_off + jx * S.ncy + jy;
-            const int c0 = p.col_clus_start[col], c1 = p.col_clus_start[col + 1];
-            cs = max(c0, ci);
-            len = max(c1 - cs, 0);
+            const int c0 = max(p.col_clus_start[col], ci), c1 = p.col_clus_start[col + 1];
             sbase = (1 - kx) * 9 + (1 - ky) * 3 + 1;
-            for (int kz = -1; kz <= 1; ++kz) {
+            for (int kz = -1; kz <= 1 && c0 < c1; ++kz) {
+                // clusters whose z extent, moved by oz, comes within rl_col of ci's
                 const float oz = (float)kz * S.box.z;
-                if (lo.z - p.rl_col > oz + S.box.z || hi.z + p.rl_col < oz) continue;
+                const float zlo = (lo.z - p.rl_col) - oz, zhi = (hi.z + p.rl_col) - oz;
+                const int a = z_bound(p.bbox, c0, c1, 1, zlo);
+                const int b = z_bound(p.bbox, a, c1, 0, zhi);
+                if (b <= a) continue;
+                if (nz == 0) {
+                    cs0 = a;
+                    len0 = b - a;
+                } else if (nz == 1) {
+                    cs1 = a;
+                    len1 = b - a;
+                } else {
+                    cs2 = a;
+                    len2 = b - a;
+                }
                 zpack |= (kz + 1) << (2 * nz);
                 ++nz;
             }
         }
-        const int tot = len * nz;
+        const int tot = len0 + len1 + len2;
         int incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -115,12 +141,12 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         __syncwarp();
         ws.incl[lane] = incl;
-        ws.cs[lane] = cs;
-        ws.len[lane] = len;
+        ws.cs[0][lane] = cs0;
+        ws.cs[1][lane] = cs1;
+        ws.cs[2][lane] = cs2;
+        ws.len01[lane] = len0 | (len1 << 16);  // a column holds at most NB_MAX_COL_ATOMS / 8 clusters
         ws.zpack[lane] = zpack;
         ws.sbase[lane] = sbase;
-        ws.ox[lane] = ox;
-        ws.oy[lane] = oy;
         __syncwarp();
         for (int u0 = 0; u0 < total; u0 += 32) {
             const int u = u0 + lane;
@@ -132,14 +158,18 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
 #pragma unroll
                 for (int step = 16; step >= 1; step >>= 1)
                     if (ws.incl[o + step - 1] <= u) o += step;
-                const int lo_u = ws.len[o];
+                const int lp = ws.len01[o];
+                const int l0 = lp & 0xffff, l01 = l0 + (lp >> 16);
                 const int first = (o == 0 ? 0 : ws.incl[o - 1]);
-                const int w = u - first;                         // index within the column's candidates
-                const int zi = (w >= lo_u) + (w >= 2 * lo_u);    // which z image (at most 3)
+                const int w = u - first;                 // index within the column's candidates
+                const int zi = (w >= l0) + (w >= l01);   // which z image (at most 3)
                 const int kz = ((ws.zpack[o] >> (2 * zi)) & 3) - 1;
-                c = ws.cs[o] + (w - zi * lo_u);
-                sidx = ws.sbase[o] - kz;
-                const float oxo = ws.ox[o], oyo = ws.oy[o], oz = (float)kz * S.box.z;
+                c = ws.cs[zi][o] + (w - (zi == 0 ? 0 : (zi == 1 ? l0 : l01)));
+                const int sb = ws.sbase[o];
+                sidx = sb - kz;
+                // j image at x_b + ox, i.e. S_x = -ox (kx = 1 - sb / 9, ky = 1 - (sb / 3) % 3)
+                const float oxo = (float)(1 - sb / 9) * S.box.x, oyo = (float)(1 - (sb / 3) % 3) * S.box.y;
+                const float oz = (float)kz * S.box.z;
                 const float4 bl = p.bbox[2 * c], bh = p.bbox[2 * c + 1];
                 const float gx = fmaxf(0.0f, fmaxf((bl.x + oxo) - hi.x, lo.x - (bh.x + oxo)));
                 const float gy = fmaxf(0.0f, fmaxf((bl.y + oyo) - hi.y, lo.y - (bh.y + oyo)));
