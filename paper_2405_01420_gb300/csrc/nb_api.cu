@@ -330,17 +330,26 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     NB_CUDA(cudaMemsetAsync(&pl->st->excl_count, 0, sizeof(unsigned), s));
     if (excl_off) NB_CUDA(nb_launch_excl_list(pl, excl_off, excl_idx, s));
     pl->has_excl = excl_off != nullptr;
+    // ordering the clusters by list length waits for the first force or adjoint call on this list: a
+    // prune that comes first orders them by its own (pruned) work instead
     pl->sorted = 0;
-    if (!(pl->flags & NB_FLAG_NO_LIST_SORT)) {
-        NB_CUDA(nb_launch_sort_by_length(pl, pl->ci_len_outer, false, s));
-        pl->sorted = 1;
-    }
+    pl->sort_pending = !(pl->flags & NB_FLAG_NO_LIST_SORT);
     pl->searched = 1;
     pl->has_inner = 0;
     pl->has_vtiles = 0;
     pl->rlist = rlist;
     pl->r_inner = 0.0f;
     return ok();
+}
+
+// Orders the i-clusters of a search's list by length if that is still due.
+static cudaError_t sort_if_pending(nb_pairlist *pl, cudaStream_t s) {
+    if (!pl->sort_pending) return cudaSuccess;
+    pl->sort_pending = 0;
+    if (pl->flags & NB_FLAG_NO_LIST_SORT) return cudaSuccess;
+    const cudaError_t e = nb_launch_sort_by_length(pl, pl->ci_len_outer, false, s);
+    if (e == cudaSuccess) pl->sorted = 1;
+    return e;
 }
 
 extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, void *stream) {
@@ -356,6 +365,7 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
     const bool sort = !(pl->flags & NB_FLAG_NO_LIST_SORT);
     NB_CUDA(nb_launch_prune(pl, r2cut, stale_bound2(pl->rlist, r_inner), s));
     pl->sorted = 0;
+    pl->sort_pending = 0;
     if (sort) {
         NB_CUDA(nb_launch_sort_by_length(pl, pl->len_key, true, s));
         pl->sorted = 1;
@@ -391,6 +401,7 @@ extern "C" int nb_forces_part(nb_pairlist *pl, int part, const float *coords, co
     const int kpart = split ? part : NB_PART_ALL;
     const bool last = part != NB_PART_LOCAL;  // this call ends the evaluation
     if (compute) {
+        NB_CUDA(sort_if_pending(pl, s));
         NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, energies, kpart, s));
         if (pl->ev_start) NB_CUDA(cudaEventRecord(pl->ev_start, s));
         const int fpart = (!split && part == NB_PART_LOCAL) ? NB_PART_ALL : kpart;
@@ -432,6 +443,7 @@ extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q,
         return fail(NB_ERR_STATE, "nb_backward: NB_COUL_EXCL_CORR needs exclusion lists at the search");
     DeviceGuard gd(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(sort_if_pending(pl, s));
     NB_CUDA(nb_launch_gather(pl, coords, q, type, ntype, 0, nullptr, NB_PART_ALL, s));
     NB_CUDA(nb_launch_backward(pl, ntype, ljparams, rc, beta, g, grad_x, grad_q, grad_lj,
                                stale_bound2(pl->rlist, rc), stale_bound2(pl->r_inner, rc), s));

@@ -109,6 +109,8 @@ struct nb_pairlist {
     int *len_cursor;      // [NB_LEN_BINS]
     int *ci_order;        // [nc_max] i-clusters by decreasing list length
     int sorted;           // ci_order matches the list the forces will use
+    int sort_pending;     // the last search's list is sorted by length at its first use (unless a prune
+                          // comes first and sorts its own)
     int *vt_slot;         // [2 cap * 8] gathered tiles: j slot | shift << 27
     unsigned *vt_mask;    // [2 cap] 4 x 8 in-range bits per gathered tile
     int *half_start;      // [2 parts][2 nc_max] first gathered tile of each half i-cluster

@@ -14,10 +14,21 @@
 
 namespace {
 
-__global__ void k_len_hist(const int *__restrict__ ci_len, const nb_dev_state *st, int *__restrict__ hist) {
+// Both kernels aggregate in shared memory first: the lengths of many
+// clusters fall in a few bins, and global atomics on one address serialise.
+constexpr int kSortThreads = 256;
+
+__global__ void __launch_bounds__(kSortThreads) k_len_hist(const int *__restrict__ ci_len, const nb_dev_state *st,
+                                                           int *__restrict__ hist) {
+    __shared__ int s_cnt[NB_LEN_BINS];
     const int nc = st->nc;
+    for (int b = threadIdx.x; b < NB_LEN_BINS; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
     for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < nc; ci += gridDim.x * blockDim.x)
-        atomicAdd(&hist[min(ci_len[ci], NB_LEN_BINS - 1)], 1);
+        atomicAdd(&s_cnt[min(ci_len[ci], NB_LEN_BINS - 1)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < NB_LEN_BINS; b += blockDim.x)
+        if (s_cnt[b] > 0) atomicAdd(&hist[b], s_cnt[b]);
 }
 
 // One CTA of NB_LEN_BINS threads: offsets[len] = number of clusters with a
@@ -39,12 +50,27 @@ __global__ void __launch_bounds__(NB_LEN_BINS) k_len_offsets(const int *__restri
     cursor[len] = 0;
 }
 
-__global__ void k_len_scatter(const int *__restrict__ ci_len, const nb_dev_state *st, const int *__restrict__ offsets,
-                              int *__restrict__ cursor, int *__restrict__ order) {
+// Each pass of a CTA places kSortThreads clusters: ranks within the CTA by
+// shared atomics, then one global atomic per occupied bin reserves the
+// CTA's places in that bin.
+__global__ void __launch_bounds__(kSortThreads) k_len_scatter(const int *__restrict__ ci_len, const nb_dev_state *st,
+                                                              const int *__restrict__ offsets,
+                                                              int *__restrict__ cursor, int *__restrict__ order) {
+    __shared__ int s_cnt[NB_LEN_BINS];
+    __shared__ int s_base[NB_LEN_BINS];
     const int nc = st->nc;
-    for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < nc; ci += gridDim.x * blockDim.x) {
-        const int len = min(ci_len[ci], NB_LEN_BINS - 1);
-        order[offsets[len] + atomicAdd(&cursor[len], 1)] = ci;
+    for (int c0 = blockIdx.x * blockDim.x; c0 < nc; c0 += gridDim.x * blockDim.x) {
+        for (int b = threadIdx.x; b < NB_LEN_BINS; b += blockDim.x) s_cnt[b] = 0;
+        __syncthreads();
+        const int ci = c0 + (int)threadIdx.x;
+        const int len = ci < nc ? min(ci_len[ci], NB_LEN_BINS - 1) : 0;
+        const int rank = ci < nc ? atomicAdd(&s_cnt[len], 1) : 0;
+        __syncthreads();
+        for (int b = threadIdx.x; b < NB_LEN_BINS; b += blockDim.x)
+            if (s_cnt[b] > 0) s_base[b] = atomicAdd(&cursor[b], s_cnt[b]);
+        __syncthreads();
+        if (ci < nc) order[offsets[len] + s_base[len] + rank] = ci;
+        __syncthreads();
     }
 }
 
@@ -55,13 +81,13 @@ cudaError_t nb_clear_len_hist(nb_pairlist *pl, cudaStream_t s) {
 }
 
 cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, bool hist_ready, cudaStream_t s) {
-    const int blocks = max(1, min((pl->nc_max + 255) / 256, pl->num_sms * 4));
+    const int blocks = max(1, min((pl->nc_max + kSortThreads - 1) / kSortThreads, pl->num_sms * 4));
     if (!hist_ready) {
         cudaError_t e = nb_clear_len_hist(pl, s);
         if (e != cudaSuccess) return e;
-        k_len_hist<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_hist);
+        k_len_hist<<<blocks, kSortThreads, 0, s>>>(ci_len, pl->st, pl->len_hist);
     }
     k_len_offsets<<<1, NB_LEN_BINS, 0, s>>>(pl->len_hist, pl->len_offsets, pl->len_cursor);
-    k_len_scatter<<<blocks, 256, 0, s>>>(ci_len, pl->st, pl->len_offsets, pl->len_cursor, pl->ci_order);
+    k_len_scatter<<<blocks, kSortThreads, 0, s>>>(ci_len, pl->st, pl->len_offsets, pl->len_cursor, pl->ci_order);
     return cudaGetLastError();
 }
