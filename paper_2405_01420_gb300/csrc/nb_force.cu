@@ -53,6 +53,8 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
+    nb_pdl_wait();
+    nb_pdl_release();
     const int nslot = p.st->nc * NB_CLUSTER;
     float d2s_max = 0.0f, d2p_max = 0.0f;
     for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nslot; slot += gridDim.x * blockDim.x) {
@@ -161,6 +163,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
     __shared__ float4 s_xj[kWarps][CHUNK * NB_CLUSTER];
     __shared__ int s_tj[kWarps][CHUNK * NB_CLUSTER];
     __shared__ unsigned char s_hj[kWarps][CHUNK];  // home bits of the staged j clusters
+    nb_pdl_wait();
+    nb_pdl_release();
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -333,6 +337,8 @@ __global__ void k_clus_home(int nc_max, const int *__restrict__ perm, int n_home
 
 __global__ void k_scatter(int n, const int *__restrict__ pos, const float4 *__restrict__ fsort,
                           float *__restrict__ forces) {
+    nb_pdl_wait();
+    nb_pdl_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 f = fsort[pos[i]];
@@ -384,8 +390,7 @@ cudaError_t nb_launch_gather(nb_pairlist *pl, const float *coords, const float *
     p.snapshot = snapshot;
     int blocks = (pl->nc_max * NB_CLUSTER + 255) / 256;
     blocks = max(1, min(blocks, pl->num_sms * 8));
-    k_gather<<<blocks, 256, 0, s>>>(p);
-    return cudaGetLastError();
+    return nb_launch_pdl(k_gather, blocks, 256, 0, s, p);
 }
 
 cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, float rc, float beta,
@@ -434,8 +439,7 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     int blocks = pl->num_sms * use;
     blocks = min(blocks, (pl->nc_max + threads / 32 - 1) / (threads / 32));
     blocks = max(blocks, 1);
-    fn<<<blocks, threads, smem, s>>>(p);
-    return cudaGetLastError();
+    return nb_launch_pdl(fn, blocks, threads, smem, s, p);
 }
 
 cudaError_t nb_launch_clus_home(nb_pairlist *pl, cudaStream_t s) {
@@ -446,6 +450,6 @@ cudaError_t nb_launch_clus_home(nb_pairlist *pl, cudaStream_t s) {
 
 cudaError_t nb_launch_scatter(nb_pairlist *pl, float *forces, cudaStream_t s) {
     const int n = pl->n_atoms;
-    k_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, pl->pos, pl->fsort, forces);
-    return cudaGetLastError();
+    return nb_launch_pdl(k_scatter, (n + 255) / 256, 256, 0, s, n, (const int *)pl->pos, (const float4 *)pl->fsort,
+                         forces);
 }

@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     __shared__ float4 s_xi[kWarps][4];
     __shared__ int s_tr[kWarps][4];
     __shared__ float4 s_xp[kWarps][2][2];  // row pair k: (x_a, x_b, y_a, y_b), (z_a, z_b, fq_a, fq_b)
+    nb_pdl_wait();  // launched with nb_launch_pdl: the gather has completed from here on
+    nb_pdl_release();
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
         const float c6 = p.ljparams[2 * k], c12 = p.ljparams[2 * k + 1];
@@ -328,6 +330,5 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     const int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
     int blocks = pl->num_sms * use;
     blocks = min(blocks, (2 * p.nreg * pl->nc_max + threads / 32 - 1) / (threads / 32));
-    fn<<<max(blocks, 1), threads, smem, s>>>(p);
-    return cudaGetLastError();
+    return nb_launch_pdl(fn, max(blocks, 1), threads, smem, s, p);
 }

@@ -165,6 +165,35 @@ __device__ __forceinline__ int nb_shift_z(int s) { return s % 3 - 1; }
 int nb_record_error(int code, const char *msg);
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch. A kernel launched with nb_launch_pdl may be
+// scheduled while the work before it in the stream is still running: its
+// blocks fill SMs that the predecessor's tail leaves idle, so the launch
+// latency between dependent kernels is hidden. Such a kernel starts with
+// nb_pdl_wait() (the predecessor has completed and its writes are visible;
+// nothing is read or written before it) and then nb_pdl_release(), which
+// lets its own successor be scheduled once all of its blocks have started.
+// Both are no-ops for a kernel launched the usual way.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void nb_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void nb_pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t nb_launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                          Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (return cudaError_t of the launch).
 // ---------------------------------------------------------------------------
 cudaError_t nb_launch_set_system(nb_pairlist *pl, const nb_sys &one, cudaStream_t s);

@@ -111,6 +111,8 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
     __shared__ int4 s_ent[kPruneThreads / 32][32];
     __shared__ int s_rslot[kPruneThreads / 32][kSets][kStage];
     __shared__ unsigned s_rmask[kPruneThreads / 32][kSets][kStage];
+    nb_pdl_wait();  // launched with nb_launch_pdl: the prune's gather has completed from here on
+    nb_pdl_release();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // displacement since the search must leave the outer list complete at r_inner
         const unsigned ds = p.st->cur_d2_search;
@@ -294,11 +296,7 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     blocks = min(blocks, (pl->nc_max + kPruneThreads / 32 - 1) / (kPruneThreads / 32));
     p.clus_home = pl->clus_home;
     p.reg_stride = 2 * pl->nc_max;
-    if (!p.vt_slot)
-        k_prune<false, 1><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
-    else if (pl->vt_parts == 2)
-        k_prune<true, 2><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
-    else
-        k_prune<true, 1><<<max(blocks, 1), kPruneThreads, 0, s>>>(p);
-    return cudaGetLastError();
+    if (!p.vt_slot) return nb_launch_pdl(k_prune<false, 1>, max(blocks, 1), kPruneThreads, 0, s, p);
+    if (pl->vt_parts == 2) return nb_launch_pdl(k_prune<true, 2>, max(blocks, 1), kPruneThreads, 0, s, p);
+    return nb_launch_pdl(k_prune<true, 1>, max(blocks, 1), kPruneThreads, 0, s, p);
 }

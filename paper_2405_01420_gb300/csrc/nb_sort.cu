@@ -36,6 +36,8 @@ __global__ void __launch_bounds__(kSortThreads) k_len_hist(const int *__restrict
 __global__ void __launch_bounds__(NB_LEN_BINS) k_len_offsets(const int *__restrict__ hist, int *__restrict__ offsets,
                                                            int *__restrict__ cursor) {
     __shared__ int s[NB_LEN_BINS];
+    nb_pdl_wait();
+    nb_pdl_release();
     const int t = threadIdx.x;
     s[t] = hist[NB_LEN_BINS - 1 - t];  // reversed: longest first
     __syncthreads();
@@ -58,6 +60,8 @@ __global__ void __launch_bounds__(kSortThreads) k_len_scatter(const int *__restr
                                                               int *__restrict__ cursor, int *__restrict__ order) {
     __shared__ int s_cnt[NB_LEN_BINS];
     __shared__ int s_base[NB_LEN_BINS];
+    nb_pdl_wait();
+    nb_pdl_release();
     const int nc = st->nc;
     for (int c0 = blockIdx.x * blockDim.x; c0 < nc; c0 += gridDim.x * blockDim.x) {
         for (int b = threadIdx.x; b < NB_LEN_BINS; b += blockDim.x) s_cnt[b] = 0;
@@ -87,7 +91,9 @@ cudaError_t nb_launch_sort_by_length(nb_pairlist *pl, const int *ci_len, bool hi
         if (e != cudaSuccess) return e;
         k_len_hist<<<blocks, kSortThreads, 0, s>>>(ci_len, pl->st, pl->len_hist);
     }
-    k_len_offsets<<<1, NB_LEN_BINS, 0, s>>>(pl->len_hist, pl->len_offsets, pl->len_cursor);
-    k_len_scatter<<<blocks, kSortThreads, 0, s>>>(ci_len, pl->st, pl->len_offsets, pl->len_cursor, pl->ci_order);
-    return cudaGetLastError();
+    cudaError_t e = nb_launch_pdl(k_len_offsets, 1, NB_LEN_BINS, 0, s, (const int *)pl->len_hist, pl->len_offsets,
+                                  pl->len_cursor);
+    if (e != cudaSuccess) return e;
+    return nb_launch_pdl(k_len_scatter, blocks, kSortThreads, 0, s, ci_len, (const nb_dev_state *)pl->st,
+                         (const int *)pl->len_offsets, pl->len_cursor, pl->ci_order);
 }
