@@ -54,6 +54,8 @@ struct BwdParams {
 __global__ void k_gather_g(int nmax_slots, const int *__restrict__ perm, const float *__restrict__ g,
                            float4 *__restrict__ gsort, float4 *__restrict__ bsort, double *__restrict__ glj_acc,
                            int nlj, const nb_dev_state *st) {
+    nb_pdl_wait();
+    nb_pdl_release();
     const int nslot = min(st->nc * NB_CLUSTER, nmax_slots);
     for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < nslot; slot += gridDim.x * blockDim.x) {
         const int atom = perm[slot];
@@ -82,6 +84,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdParams p) {
     __shared__ float4 s_xj[kBwdWarps][kChunk * NB_CLUSTER];
     __shared__ float4 s_gj[kBwdWarps][kChunk * NB_CLUSTER];
     __shared__ int s_tj[kBwdWarps][kChunk * NB_CLUSTER];
+    nb_pdl_wait();
+    nb_pdl_release();
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x)
         s_lj[k] = make_float4(p.ljparams[2 * k], p.ljparams[2 * k + 1], 0.0f, 0.0f);
@@ -215,6 +219,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdParams p) {
 }
 
 __global__ void k_bwd_final(int ntype, const double *__restrict__ acc, double *__restrict__ out) {
+    nb_pdl_wait();
+    nb_pdl_release();
     const int k = threadIdx.x;
     if (k >= ntype * ntype) return;
     const int a = k / ntype, c = k % ntype;
@@ -225,6 +231,8 @@ __global__ void k_bwd_final(int ntype, const double *__restrict__ acc, double *_
 
 __global__ void k_bwd_scatter(int n, const int *__restrict__ pos, const float4 *__restrict__ bsort,
                               float *__restrict__ grad_x, float *__restrict__ grad_q) {
+    nb_pdl_wait();
+    nb_pdl_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 v = bsort[pos[i]];
@@ -245,7 +253,8 @@ cudaError_t launch_bwd(nb_pairlist *pl, const BwdParams &p, cudaStream_t s) {
         if (per_sm < 1) per_sm = 1;
     }
     int blocks = min(pl->num_sms * per_sm, (pl->nc_max + kBwdWarps - 1) / kBwdWarps);
-    k_backward<NT, COUL><<<max(blocks, 1), kBwdThreads, smem, s>>>(p);
+    const cudaError_t e = nb_launch_pdl(k_backward<NT, COUL>, max(blocks, 1), kBwdThreads, smem, s, p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -264,7 +273,9 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
     const int nslot = pl->nc_max * NB_CLUSTER;
     const int nlj = 2 * ntype * ntype;
     int gb = min((nslot + 255) / 256, pl->num_sms * 8);
-    k_gather_g<<<max(gb, 1), 256, 0, s>>>(nslot, pl->perm, g, pl->gsort, pl->bsort, pl->glj_acc, nlj, pl->st);
+    cudaError_t e = nb_launch_pdl(k_gather_g, max(gb, 1), 256, 0, s, nslot, (const int *)pl->perm, g, pl->gsort,
+                                  pl->bsort, pl->glj_acc, nlj, (const nb_dev_state *)pl->st);
+    if (e != cudaSuccess) return e;
     BwdParams p;
     p.xq = pl->xq;
     p.tsort = pl->tsort;
@@ -285,7 +296,6 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
     p.stale_search2 = stale_search2;
     p.stale_prune2 = stale_prune2;
     p.has_inner = pl->has_inner;
-    cudaError_t e;
     if (pl->has_vtiles && !(pl->flags & NB_FLAG_CLUSTER_TILES))  // gathered tiles after a prune
         e = nb_launch_backward_vt(pl, ntype, ljparams, rc, beta, stale_prune2, s);
     else if (coul == NB_COULK_RF)  // the Ewald shift does not change forces
@@ -297,8 +307,9 @@ cudaError_t nb_launch_backward(nb_pairlist *pl, int ntype, const float *ljparams
         e = nb_launch_excl_corr_adj(pl, rc, beta, s);
         if (e != cudaSuccess) return e;
     }
-    k_bwd_final<<<1, 32, 0, s>>>(ntype, pl->glj_acc, grad_lj);
+    e = nb_launch_pdl(k_bwd_final, 1, 32, 0, s, ntype, (const double *)pl->glj_acc, grad_lj);
+    if (e != cudaSuccess) return e;
     const int n = pl->n_atoms;
-    k_bwd_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, pl->pos, pl->bsort, grad_x, grad_q);
-    return cudaGetLastError();
+    return nb_launch_pdl(k_bwd_scatter, (n + 255) / 256, 256, 0, s, n, (const int *)pl->pos, (const float4 *)pl->bsort,
+                         grad_x, grad_q);
 }

@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
     __shared__ float4 s_xi[kBvtWarps][4];  // (x, y, z, f q)
     __shared__ float4 s_gi[kBvtWarps][4];
     __shared__ int s_tr[kBvtWarps][4];     // LJ table row of each i row
+    nb_pdl_wait();
+    nb_pdl_release();
     const int nt2 = p.ntype * p.ntype;
     for (int k = threadIdx.x; k < nt2; k += blockDim.x)
         s_lj[k] = make_float4(p.ljparams[2 * k], p.ljparams[2 * k + 1], 0.0f, 0.0f);
@@ -213,8 +215,7 @@ cudaError_t launch_bvt(nb_pairlist *pl, const BvtParams &p, cudaStream_t s) {
         if (per_sm < 1) per_sm = 1;
     }
     const int blocks = min(pl->num_sms * per_sm, (2 * p.nreg * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
-    k_backward_vt<NT, COUL><<<max(blocks, 1), kBvtThreads, smem, s>>>(p);
-    return cudaGetLastError();
+    return nb_launch_pdl(k_backward_vt<NT, COUL>, max(blocks, 1), kBvtThreads, smem, s, p);
 }
 
 }  // namespace
