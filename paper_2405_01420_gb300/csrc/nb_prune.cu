@@ -3,17 +3,24 @@
 // post-pruning list sorting, the prune also computes the list-size
 // histogram that the sort needs.
 //
-// One warp per i-cluster (work counter). For each outer entry the 32 lanes
-// test its 64 atom pairs (lane l: pairs (l>>3, l&7) and (l>>3 + 4, l&7),
-// i.e. mask bits l and 32 + l) with the FP32 distance contract; the two
-// ballots are the new mask words. Entries with an empty mask are dropped.
-// The inner list of ci is written to its own buffer at the same offset as
-// its outer list (the kept entries fill a prefix of that range).
-#include "nb_internal.cuh"
+// One warp per i-cluster (work counter). The outer entries are taken 32 at
+// a time, one per lane; the warp first stages the 32 j clusters in shared
+// memory (coalesced cp.async, 8 lanes per cluster), then each lane tests
+// the 64 atom pairs of its entry with the FP32 distance contract, on the
+// packed two-wide FP32 instructions (the 8 rows of ci as 4 row pairs in
+// registers, against each j atom). Each lane-wise operation is the IEEE
+// operation of the scalar contract, so the decisions are those of
+// nb_r2(...) < r2cut. Entries with an empty mask are dropped. The inner
+// list of ci is written to its own buffer at the same offset as its outer
+// list (the kept entries fill a prefix of that range).
+#include "nb_pair_x2.cuh"
+#include "nb_warp.cuh"
 
 namespace {
 
-constexpr int kPruneThreads = 256;
+constexpr int kPruneThreads = 128;
+constexpr int kPruneWarps = kPruneThreads / 32;
+constexpr int kPruneCtasPerSm = 6;  // 80 registers per thread (a few bytes spill; faster than 4 CTAs at 106)
 
 struct PruneParams {
     const float4 *xq;
@@ -69,48 +76,48 @@ __device__ __forceinline__ void flush_tiles(const int *ring_slot, const unsigned
     }
 }
 
-template <bool SHIFT>
-__device__ __forceinline__ bool in_range(const float4 xi, const float4 xj, float Sx, float Sy, float Sz,
-                                         float r2cut) {
-    float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y), dz = __fsub_rn(xi.z, xj.z);
-    if (SHIFT) {
-        dx = __fadd_rn(dx, Sx);
-        dy = __fadd_rn(dy, Sy);
-        dz = __fadd_rn(dz, Sz);
+// The new masks of one entry (the lane's): its 64 atom pairs against r2cut,
+// ANDed with the entry's old masks. rx/ry/rz: rows (2k, 2k + 1) of ci as
+// packed pairs; xj: the j cluster's 8 atoms (shared memory); S: the entry's
+// shift (0 for the center, where adding it is exact).
+__device__ __forceinline__ uint2 test_entry(const int4 e, const float2 (&rx)[4], const float2 (&ry)[4],
+                                            const float2 (&rz)[4], const float4 *xj, const float4 S, float r2cut) {
+    const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z);
+    unsigned lo = 0u, hi = 0u;
+#pragma unroll
+    for (int b = 0; b < NB_CLUSTER; ++b) {
+        const float4 x = xj[b];
+        const float2 nx = nb_f2(-x.x), ny = nb_f2(-x.y), nz = nb_f2(-x.z);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 dx = __fadd2_rn(__fadd2_rn(rx[k], nx), Sx);
+            const float2 dy = __fadd2_rn(__fadd2_rn(ry[k], ny), Sy);
+            const float2 dz = __fadd2_rn(__fadd2_rn(rz[k], nz), Sz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            // row a = 2k (.x) and 2k + 1 (.y): bit a * 8 + b of the low word (rows 0-3) or the high word
+            const unsigned bits = (r2.x < r2cut ? 1u << b : 0u) | (r2.y < r2cut ? 1u << (8 + b) : 0u);
+            if (k < 2)
+                lo |= bits << (16 * k);
+            else
+                hi |= bits << (16 * (k - 2));
+        }
     }
-    return nb_r2(dx, dy, dz) < r2cut;
-}
-
-// Tests the 64 atom pairs of one entry; returns the two new mask words.
-__device__ __forceinline__ uint2 prune_entry(const int4 e, const float4 xi1, const float4 xi2, const float4 xj,
-                                             const unsigned lanebit, const float4 *shift, const PruneParams &p) {
-    bool in1, in2;
-    if (e.y == NB_SHIFT_CENTER) {
-        in1 = in_range<false>(xi1, xj, 0.f, 0.f, 0.f, p.r2cut);
-        in2 = in_range<false>(xi2, xj, 0.f, 0.f, 0.f, p.r2cut);
-    } else {
-        const float4 S = shift[e.y];
-        in1 = in_range<true>(xi1, xj, S.x, S.y, S.z, p.r2cut);
-        in2 = in_range<true>(xi2, xj, S.x, S.y, S.z, p.r2cut);
-    }
-    in1 = in1 && ((unsigned)e.z & lanebit);
-    in2 = in2 && ((unsigned)e.w & lanebit);
-    return make_uint2(__ballot_sync(0xffffffffu, in1), __ballot_sync(0xffffffffu, in2));
+    return make_uint2(lo & (unsigned)e.z, hi & (unsigned)e.w);
 }
 
 // One warp per i-cluster. The outer entries of ci are read 32 at a time
-// (one per lane, coalesced) into shared memory; the warp tests them two per
-// iteration (independent loads for latency hiding); lane t keeps the new
-// masks of entry t, and the kept entries are written back compacted and
-// coalesced.
+// (one per lane, coalesced); lane t tests entry t and keeps its new masks,
+// and the kept entries are written back compacted and coalesced.
 // With a halo (NPART = 2) the tiles of each half are gathered in two sets:
 // pairs of two home atoms (region 0) and the rest (region 1).
 template <bool TILES, int NPART>
-__global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
+__global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneParams p) {
     constexpr int kStage = Ring<NPART>::kStage, kSub = Ring<NPART>::kSub, kSets = 2 * NPART;
-    __shared__ int4 s_ent[kPruneThreads / 32][32];
-    __shared__ int s_rslot[kPruneThreads / 32][kSets][kStage];
-    __shared__ unsigned s_rmask[kPruneThreads / 32][kSets][kStage];
+    // the j clusters of a chunk's entries; one float4 of padding per entry keeps the lanes'
+    // 16-byte reads of one atom index free of bank conflicts
+    __shared__ float4 s_xj[kPruneWarps][32][NB_CLUSTER + 1];
+    __shared__ int s_rslot[kPruneWarps][kSets][kStage];
+    __shared__ unsigned s_rmask[kPruneWarps][kSets][kStage];
     nb_pdl_wait();  // launched with nb_launch_pdl: the prune's gather has completed from here on
     nb_pdl_release();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -123,9 +130,7 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         if (__uint_as_float(ds) > p.stale_search2) atomicOr(&p.st->err, NB_DEV_STALE_SEARCH);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = lane & 7, a1 = lane >> 3, a2 = a1 + 4;
     const unsigned lanebit = 1u << lane;
-    int4 *ent = s_ent[warp];
     const int nc = p.st->nc;
     for (;;) {
         unsigned w = 0;
@@ -137,7 +142,14 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         const int k0 = p.ci_start[ci], n = p.ci_len_outer[ci];
         // tiles of set r (part r >> 1, half r & 1) go to [2 NPART k0 + r n, + n):
         // each entry adds at most 8 atoms to a set
-        const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
+        float2 rx[4], ry[4], rz[4];  // rows (2k, 2k + 1) of ci
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 ra = p.xq[ci * NB_CLUSTER + 2 * k], rb = p.xq[ci * NB_CLUSTER + 2 * k + 1];
+            rx[k] = make_float2(ra.x, rb.x);
+            ry[k] = make_float2(ra.y, rb.y);
+            rz[k] = make_float2(ra.z, rb.z);
+        }
         unsigned rows_lo = 0u, rows_hi = 0u;  // home rows of ci as byte masks (rows 0-3 / 4-7)
         if (NPART == 2) {
             const unsigned hci = p.clus_home[ci];
@@ -153,28 +165,22 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune(PruneParams p) {
         for (int r = 0; r < kSets; ++r) head[r] = fill[r] = ntile[r] = 0;
         for (int base = 0; base < n; base += 32) {
             const int cnt = min(32, n - base);
-            __syncwarp();
-            if (lane < cnt) ent[lane] = p.outer[k0 + base + lane];
+            int4 e = make_int4(0, NB_SHIFT_CENTER, 0, 0);
+            if (lane < cnt) e = p.outer[k0 + base + lane];
+            // stage the chunk's j clusters: 8 lanes copy one cluster (128 contiguous bytes)
+            __syncwarp();  // the previous chunk's reads of s_xj are done
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {  // 4 clusters per pass
+                const int t = 4 * k + (lane >> 3);
+                const int cj = __shfl_sync(0xffffffffu, e.x, t);
+                if (t < cnt) cp_async16(&s_xj[warp][t][lane & 7], p.xq + cj * NB_CLUSTER + (lane & 7));
+            }
+            cp_async_wait_all();
             __syncwarp();
             uint2 mine = make_uint2(0u, 0u);
-            int t = 0;
-            for (; t + 1 < cnt; t += 2) {
-                const int4 e0 = ent[t], e1 = ent[t + 1];
-                const float4 xj0 = p.xq[e0.x * NB_CLUSTER + b];
-                const float4 xj1 = p.xq[e1.x * NB_CLUSTER + b];
-                const uint2 m0 = prune_entry(e0, xi1, xi2, xj0, lanebit, shift, p);
-                const uint2 m1 = prune_entry(e1, xi1, xi2, xj1, lanebit, shift, p);
-                if (lane == t) mine = m0;
-                if (lane == t + 1) mine = m1;
-            }
-            if (t < cnt) {
-                const int4 e0 = ent[t];
-                const uint2 m0 = prune_entry(e0, xi1, xi2, p.xq[e0.x * NB_CLUSTER + b], lanebit, shift, p);
-                if (lane == t) mine = m0;
-            }
+            if (lane < cnt) mine = test_entry(e, rx, ry, rz, s_xj[warp][lane], shift[e.y], p.r2cut);
             const bool keep = lane < cnt && (mine.x | mine.y) != 0u;
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            const int4 e = ent[lane];
             if (keep)
                 p.inner[k0 + out + __popc(bal & (lanebit - 1u))] = make_int4(e.x, e.y, (int)mine.x, (int)mine.y);
             out += __popc(bal);
@@ -292,8 +298,8 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     p.r2cut = r_inner2;
     p.stale_search2 = stale_search2;
     // work_prune and inner_count were reset by the snapshot gather before this launch
-    int blocks = pl->num_sms * 4;
-    blocks = min(blocks, (pl->nc_max + kPruneThreads / 32 - 1) / (kPruneThreads / 32));
+    int blocks = pl->num_sms * kPruneCtasPerSm;
+    blocks = min(blocks, (pl->nc_max + kPruneWarps - 1) / kPruneWarps);
     p.clus_home = pl->clus_home;
     p.reg_stride = 2 * pl->nc_max;
     if (!p.vt_slot) return nb_launch_pdl(k_prune<false, 1>, max(blocks, 1), kPruneThreads, 0, s, p);
