@@ -57,8 +57,7 @@ struct WalkShared {
     int incl[32];     // inclusive prefix of the candidates of the batch's columns
     int cs[3][32];    // first candidate cluster of each z image of each column
     int len01[32];    // candidates of the column's first two z images (16 bits each)
-    int zpack[32];    // kz + 1 of the column's z images, 2 bits each (up to 3)
-    int sbase[32];    // shift index without the z part: (1 - kx) * 9 + (1 - ky) * 3 + 1
+    int zpack[32];    // kz + 1 of the column's z images, 2 bits each (up to 3); kx + 1 at bit 8, ky + 1 at bit 10
 };
 
 // First cluster c in [a, b) with bbox[2c + hi].z >= z (hi = 1) or > z
@@ -90,7 +89,7 @@ __device__ __forceinline__ int z_bound(const float4 *bbox, int a, int b, int hi,
 template <typename Visit>
 __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, const float4 lo, const float4 hi, int ni,
                                                const nb_sys &S, const int *tab_c, const unsigned long long *tab_m,
-                                               int ntab, WalkShared &ws, int lane, Visit visit) {
+                                               int ntab, int tlo, int thi, WalkShared &ws, int lane, Visit visit) {
     int nout = 0;
     const int jx0 = max((int)floorf((lo.x - p.rl_col) * S.inv_sx), -S.ncx);
     const int jx1 = min((int)floorf((hi.x + p.rl_col) * S.inv_sx), 2 * S.ncx - 1);
@@ -98,18 +97,23 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
     const int jy1 = min((int)floorf((hi.y + p.rl_col) * S.inv_sy), 2 * S.ncy - 1);
     const int nyr = jy1 - jy0 + 1;
     const int ncols = (jx1 - jx0 + 1) * nyr;
+    const float inv_nyr = 1.0f / (float)nyr;
     for (int kb = 0; kb < ncols; kb += 32) {
         // this lane's column: its candidate range and z images
         const int k = kb + lane;
         int cs0 = 0, cs1 = 0, cs2 = 0, len0 = 0, len1 = 0, len2 = 0;
-        int zpack = 0, nz = 0, sbase = 0;
+        int zpack = 0, nz = 0;
         if (k < ncols) {
-            const int jxu = jx0 + k / nyr, jyu = jy0 + k % nyr;
+            // k = kxr * nyr + kyr; the float quotient is off by at most one for these small integers
+            int kxr = (int)((float)k * inv_nyr);
+            kxr += (kxr + 1) * nyr <= k;
+            kxr -= kxr * nyr > k;
+            const int jxu = jx0 + kxr, jyu = jy0 + (k - kxr * nyr);
             const int kx = image_of(jxu, S.ncx), ky = image_of(jyu, S.ncy);
             const int jx = jxu - kx * S.ncx, jy = jyu - ky * S.ncy;
             const int col = S.col_off + jx * S.ncy + jy;
             const int c0 = max(p.col_clus_start[col], ci), c1 = p.col_clus_start[col + 1];
-            sbase = (1 - kx) * 9 + (1 - ky) * 3 + 1;
+            zpack = ((kx + 1) << 8) | ((ky + 1) << 10);
             for (int kz = -1; kz <= 1 && c0 < c1; ++kz) {
                 // clusters whose z extent, moved by oz, comes within rl_col of ci's
                 const float oz = (float)kz * S.box.z;
@@ -146,7 +150,6 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
         ws.cs[2][lane] = cs2;
         ws.len01[lane] = len0 | (len1 << 16);  // a column holds at most NB_MAX_COL_ATOMS / 8 clusters
         ws.zpack[lane] = zpack;
-        ws.sbase[lane] = sbase;
         __syncwarp();
         for (int u0 = 0; u0 < total; u0 += 32) {
             const int u = u0 + lane;
@@ -163,12 +166,13 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
                 const int first = (o == 0 ? 0 : ws.incl[o - 1]);
                 const int w = u - first;                 // index within the column's candidates
                 const int zi = (w >= l0) + (w >= l01);   // which z image (at most 3)
-                const int kz = ((ws.zpack[o] >> (2 * zi)) & 3) - 1;
+                const int zp = ws.zpack[o];
+                const int kz = ((zp >> (2 * zi)) & 3) - 1;
                 c = ws.cs[zi][o] + (w - (zi == 0 ? 0 : (zi == 1 ? l0 : l01)));
-                const int sb = ws.sbase[o];
-                sidx = sb - kz;
-                // j image at x_b + ox, i.e. S_x = -ox (kx = 1 - sb / 9, ky = 1 - (sb / 3) % 3)
-                const float oxo = (float)(1 - sb / 9) * S.box.x, oyo = (float)(1 - (sb / 3) % 3) * S.box.y;
+                const int kx = ((zp >> 8) & 3) - 1, ky = ((zp >> 10) & 3) - 1;
+                sidx = (1 - kx) * 9 + (1 - ky) * 3 + 1 - kz;
+                // j image at x_b + ox, i.e. S_x = -ox
+                const float oxo = (float)kx * S.box.x, oyo = (float)ky * S.box.y;
                 const float oz = (float)kz * S.box.z;
                 const float4 bl = p.bbox[2 * c], bh = p.bbox[2 * c + 1];
                 const float gx = fmaxf(0.0f, fmaxf((bl.x + oxo) - hi.x, lo.x - (bh.x + oxo)));
@@ -180,8 +184,9 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
                     const int nj = __float_as_int(bl.w);
                     m = row_mask(ni) * (unsigned long long)((1u << nj) - 1u);
                     if (c == ci) m &= (sidx == NB_SHIFT_CENTER) ? kUpperStrict : ~kDiagonal;
-                    for (int q = 0; q < ntab; ++q)
-                        if (tab_c[q] == c) m &= ~tab_m[q];
+                    if (c >= tlo && c <= thi)
+                        for (int q = 0; q < ntab; ++q)
+                            if (tab_c[q] == c) m &= ~tab_m[q];
                     keep = (m != 0ull);
                 }
             }
@@ -203,7 +208,6 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
     __shared__ int s_nexcl[kSearchWarps];
     __shared__ int s_tab_c[kSearchWarps][kExclTab];
     __shared__ unsigned long long s_tab_m[kSearchWarps][kExclTab];
-    __shared__ int s_ntab[kSearchWarps];
     __shared__ WalkShared s_walk[kSearchWarps];
     __shared__ int4 s_buf[kSearchWarps][kSearchBuf];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -237,36 +241,59 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
             if (lane == 0) atomicOr(&p.st->err, NB_DEV_EXCL_OVERFLOW);
             nex = NB_CI_EXCL_BUF;
         }
-        // fold them by j cluster (a handful of clusters per i-cluster)
-        if (lane == 0) {
-            int ntab = 0;
-            for (int e = 0; e < nex; ++e) {
-                const int2 ex = s_excl[warp][e];
-                const int cj = ex.y >> 3;
-                const unsigned long long bit = 1ull << (ex.x * 8 + (ex.y & 7));
-                int k = 0;
-                while (k < ntab && s_tab_c[warp][k] != cj) ++k;
-                if (k == ntab) {
-                    if (ntab == kExclTab) {
-                        atomicOr(&p.st->err, NB_DEV_EXCL_OVERFLOW);
-                        continue;
-                    }
-                    s_tab_c[warp][k] = cj;
-                    s_tab_m[warp][k] = 0ull;
-                    ++ntab;
+        // fold them by j cluster (a handful of clusters per i-cluster), warp-wide: in each round of
+        // 32 entries the lanes of one j cluster elect their lowest lane, which ORs their bits and
+        // files them (in a new table entry, or in the entry of an earlier round)
+        int ntab = 0;
+        for (int r0 = 0; r0 < nex; r0 += 32) {
+            const int e = r0 + lane;
+            const bool valid = e < nex;
+            const int cj = valid ? (s_excl[warp][e].y >> 3) : -1 - lane;  // idle lanes match nobody
+            const unsigned peers = __match_any_sync(0xffffffffu, cj);
+            const bool lead = valid && __ffs(peers) - 1 == lane;
+            unsigned long long m = 0ull;
+            int k = -1;
+            if (lead) {
+                for (unsigned q = peers; q; q &= q - 1u) {
+                    const int2 ex = s_excl[warp][r0 + __ffs(q) - 1];
+                    m |= 1ull << (ex.x * 8 + (ex.y & 7));
                 }
-                s_tab_m[warp][k] |= bit;
+                for (int t = 0; t < ntab; ++t)
+                    if (s_tab_c[warp][t] == cj) {
+                        k = t;
+                        break;
+                    }
             }
-            s_ntab[warp] = ntab;
+            const bool fresh = lead && k < 0;
+            const unsigned fr = __ballot_sync(0xffffffffu, fresh);
+            if (fresh) k = ntab + __popc(fr & ((1u << lane) - 1u));
+            if (lead) {
+                if (k >= kExclTab) {
+                    atomicOr(&p.st->err, NB_DEV_EXCL_OVERFLOW);
+                } else if (fresh) {
+                    s_tab_c[warp][k] = cj;
+                    s_tab_m[warp][k] = m;
+                } else {
+                    s_tab_m[warp][k] |= m;
+                }
+            }
+            ntab = min(ntab + __popc(fr), kExclTab);
+            __syncwarp();
         }
-        __syncwarp();
-        const int ntab = s_ntab[warp];
+        // the range of the table's clusters: most candidates fall outside it
+        int tlo = 0x7fffffff, thi = -1;
+        for (int t = lane; t < ntab; t += 32) {
+            tlo = min(tlo, s_tab_c[warp][t]);
+            thi = max(thi, s_tab_c[warp][t]);
+        }
+        tlo = __reduce_min_sync(0xffffffffu, tlo);
+        thi = __reduce_max_sync(0xffffffffu, thi);
         const int *tab_c = s_tab_c[warp];
         const unsigned long long *tab_m = s_tab_m[warp];
 
         // first walk: kept pairs into the warp's buffer (while they fit)
         int4 *buf = s_buf[warp];
-        const int nout = walk_candidates(p, ci, lo, hi, ni, S, tab_c, tab_m, ntab, s_walk[warp], lane,
+        const int nout = walk_candidates(p, ci, lo, hi, ni, S, tab_c, tab_m, ntab, tlo, thi, s_walk[warp], lane,
                                          [buf](int c, int sidx, unsigned long long m, int r) {
                                              if (r < kSearchBuf)
                                                  buf[r] = make_int4(c, sidx, (int)(unsigned)(m & 0xffffffffu),
@@ -285,7 +312,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
             for (int k = lane; k < nout; k += 32) p.outer[base + k] = buf[k];
         } else {  // a long list: a second walk writes it directly
             int4 *out = p.outer + base;
-            walk_candidates(p, ci, lo, hi, ni, S, tab_c, tab_m, ntab, s_walk[warp], lane,
+            walk_candidates(p, ci, lo, hi, ni, S, tab_c, tab_m, ntab, tlo, thi, s_walk[warp], lane,
                             [out](int c, int sidx, unsigned long long m, int r) {
                                 out[r] = make_int4(c, sidx, (int)(unsigned)(m & 0xffffffffu), (int)(unsigned)(m >> 32));
                             });
