@@ -40,19 +40,38 @@ struct ExclParams {
     nb_coul cc;
 };
 
+// One thread per atom; the warp reserves the places of its pairs with one
+// atomic per round (all threads of a warp on one counter would serialise).
 __global__ void __launch_bounds__(kExclThreads) k_excl_list(int n, const int *__restrict__ excl_off,
                                                             const int *__restrict__ excl_idx,
                                                             const int *__restrict__ pos, int2 *__restrict__ pairs,
                                                             unsigned cap, nb_dev_state *st) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        for (int k = excl_off[i]; k < excl_off[i + 1]; ++k) {
-            const int j = excl_idx[k];
-            if (j <= i || j >= n) continue;  // each pair once; indices outside [0, n) are flagged by the search
-            const unsigned idx = atomicAdd(&st->excl_count, 1u);
-            if (idx < cap)
-                pairs[idx] = make_int2(pos[i], pos[j]);
-            else
-                atomicOr(&st->err, NB_DEV_EXCL_OVERFLOW);
+    const int lane = threadIdx.x & 31;
+    // every lane of a warp runs the same rounds, so the warp-wide votes below see all of it
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + (int)threadIdx.x;
+        int k = i < n ? excl_off[i] : 0;
+        const int k1 = i < n ? excl_off[i + 1] : 0;
+        for (;;) {
+            // this lane's next pair with j > i (each pair once; indices outside [0, n) are flagged by the search)
+            int j = -1;
+            while (k < k1 && j < 0) {
+                const int c = excl_idx[k++];
+                if (c > i && c < n) j = c;
+            }
+            const bool has = j >= 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, has);
+            if (bal == 0u) break;
+            unsigned base = 0u;
+            if (lane == __ffs(bal) - 1) base = atomicAdd(&st->excl_count, (unsigned)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+            if (has) {
+                const unsigned idx = base + (unsigned)__popc(bal & ((1u << lane) - 1u));
+                if (idx < cap)
+                    pairs[idx] = make_int2(pos[i], pos[j]);
+                else
+                    atomicOr(&st->err, NB_DEV_EXCL_OVERFLOW);
+            }
         }
     }
 }
