@@ -160,8 +160,14 @@ __global__ void __launch_bounds__(256) k_col_sort(
     int ncl = (cnt + NB_CLUSTER - 1) / NB_CLUSTER;
     int s0 = c0 * NB_CLUSTER;
     const float4 pad = make_float4(NB_PAD_COORD, NB_PAD_COORD, NB_PAD_COORD, 0.0f);
-    for (int k = threadIdx.x; k < ncl * NB_CLUSTER; k += blockDim.x) {
-        int slot = s0 + k;
+    const int csys = col_sys[col];
+    // one thread per slot; the 8 slots of a cluster are 8 aligned lanes of a warp, which reduce the
+    // cluster's bounding box over its real atoms with shuffles (every lane of a warp takes part)
+    const int nslots = ncl * NB_CLUSTER;
+    for (int k0 = 0; k0 < nslots; k0 += blockDim.x) {
+        const int k = k0 + (int)threadIdx.x;
+        const int slot = s0 + k;
+        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f), hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.0f);
         if (k < cnt) {
             int atom = (int)(sk[k] & 0xffffffffu);
             float4 w = xw[atom];
@@ -169,32 +175,33 @@ __global__ void __launch_bounds__(256) k_col_sort(
             pos[atom] = slot;
             xref[slot] = w;
             xprune[slot] = w;
-        } else {
+            lo = make_float4(w.x, w.y, w.z, 0.0f);
+            hi = lo;
+        } else if (k < nslots) {
             perm[slot] = -1;
             xref[slot] = pad;
             xprune[slot] = pad;
             xq[slot] = pad;
             tsort[slot] = 0;
         }
-    }
-    // bounding boxes: one thread per cluster, real atoms only
-    const int csys = col_sys[col];
-    for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
-        clus_sys[c0 + c] = csys;
-        int nreal = min(NB_CLUSTER, cnt - c * NB_CLUSTER);
-        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, __int_as_float(nreal));
-        float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, __int_as_float(col));
-        for (int a = 0; a < nreal; ++a) {
-            float4 w = xw[(int)(sk[c * NB_CLUSTER + a] & 0xffffffffu)];
-            lo.x = fminf(lo.x, w.x);
-            lo.y = fminf(lo.y, w.y);
-            lo.z = fminf(lo.z, w.z);
-            hi.x = fmaxf(hi.x, w.x);
-            hi.y = fmaxf(hi.y, w.y);
-            hi.z = fmaxf(hi.z, w.z);
+#pragma unroll
+        for (int o = 1; o < NB_CLUSTER; o <<= 1) {
+            lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+            lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+            lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+            hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+            hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+            hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
         }
-        bbox[2 * (c0 + c)] = lo;
-        bbox[2 * (c0 + c) + 1] = hi;
+        if (k < nslots && (k & (NB_CLUSTER - 1)) == 0) {
+            const int c = k / NB_CLUSTER;
+            const int nreal = min(NB_CLUSTER, cnt - k);
+            lo.w = __int_as_float(nreal);
+            hi.w = __int_as_float(col);
+            bbox[2 * (c0 + c)] = lo;
+            bbox[2 * (c0 + c) + 1] = hi;
+            clus_sys[c0 + c] = csys;
+        }
     }
 }
 

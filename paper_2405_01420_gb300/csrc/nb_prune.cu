@@ -80,12 +80,17 @@ __device__ __forceinline__ void flush_tiles(const int *ring_slot, const unsigned
 // ANDed with the entry's old masks. rx/ry/rz: rows (2k, 2k + 1) of ci as
 // packed pairs; xj: the j cluster's 8 atoms (shared memory); S: the entry's
 // shift (0 for the center, where adding it is exact).
+// r2 < r2cut exactly when fl(r2 - r2cut) is negative: the difference of two
+// distinct finite floats rounds to a nonzero value of its sign (subnormals
+// are kept), and equal values give +0. So one packed subtraction decides two
+// pairs, and a funnel shift moves each sign bit into the row's mask byte; j
+// atoms are taken from 7 down to 0 so that atom b ends at bit b.
 __device__ __forceinline__ uint2 test_entry(const int4 e, const float2 (&rx)[4], const float2 (&ry)[4],
                                             const float2 (&rz)[4], const float4 *xj, const float4 S, float r2cut) {
-    const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z);
-    unsigned lo = 0u, hi = 0u;
+    const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z), nr2cut = nb_f2(-r2cut);
+    unsigned ma[4] = {0u, 0u, 0u, 0u}, mb[4] = {0u, 0u, 0u, 0u};  // rows 2k and 2k + 1
 #pragma unroll
-    for (int b = 0; b < NB_CLUSTER; ++b) {
+    for (int b = NB_CLUSTER - 1; b >= 0; --b) {
         const float4 x = xj[b];
         const float2 nx = nb_f2(-x.x), ny = nb_f2(-x.y), nz = nb_f2(-x.z);
 #pragma unroll
@@ -94,14 +99,14 @@ __device__ __forceinline__ uint2 test_entry(const int4 e, const float2 (&rx)[4],
             const float2 dy = __fadd2_rn(__fadd2_rn(ry[k], ny), Sy);
             const float2 dz = __fadd2_rn(__fadd2_rn(rz[k], nz), Sz);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            // row a = 2k (.x) and 2k + 1 (.y): bit a * 8 + b of the low word (rows 0-3) or the high word
-            const unsigned bits = (r2.x < r2cut ? 1u << b : 0u) | (r2.y < r2cut ? 1u << (8 + b) : 0u);
-            if (k < 2)
-                lo |= bits << (16 * k);
-            else
-                hi |= bits << (16 * (k - 2));
+            const float2 t = __fadd2_rn(r2, nr2cut);
+            ma[k] = __funnelshift_l(__float_as_uint(t.x), ma[k], 1);
+            mb[k] = __funnelshift_l(__float_as_uint(t.y), mb[k], 1);
         }
     }
+    // bit a * 8 + b: rows 0-3 in the low word, rows 4-7 in the high word
+    const unsigned lo = ma[0] | (mb[0] << 8) | (ma[1] << 16) | (mb[1] << 24);
+    const unsigned hi = ma[2] | (mb[2] << 8) | (ma[3] << 16) | (mb[3] << 24);
     return make_uint2(lo & (unsigned)e.z, hi & (unsigned)e.w);
 }
 
