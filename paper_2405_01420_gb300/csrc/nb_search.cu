@@ -98,6 +98,10 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
     const int nyr = jy1 - jy0 + 1;
     const int ncols = (jx1 - jx0 + 1) * nyr;
     const float inv_nyr = 1.0f / (float)nyr;
+    // cell edges; the binning's boundaries differ from these products by rounding only, far
+    // below the 1e-3 nm by which rl_col exceeds the list radius
+    const float csx = S.box.x / (float)S.ncx, csy = S.box.y / (float)S.ncy;
+    const float rl_col2 = p.rl_col * p.rl_col;
     for (int kb = 0; kb < ncols; kb += 32) {
         // this lane's column: its candidate range and z images
         const int k = kb + lane;
@@ -112,7 +116,13 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
             const int kx = image_of(jxu, S.ncx), ky = image_of(jyu, S.ncy);
             const int jx = jxu - kx * S.ncx, jy = jyu - ky * S.ncy;
             const int col = S.col_off + jx * S.ncy + jy;
-            const int c0 = max(p.col_clus_start[col], ci), c1 = p.col_clus_start[col + 1];
+            // the column's cell (this image) in the xy plane; a cell farther than rl_col from ci's box
+            // (a corner of the square of columns) holds no candidate
+            const float cx0 = (float)jxu * csx, cy0 = (float)jyu * csy;
+            const float gx = fmaxf(0.0f, fmaxf(cx0 - hi.x, lo.x - (cx0 + csx)));
+            const float gy = fmaxf(0.0f, fmaxf(cy0 - hi.y, lo.y - (cy0 + csy)));
+            const bool near = gx * gx + gy * gy < rl_col2;
+            const int c0 = max(p.col_clus_start[col], ci), c1 = near ? p.col_clus_start[col + 1] : 0;
             zpack = ((kx + 1) << 8) | ((ky + 1) << 10);
             for (int kz = -1; kz <= 1 && c0 < c1; ++kz) {
                 // clusters whose z extent, moved by oz, comes within rl_col of ci's
@@ -203,7 +213,7 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
 // kept pairs in shared memory, one atomic reserves exactly that many list
 // entries, and the warp copies them out coalesced; a list longer than the
 // stage is written by a second walk (the same decisions) instead.
-__global__ void __launch_bounds__(kSearchWarps * 32) k_search(SearchParams p) {
+__global__ void __launch_bounds__(kSearchWarps * 32, 4) k_search(SearchParams p) {
     __shared__ int2 s_excl[kSearchWarps][NB_CI_EXCL_BUF];
     __shared__ int s_nexcl[kSearchWarps];
     __shared__ int s_tab_c[kSearchWarps][kExclTab];
