@@ -756,6 +756,30 @@ def run_ours(args, rank, world, local):
                "copies": "second stream, double-buffered: overlapped with the evaluations"}
         assert eng.check() == 0
 
+    # the list's side of an evaluation: search and prune calls timed on their own (events, median of 5),
+    # and the pair slots the force kernel computes (32 per gathered tile of the current list)
+    slots = 32 * eng.pl.stats()["gathered_tiles"]
+    x_last = frames_d[args.evals - 1]
+
+    def _call_us(fn):
+        ts = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(1e3 * a.elapsed_time(b))
+        return statistics.median(ts)
+
+    search_us = _call_us(lambda: eng.pl.search(x_last, box.box, RLIST, eo, ei))
+    prune_us = _call_us(lambda: eng.pl.prune(x_last, R_INNER))
+    list_side = {"search_us_per_call": search_us, "prune_us_per_call": prune_us,
+                 "list_us_per_eval": (search_us * searches + prune_us * prunes) / args.evals,
+                 "pair_slots_per_eval": slots, "slot_efficiency": pairs_per_eval / slots if slots else None}
+    assert eng.check() == 0
+
     backward = None if args.no_extras else bench_backward(dev)
     batched = None if args.no_extras else bench_batch(dev)
     halo = None if args.no_extras else bench_halo(dev)
@@ -793,6 +817,7 @@ def run_ours(args, rank, world, local):
         "config": dict(workload_desc(args.evals), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "us_per_eval": 1e3 * ms_step / args.evals,
         "pairs_per_eval": pairs_per_eval,
+        "list": list_side,
         "searches_per_step": searches, "prunes_per_step": prunes,
         "force_shape": {"threads": shape[0], "chunk": shape[1], "blocks_per_sm": shape[2], "tuned_ms": shape_times,
                         "tile_form": tile_form, "tile_form_ms": tile_times},

@@ -108,6 +108,8 @@ typedef struct {
     float max_disp_search;   /* largest atom displacement since the search, as seen by the last call */
     float max_disp_prune;    /* largest atom displacement since the last prune, as seen by the last call */
     unsigned error_word;     /* sticky device error bits (not cleared by this call) */
+    long long gathered_tiles; /* 4 x 8 gathered tiles written by the last prune (32 pair slots each;
+                                 0 if none) */
 } nb_stats;
 
 /* Library version string, e.g. "nb 0.1.0 sm_103a". */

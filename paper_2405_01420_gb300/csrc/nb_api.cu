@@ -486,6 +486,7 @@ extern "C" int nb_pairlist_stats(nb_pairlist *pl, nb_stats *out, void *stream) {
     out->max_disp_search = std::sqrt(ds);
     out->max_disp_prune = std::sqrt(dp);
     out->error_word = st.err;
+    out->gathered_tiles = pl->has_vtiles ? (long long)st.tile_count : 0;
     return ok();
 }
 

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
             if (p.snapshot) {  // a prune follows this gather
                 p.st->work_prune = 0u;
                 p.st->inner_count = 0ull;
+                p.st->tile_count = 0ull;
             }
         }
         if (p.energies && p.part != NB_PART_NONLOCAL)

@@ -31,6 +31,7 @@ struct nb_dev_state {
     unsigned cur_d2_prune;
     unsigned long long npairs;     // in-range pairs counted by the last force call
     unsigned excl_count;           // excluded pairs recorded by the last search
+    unsigned long long tile_count; // gathered tiles written by the last prune
 };
 
 // Per-system parameters (one entry per independent box). A single-system

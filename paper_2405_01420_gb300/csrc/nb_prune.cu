@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
                 key = 0;
 #pragma unroll
                 for (int r = 0; r < kSets; ++r) key += ntile[r];
+                atomicAdd(&p.st->tile_count, (unsigned long long)key);
             }
             p.len_key[ci] = key;
             if (p.len_hist) atomicAdd(&p.len_hist[min(key, NB_LEN_BINS - 1)], 1);

@@ -77,6 +77,7 @@ class nb_stats(ctypes.Structure):
         ("max_disp_search", ctypes.c_float),
         ("max_disp_prune", ctypes.c_float),
         ("error_word", ctypes.c_uint),
+        ("gathered_tiles", ctypes.c_longlong),
     ]
 
 

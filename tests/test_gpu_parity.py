@@ -138,6 +138,8 @@ def test_gathered_tiles_cover_r_inner(nb, nw, seed):
     for p_ in range(8):
         cols += ((tiles["masks"] >> np.uint32(p_)) & np.uint32(0x01010101)) != 0
     assert (cols[~last] == 8).all()
+    # the prune's own count of the tiles it wrote (nb_pairlist_stats)
+    assert pl.stats()["gathered_tiles"] == hid.size
     pl.close()
 
 
