@@ -444,3 +444,82 @@ def test_list_sorting_does_not_change_results(nb):
     assert n1 == n2
     np.testing.assert_allclose(F1, F2, rtol=0, atol=1e-5 * np.abs(F2).max())
     assert rel(E1[0], E2[0]) <= 1e-7 and rel(E1[1], E2[1]) <= 1e-7
+
+
+def tiled_along_z(b, reps):
+    """The cubic box b repeated reps times along z: an orthorhombic L x L x reps L box of whole
+    molecules (each water made whole by the minimum image before it is copied and rewrapped)."""
+    L = b.box.astype(np.float64)
+    x = b.coords.astype(np.float64).reshape(-1, 3, 3)  # [molecule, atom (O, H, H), xyz]
+    d = x[:, 1:, :] - x[:, :1, :]
+    x[:, 1:, :] = x[:, :1, :] + d - L * np.rint(d / L)
+    box = np.array([L[0], L[1], reps * L[2]])
+    y = np.concatenate([x + np.array([0.0, 0.0, k * L[2]]) for k in range(reps)]).reshape(-1, 3)
+    y -= box * np.floor(y / box)
+
+    class Tiled:
+        pass
+
+    t = Tiled()
+    n = b.n_atoms
+    t.coords = y.astype(np.float32)
+    t.box = box.astype(np.float32)
+    t.n_atoms = reps * n
+    t.q = np.tile(b.q, reps)
+    t.type = np.tile(b.type, reps)
+    t.ljparams = b.ljparams
+    t.excl_off = np.concatenate([[0]] + [b.excl_off[1:] + k * b.excl_off[-1] for k in range(reps)]).astype(np.int32)
+    t.excl_idx = np.concatenate([b.excl_idx + k * n for k in range(reps)]).astype(np.int32)
+    return t
+
+
+def test_elongated_orthorhombic_box(nb):
+    """2.48 x 2.48 x 19.9 nm (512 waters tiled 8 times along z): grid columns of about 490 atoms
+    (the column sort's larger sorting network), long z ranges in the search, per-axis minimum
+    images; pair coverage, forces and energies against the oracle."""
+    b = tiled_along_z(synth.water_box(512, 1), 8)
+    rc, rlist, r_in = 0.9, 1.0, 0.95
+    beta = synth.ewald_beta(rc)
+    d = to_dev(b)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
+    pl.search(d["coords"], b.box, rlist, d["excl_off"], d["excl_idx"])
+    st = pl.stats()
+    assert st["n_clusters"] * 8 >= b.n_atoms and b.n_atoms / st["n_columns"] > 256
+    pairs = oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx)
+    for prune in (False, True):
+        if prune:
+            pl.prune(d["coords"], r_in)
+        F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
+        torch.cuda.synchronize()
+        assert pl.status() == 0
+        assert pl.stats()["pairs_last"] == len(pairs)
+        Fo, elj, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                              b.excl_idx)
+        compare_forces(F.cpu().numpy(), Fo)
+        check_energies(E, elj, ec)
+    pl.close()
+
+
+@pytest.mark.parametrize("cluster_tiles", [False, True])
+def test_thirty_two_lj_types(nb, cluster_tiles):
+    """The largest LJ table the API takes (32 types, geometric rule, random charges), on both tile
+    forms after a prune."""
+    b = synth.water_box(1000, 9)
+    p = synth.diff_params(b, seed=9, ntype=32)
+    lj = synth.combine_geometric(p["c6"], p["c12"]).astype(np.float32)
+    q = p["q"].astype(np.float32)
+    rc = 1.0
+    beta = synth.ewald_beta(rc)
+    d = to_dev(b)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True, cluster_tiles=cluster_tiles)
+    pl.search(d["coords"], b.box, 1.1, d["excl_off"], d["excl_idx"])
+    pl.prune(d["coords"], 1.04)
+    F, E = pl.forces(d["coords"], torch.from_numpy(q).cuda(), torch.from_numpy(p["type"]).cuda(),
+                     torch.from_numpy(lj).cuda(), rc, beta)
+    torch.cuda.synchronize()
+    assert pl.status() == 0
+    assert int(p["type"].max()) == 31
+    Fo, elj, ec, _ = oracle.energy_forces(b.coords, q, p["type"], lj, b.box, rc, beta, b.excl_off, b.excl_idx)
+    compare_forces(F.cpu().numpy(), Fo)
+    check_energies(E, elj, ec)
+    pl.close()
