@@ -29,23 +29,34 @@ __global__ void k_set_system(nb_sys *sys, float4 *sys_shift, nb_sys one) {
 __global__ void k_bin(int n, const float *__restrict__ coords, const int *__restrict__ atom_sys,
                       const nb_sys *__restrict__ sys, int *__restrict__ col_count, int *__restrict__ atom_col,
                       int *__restrict__ atom_slot, float4 *__restrict__ xw, nb_dev_state *st) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const nb_sys S = sys[atom_sys[i]];
-    float x = coords[3 * i + 0], y = coords[3 * i + 1], z = coords[3 * i + 2];
-    if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
-        atomicOr(&st->err, NB_DEV_NONFINITE);
-        x = 0.0f;
-        y = 0.0f;
-        z = 0.0f;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int col = -1 - lane;  // lanes past the end match nobody below
+    if (i < n) {
+        const nb_sys S = sys[atom_sys[i]];
+        float x = coords[3 * i + 0], y = coords[3 * i + 1], z = coords[3 * i + 2];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            atomicOr(&st->err, NB_DEV_NONFINITE);
+            x = 0.0f;
+            y = 0.0f;
+            z = 0.0f;
+        }
+        float4 w = make_float4(nb_wrap(x, S.box.x), nb_wrap(y, S.box.y), nb_wrap(z, S.box.z), 0.0f);
+        int cx = min(S.ncx - 1, max(0, (int)floorf(w.x * S.inv_sx)));
+        int cy = min(S.ncy - 1, max(0, (int)floorf(w.y * S.inv_sy)));
+        col = S.col_off + cx * S.ncy + cy;
+        xw[i] = w;
+        atom_col[i] = col;
     }
-    float4 w = make_float4(nb_wrap(x, S.box.x), nb_wrap(y, S.box.y), nb_wrap(z, S.box.z), 0.0f);
-    int cx = min(S.ncx - 1, max(0, (int)floorf(w.x * S.inv_sx)));
-    int cy = min(S.ncy - 1, max(0, (int)floorf(w.y * S.inv_sy)));
-    int col = S.col_off + cx * S.ncy + cy;
-    xw[i] = w;
-    atom_col[i] = col;
-    atom_slot[i] = atomicAdd(&col_count[col], 1);
+    // arrival ranks within the column: one atomic per group of lanes in the same column (neighbouring
+    // atoms often share one, and atomics on one counter serialise); the per-column sort orders the
+    // atoms by (z, index) afterwards, so the ranks' order does not show in the result
+    const unsigned peers = __match_any_sync(0xffffffffu, col);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (i < n && lane == leader) base = atomicAdd(&col_count[col], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (i < n) atom_slot[i] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Single CTA: exclusive scans of col_count (atoms) and ceil(count/8)
