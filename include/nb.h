@@ -363,9 +363,12 @@ int nb_forces_part(nb_pairlist *pl, int part, const float *coords, const float *
  *           otherwise >= 1. Ignored for Ewald.
  *   flags   NB_COUL_SHIFT (Ewald only) | NB_COUL_EXCL_CORR. The correction
  *           covers the excluded pairs of the exclusion lists given to the
- *           last nb_search (the search keeps them as its own slot pairs, up
- *           to 8 per atom; beyond that NB_DEV_EXCL_OVERFLOW). Excluded pairs
- *           carry no LJ. The self terms (i = i) are constants the caller adds.
+ *           last nb_search: a search made while NB_COUL_EXCL_CORR is set
+ *           keeps them as its own slot pairs (up to 8 per atom; beyond that
+ *           NB_DEV_EXCL_OVERFLOW), so set the flag before the search; a
+ *           force or adjoint call with the flag on a list searched without
+ *           it fails with NB_ERR_STATE. Excluded pairs carry no LJ. The self
+ *           terms (i = i) are constants the caller adds.
  * Energies: the corrections are part of E_coul. Errors: NB_ERR_ARG for an
  * unknown kind or flag, eps_rf in (0, 1), or NB_COUL_SHIFT with RF.
  */

@@ -325,11 +325,13 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     const float rl_col = (float)(rle + 1e-3);
     NB_CUDA(nb_launch_search(pl, excl_off, excl_idx, rl2, rl_col, s));
     if (pl->vt_parts == 2) NB_CUDA(nb_launch_clus_home(pl, s));  // home bits of the clusters (a halo)
-    // the excluded pairs, kept as slot pairs for the excluded-pair correction
-    // (the caller's lists are read only during this call)
-    NB_CUDA(cudaMemsetAsync(&pl->st->excl_count, 0, sizeof(unsigned), s));
-    if (excl_off) NB_CUDA(nb_launch_excl_list(pl, excl_off, excl_idx, s));
-    pl->has_excl = excl_off != nullptr;
+    // the excluded pairs, as slot pairs, for the excluded-pair correction (only when it is on: the
+    // caller's lists are read only during this call)
+    pl->has_excl = excl_off != nullptr && (pl->coul_flags & NB_COUL_EXCL_CORR);
+    if (pl->has_excl) {
+        NB_CUDA(cudaMemsetAsync(&pl->st->excl_count, 0, sizeof(unsigned), s));
+        NB_CUDA(nb_launch_excl_list(pl, excl_off, excl_idx, s));
+    }
     // ordering the clusters by list length waits for the first force or adjoint call on this list: a
     // prune that comes first orders them by its own (pruned) work instead
     pl->sorted = 0;
@@ -391,7 +393,7 @@ extern "C" int nb_forces_part(nb_pairlist *pl, int part, const float *coords, co
     if (pl->coul_kind == NB_COUL_EWALD && (!(beta >= 0.0f) || !((double)beta * rc <= 3.2)))
         return fail(NB_ERR_ARG, "nb_forces: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
     if ((pl->coul_flags & NB_COUL_EXCL_CORR) && !pl->has_excl)
-        return fail(NB_ERR_STATE, "nb_forces: NB_COUL_EXCL_CORR needs exclusion lists at the search");
+        return fail(NB_ERR_STATE, "nb_forces: NB_COUL_EXCL_CORR needs a search with exclusion lists made while it was set");
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
     // Without a halo the local part is the whole computation and the
@@ -440,7 +442,7 @@ extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q,
     if (pl->coul_kind == NB_COUL_EWALD && (!(beta >= 0.0f) || !((double)beta * rc <= 3.2)))
         return fail(NB_ERR_ARG, "nb_backward: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
     if ((pl->coul_flags & NB_COUL_EXCL_CORR) && !pl->has_excl)
-        return fail(NB_ERR_STATE, "nb_backward: NB_COUL_EXCL_CORR needs exclusion lists at the search");
+        return fail(NB_ERR_STATE, "nb_backward: NB_COUL_EXCL_CORR needs a search with exclusion lists made while it was set");
     DeviceGuard gd(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(sort_if_pending(pl, s));

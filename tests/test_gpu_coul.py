@@ -155,4 +155,15 @@ def test_coulomb_argument_errors(nb):
     with pytest.raises(nb.NBError) as e:
         pl.forces(d["coords"], d["q"], d["type"], d["lj"], 0.9, synth.ewald_beta(0.9))
     assert e.value.code == nb.NB_ERR_STATE
+    # ... given to a search made while the correction was set: turned on after the search, it is refused
+    pl.set_coulomb(kind="ewald")
+    pl.search(d["coords"], b.box, 0.9, d["excl_off"], d["excl_idx"])
+    pl.set_coulomb(kind="ewald", excl_corr=True)
+    with pytest.raises(nb.NBError) as e:
+        pl.forces(d["coords"], d["q"], d["type"], d["lj"], 0.9, synth.ewald_beta(0.9))
+    assert e.value.code == nb.NB_ERR_STATE
+    with pytest.raises(nb.NBError) as e:
+        pl.backward(d["coords"], d["q"], d["type"], d["lj"], 0.9, synth.ewald_beta(0.9),
+                    torch.zeros((b.n_atoms, 3), device="cuda"))
+    assert e.value.code == nb.NB_ERR_STATE
     pl.close()
