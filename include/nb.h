@@ -417,7 +417,7 @@ int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_s
  * it and give wrong results.
  */
 #define NB_NOALLOC_MAX_ATOMS 4096
-#define NB_NOALLOC_SCRATCH_BYTES 2450944
+#define NB_NOALLOC_SCRATCH_BYTES 2518528
 int nb_forces_noalloc(int n_atoms, const float *coords, const float *box, const float *q, const int *type,
                       int ntype, const float *ljparams, float rc, float beta, const int *excl_off,
                       const int *excl_idx, float *forces, double *energies, unsigned *error_word,

@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(256) k_col_sort(
     const int *__restrict__ col_clus_start, const unsigned long long *__restrict__ keys,
     const float4 *__restrict__ xw, const int *__restrict__ col_sys, int *__restrict__ perm,
     int *__restrict__ pos, float4 *__restrict__ xref, float4 *__restrict__ xprune, float4 *__restrict__ xq,
-    int *__restrict__ tsort, float4 *__restrict__ bbox, int *__restrict__ clus_sys) {
+    int *__restrict__ tsort, float4 *__restrict__ bbox, int *__restrict__ clus_sys, const nb_sys *__restrict__ sys,
+    int *__restrict__ ztab) {
     __shared__ unsigned long long sk[NB_MAX_COL_ATOMS];
     int col = blockIdx.x;
     int cnt = min(col_count[col], NB_MAX_COL_ATOMS);  // overflow already flagged by the scan
@@ -172,6 +173,21 @@ __global__ void __launch_bounds__(256) k_col_sort(
     int s0 = c0 * NB_CLUSTER;
     const float4 pad = make_float4(NB_PAD_COORD, NB_PAD_COORD, NB_PAD_COORD, 0.0f);
     const int csys = col_sys[col];
+    // the column's z index: per bin k, the first cluster whose upper z bound (its last atom's z; the
+    // keys are sorted by z) reaches k Lz / NB_ZBINS
+    if (threadIdx.x <= NB_ZBINS) {
+        const float zb = (float)threadIdx.x * (sys[csys].box.z / (float)NB_ZBINS);
+        int a = 0, b = ncl;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            const float hz = __uint_as_float((unsigned)(sk[min(NB_CLUSTER * m + NB_CLUSTER - 1, cnt - 1)] >> 32));
+            if (hz >= zb)
+                b = m;
+            else
+                a = m + 1;
+        }
+        ztab[col * (NB_ZBINS + 1) + threadIdx.x] = c0 + a;
+    }
     // one thread per slot; the 8 slots of a cluster are 8 aligned lanes of a warp, which reduce the
     // cluster's bounding box over its real atoms with shuffles (every lane of a warp takes part)
     const int nslots = ncl * NB_CLUSTER;
@@ -234,6 +250,6 @@ cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream
     k_col_scatter<<<gb, bs, 0, s>>>(n, pl->xw, pl->atom_col, pl->atom_slot, pl->col_atom_start, pl->keys);
     k_col_sort<<<pl->ncol, 256, 0, s>>>(pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->keys, pl->xw,
                                         pl->col_sys, pl->perm, pl->pos, pl->xref, pl->xprune, pl->xq, pl->tsort,
-                                        pl->bbox, pl->clus_sys);
+                                        pl->bbox, pl->clus_sys, pl->sys, pl->ztab);
     return cudaGetLastError();
 }

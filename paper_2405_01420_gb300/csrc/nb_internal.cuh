@@ -13,6 +13,7 @@
 #define NB_CI_EXCL_BUF 256      // exclusions within one i-cluster
 #define NB_SHIFT_CENTER 13      // shift index of S = (0, 0, 0)
 #define NB_LEN_BINS 512         // list-length histogram bins (lengths >= 511 share the last)
+#define NB_ZBINS 32             // z bins of a grid column's index of its clusters (ztab)
 #define NB_COULOMB_F 138.935458f
 
 // Device-side state of one pair list (one allocation, zeroed at creation).
@@ -90,6 +91,8 @@ struct nb_pairlist {
     int *tsort;           // [8 nc_max] LJ type of the current call
     float4 *fsort;        // [8 nc_max] force accumulators, sorted order
     float4 *bbox;         // [2 nc_max] lo (w = real atom count), hi (w = column)
+    int *ztab;            // [ncol_max (NB_ZBINS + 1)] per column: the first cluster whose upper z bound
+                          // reaches k Lz / NB_ZBINS, k = 0..NB_ZBINS (the column's end for none)
     int4 *outer;          // [cap] (cj, shift, mask lo, mask hi)
     int4 *inner;          // [cap]
     int *ci_start;        // [nc_max] first entry of i-cluster ci (both lists)

@@ -50,7 +50,8 @@ constexpr size_t kOffShift = kOffSys + align256(sizeof(nb_sys));
 constexpr size_t kOffAtomSys = kOffShift + align256(sizeof(float4) * 27);
 constexpr size_t kOffColSys = kOffAtomSys + align256(sizeof(int) * kMaxAtoms);
 constexpr size_t kOffClusSys = kOffColSys + align256(sizeof(int) * kMaxCols);
-constexpr size_t kScratchBytes = kOffClusSys + align256(sizeof(int) * kMaxNc);
+constexpr size_t kOffZtab = kOffClusSys + align256(sizeof(int) * kMaxNc);
+constexpr size_t kScratchBytes = kOffZtab + align256(sizeof(int) * kMaxCols * (NB_ZBINS + 1));
 
 static_assert(kScratchBytes == NB_NOALLOC_SCRATCH_BYTES, "update NB_NOALLOC_SCRATCH_BYTES in nb.h");
 
@@ -136,6 +137,7 @@ extern "C" int nb_forces_noalloc(int n_atoms, const float *coords, const float *
     pl.atom_sys = (int *)(base + kOffAtomSys);
     pl.col_sys = (int *)(base + kOffColSys);
     pl.clus_sys = (int *)(base + kOffClusSys);
+    pl.ztab = (int *)(base + kOffZtab);
     for (int k = 0; k < 3; ++k) pl.box[k] = box[k];
 
     // same grid rule as nb_search

@@ -25,6 +25,7 @@ constexpr unsigned long long kDiagonal = 0x8040201008040201ull;
 struct SearchParams {
     const float4 *bbox;
     const int *col_clus_start;
+    const int *ztab;  // per column: first cluster whose upper z bound reaches k Lz / NB_ZBINS
     const int *perm;
     const int *pos;
     const int *excl_off;
@@ -63,23 +64,26 @@ struct WalkShared {
 // First cluster c in [a, b) with bbox[2c + hi].z >= z (hi = 1) or > z
 // (hi = 0, strict), for z-sorted clusters of one column: their lower and
 // upper z bounds are both non-decreasing in c (the column's atoms are
-// sorted by z and a cluster holds consecutive ones).
-__device__ __forceinline__ int z_bound(const float4 *bbox, int a, int b, int hi, float z) {
-    while (a < b) {
-        const int m = (a + b) >> 1;
-        const float v = bbox[2 * m + hi].z;
-        if (hi ? v >= z : v > z)
-            b = m;
-        else
-            a = m + 1;
+// sorted by z and a cluster holds consecutive ones). zt is the column's z
+// index: every cluster before zt[k] has its upper bound below k dz, so for
+// k dz <= z neither test can hold there; k one bin below z's keeps the
+// start clear of rounding, and a short forward scan finds the answer.
+__device__ __forceinline__ int z_first(const float4 *bbox, const int *zt, int a, int b, int hi, float z,
+                                       float inv_dz) {
+    const int k = min(max((int)floorf(z * inv_dz) - 1, 0), NB_ZBINS);
+    int c = max(a, zt[k]);
+    while (c < b) {
+        const float v = bbox[2 * c + hi].z;
+        if (hi ? v >= z : v > z) break;
+        ++c;
     }
-    return a;
+    return c;
 }
 
 // Walks the candidate clusters of ci: the grid columns within rl_col of its
 // bounding box (with periodic images), their z images, and in each the
-// clusters cj >= ci whose z extent comes within rl_col of ci's (two binary
-// searches per column and image; a column spans the whole box in z). A
+// clusters cj >= ci whose z extent comes within rl_col of ci's (found from
+// the column's z index; a column spans the whole box in z). A
 // batch of 32 columns is read in parallel (one per lane); a warp scan lays
 // their candidates end to end, and the lanes then test 32 candidates at a
 // time (the column of a candidate found by binary search over the scan). visit(c, sidx, m, r) is called by every lane that
@@ -101,6 +105,7 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
     // cell edges; the binning's boundaries differ from these products by rounding only, far
     // below the 1e-3 nm by which rl_col exceeds the list radius
     const float csx = S.box.x / (float)S.ncx, csy = S.box.y / (float)S.ncy;
+    const float inv_dz = (float)NB_ZBINS / S.box.z;
     const float rl_col2 = p.rl_col * p.rl_col;
     for (int kb = 0; kb < ncols; kb += 32) {
         // this lane's column: its candidate range and z images
@@ -123,13 +128,14 @@ __device__ __forceinline__ int walk_candidates(const SearchParams &p, int ci, co
             const float gy = fmaxf(0.0f, fmaxf(cy0 - hi.y, lo.y - (cy0 + csy)));
             const bool near = gx * gx + gy * gy < rl_col2;
             const int c0 = max(p.col_clus_start[col], ci), c1 = near ? p.col_clus_start[col + 1] : 0;
+            const int *zt = p.ztab + col * (NB_ZBINS + 1);
             zpack = ((kx + 1) << 8) | ((ky + 1) << 10);
             for (int kz = -1; kz <= 1 && c0 < c1; ++kz) {
                 // clusters whose z extent, moved by oz, comes within rl_col of ci's
                 const float oz = (float)kz * S.box.z;
                 const float zlo = (lo.z - p.rl_col) - oz, zhi = (hi.z + p.rl_col) - oz;
-                const int a = z_bound(p.bbox, c0, c1, 1, zlo);
-                const int b = z_bound(p.bbox, a, c1, 0, zhi);
+                const int a = z_first(p.bbox, zt, c0, c1, 1, zlo, inv_dz);
+                const int b = z_first(p.bbox, zt, a, c1, 0, zhi, inv_dz);
                 if (b <= a) continue;
                 if (nz == 0) {
                     cs0 = a;
@@ -343,6 +349,7 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
     SearchParams p;
     p.bbox = pl->bbox;
     p.col_clus_start = pl->col_clus_start;
+    p.ztab = pl->ztab;
     p.perm = pl->perm;
     p.pos = pl->pos;
     p.excl_off = excl_off;
