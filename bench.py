@@ -78,6 +78,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the backward and batched legs")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default force launch shape and gathered tiles instead of autotuning them (for profiler "
+                         "runs: under a profiler the tuner's timings, and so its choices, are not the bench's)")
     return ap.parse_args()
 
 
@@ -648,8 +651,11 @@ def run_ours(args, rank, world, local):
     restart()
     eng.compute(frames_d[0], q, typ, lj, forces, energies[0])
     force_call = lambda: nb.nb_forces(eng.pl.handle, frames_d[0], q, typ, lj, RC, beta, forces, energies[0])
-    shape, shape_times = tune_force_shape(eng.pl, force_call)
-    tile_form, tile_times = tune_tile_form(eng.pl, force_call)
+    if args.no_tune:
+        shape, shape_times, tile_form, tile_times = (256, 16, 0), None, "gathered", None
+    else:
+        shape, shape_times = tune_force_shape(eng.pl, force_call)
+        tile_form, tile_times = tune_tile_form(eng.pl, force_call)
 
     for _ in range(args.warmup):
         one_step(lambda i: frames_d[i])
