@@ -77,11 +77,18 @@ def parse_args():
     ap.add_argument("--evals", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the backward and batched legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the backward, batched, halo and million legs")
+    ap.add_argument("--legs", default="backward,batched,halo,million",
+                    help="comma-separated extra legs to run after the 96,000-atom one (default: all four)")
     ap.add_argument("--no-tune", action="store_true",
                     help="default force launch shape and gathered tiles instead of autotuning them (for profiler "
                          "runs: under a profiler the tuner's timings, and so its choices, are not the bench's)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    args.leg_set = set() if args.no_extras else {leg.strip() for leg in args.legs.split(",") if leg.strip()}
+    unknown = args.leg_set - {"backward", "batched", "halo", "million"}
+    if unknown:
+        ap.error(f"unknown legs: {sorted(unknown)}")
+    return args
 
 
 # ----------------------------------------------------------------- clocks
@@ -786,11 +793,12 @@ def run_ours(args, rank, world, local):
                  "pair_slots_per_eval": slots, "slot_efficiency": pairs_per_eval / slots if slots else None}
     assert eng.check() == 0
 
-    backward = None if args.no_extras else bench_backward(dev)
-    batched = None if args.no_extras else bench_batch(dev)
-    halo = None if args.no_extras else bench_halo(dev)
-    million = None if args.no_extras else bench_million(
-        dev, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+    legs = args.leg_set
+    backward = bench_backward(dev) if "backward" in legs else None
+    batched = bench_batch(dev) if "batched" in legs else None
+    halo = bench_halo(dev) if "halo" in legs else None
+    million = bench_million(dev, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline)) \
+        if "million" in legs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

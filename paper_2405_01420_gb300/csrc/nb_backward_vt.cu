@@ -53,16 +53,15 @@ struct BvtStage {
 };
 
 // Issues the copies of the lane's j atom in group g of the half with tiles
-// [t0, t1); returns its slot word (the pad slot with an empty mask past the end).
+// [t0, t1) (t0 < t1); returns its slot word. Past the end: the pad slot and
+// a zero-filled mask, with the loads reading tile t0 so that no lane branches.
 __device__ __forceinline__ int stage_adj(const BvtParams &p, BvtStage &st, int t0, int t1, int g, int lane) {
     const int tile = t0 + 4 * g + (lane >> 3);
-    int v = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-    if (tile < t1) {
-        v = p.vt_slot[8 * (size_t)tile + (lane & 7)];
-        cp_async4(&st.m[lane], p.vt_mask + tile);
-    } else {
-        st.m[lane] = 0u;
-    }
+    const bool live = tile < t1;
+    const int tc = live ? tile : t0;
+    const int w = p.vt_slot[8 * (size_t)tc + (lane & 7)];
+    const int v = live ? w : (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+    cp_async4_zfill(&st.m[lane], p.vt_mask + tc, live ? 4u : 0u);
     const int slot = v & 0x07ffffff;
     cp_async16(&st.xj[lane], p.xq + slot);
     cp_async16(&st.gj[lane], p.gsort + slot);
@@ -146,7 +145,7 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
             int vn = 0;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                if (a == 2 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
+                if (a == 2)  // next group's copies overlap rows 2 and 3 (past the last group: pad copies)
                     vn = stage_adj(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xi = s_xi[warp][a];
                 float d6, d12;

@@ -77,19 +77,18 @@ struct VtStage {
     unsigned m[32];
 };
 
-// Issues the copies of group g of the half with tiles [t0, t1) into st
-// (one j atom per lane); returns the lane's slot word. Lanes past the end
-// take the pad slot (never occupied, q = 0) with an empty mask.
+// Issues the copies of group g of the half with tiles [t0, t1) (t0 < t1)
+// into st (one j atom per lane); returns the lane's slot word. Lanes past
+// the end take the pad slot (never occupied, q = 0) and a zero-filled mask;
+// their loads read tile t0 instead, so that no lane branches.
 __device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, int t0, int t1, int g,
                                            int lane) {
     const int tile = t0 + 4 * g + (lane >> 3);
-    int v = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-    if (tile < t1) {
-        v = p.vt_slot[8 * (size_t)tile + (lane & 7)];
-        cp_async4(&st.m[lane], p.vt_mask + tile);
-    } else {
-        st.m[lane] = 0u;
-    }
+    const bool live = tile < t1;
+    const int tc = live ? tile : t0;
+    const int w = p.vt_slot[8 * (size_t)tc + (lane & 7)];
+    const int v = live ? w : (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+    cp_async4_zfill(&st.m[lane], p.vt_mask + tc, live ? 4u : 0u);
     const int slot = v & 0x07ffffff;
     cp_async16(&st.xj[lane], p.xq + slot);
     cp_async4(&st.tj[lane], p.tsort + slot);
@@ -212,7 +211,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             int vn = 0;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (k == 1 && g + 1 < ngroups)  // next group's copies overlap rows 2 and 3
+                if (k == 1)  // next group's copies overlap rows 2 and 3 (past the last group: pad copies)
                     vn = stage_group(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xa = s_xp[warp][k][0], xb = s_xp[warp][k][1];
                 const int c2 = nb_pair_x2<ENERGY, COUL>(

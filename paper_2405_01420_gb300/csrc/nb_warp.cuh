@@ -15,6 +15,13 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
 }
 
+// cp.async of 4 bytes of which the first n (0 or 4) are read from gmem and
+// the rest are zero-filled; with n = 0 nothing is read.
+__device__ __forceinline__ void cp_async4_zfill(void *smem, const void *gmem, unsigned n) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
+}
+
 // Waits for this thread's outstanding cp.async copies.
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
