@@ -51,7 +51,7 @@ extern "C" {
 #define NB_ERR_CUDA 2      /* a CUDA runtime call or launch failed */
 #define NB_ERR_CAPACITY 3  /* a size exceeds what the pair list was created for */
 #define NB_ERR_NONFINITE 4 /* reserved for host-side checks of non-finite input */
-#define NB_ERR_TIMEOUT 5   /* a bounded device wait gave up */
+#define NB_ERR_TIMEOUT 5   /* reserved: no kernel waits on a flag or another block, so none gives up */
 #define NB_ERR_STATE 6     /* call out of order (e.g. nb_forces before nb_search) */
 #define NB_ERR_NOMEM 7     /* device allocation failed */
 

@@ -339,6 +339,35 @@ def test_unwrapped_and_edge_coordinates(nb):
         pl.close()
 
 
+@pytest.mark.parametrize("prune", [False, True])
+def test_cutoff_just_below_half_the_box(nb, prune):
+    """rc = rlist one float below L/2 (the largest the search accepts): every
+    pair has exactly one image within rc, and cluster pairs may be listed
+    with several shifts; coverage, forces and energies still match."""
+    b = synth.water_box(512, 3)
+    rc = float(np.nextafter(np.float32(b.box.min()) / np.float32(2), np.float32(0)))
+    assert 2.0 * rc < float(b.box.min())
+    beta = synth.ewald_beta(rc)
+    d = to_dev(b)
+    pl = nb.Pairlist(b.n_atoms, count_pairs=True)
+    pl.search(d["coords"], b.box, rc, d["excl_off"], d["excl_idx"])
+    if prune:
+        pl.prune(d["coords"], rc)
+    F, E = pl.forces(d["coords"], d["q"], d["type"], d["lj"], rc, beta)
+    torch.cuda.synchronize()
+    assert pl.status() == 0
+    y = oracle.image_f32(b.coords, b.coords, b.box)
+    ref = oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx)
+    counted = expand_counted_pairs(pl.export(nb.NB_LIST_OUTER), y, b.box, rc)
+    assert len(pair_set(counted)) == len(counted), "an atom pair is listed twice"
+    assert pair_set(counted) == pair_set(ref)
+    assert pl.stats()["pairs_last"] == len(ref)
+    Fo, elj, ec, _ = oracle_ref(b, rc, beta)
+    compare_forces(F.cpu().numpy(), Fo)
+    check_energies(E, elj, ec)
+    pl.close()
+
+
 def test_zero_charges(nb):
     b = synth.water_box(512, 1)
     rc = 0.9
