@@ -71,3 +71,38 @@ def test_tracker_copy_matches_stats(nb):
     assert t["max_disp_prune"] == pytest.approx(st["max_disp_prune"], rel=1e-6)
     assert 0.003 < t["max_disp_search"] < 0.05
     pl.close()
+
+
+def test_every_evaluation_covers_the_pairs_within_rc(nb):
+    """Along a trajectory that forces searches and prunes, every evaluation
+    counts exactly the oracle's FP32 pairs within rc (images relative to the
+    frame of the last search), and its forces and energies match."""
+    from paper_2405_01420_gb300.engine import NonbondedEngine
+    b = synth.water_box(2000, 23)  # 6,000 atoms
+    n_frames = 30
+    frames = synth.random_walk_frames(b, n_frames, 0.002, seed=23)
+    rc, rlist, r_inner = 1.0, 1.1, 1.04
+    beta = synth.ewald_beta(rc)
+    d = to_dev(b)
+    eng = NonbondedEngine(b.n_atoms, b.box, rc, beta, rlist, r_inner, 10, d["excl_off"], d["excl_idx"],
+                          count_pairs=True)
+    fd = torch.from_numpy(frames).cuda()
+    F = torch.empty((b.n_atoms, 3), dtype=torch.float32, device="cuda")
+    E = torch.zeros(2, dtype=torch.float64, device="cuda")
+    searched_at = []
+    for i in range(n_frames):
+        eng.compute(fd[i], d["q"], d["type"], d["lj"], F, E)
+        s = i + 1 - eng.evals_since_search  # frame of the search the list was built on
+        if not searched_at or searched_at[-1] != s:
+            searched_at.append(s)
+        st = eng.pl.stats()
+        assert st["error_word"] == 0, (i, st["error_word"])
+        ref = oracle.pairs_f32(frames[s], frames[i], b.box, rc, b.excl_off, b.excl_idx, count_only=True)
+        assert st["pairs_last"] == ref, (i, st["pairs_last"], ref)
+        Fo, elj, ec, _ = oracle.energy_forces(frames[i], b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                              b.excl_idx)
+        compare_forces(F.cpu().numpy(), Fo)
+        e = E.cpu().numpy()
+        assert rel(e[0], elj) <= E_TOL and rel(e[1], ec) <= E_TOL, i
+    assert len(searched_at) >= 2 and eng.n_prune > eng.n_search, (searched_at, eng.n_prune)
+    eng.close()

@@ -57,6 +57,49 @@ def test_small_box_search_and_forces(nb):
     pl.close()
 
 
+@pytest.mark.parametrize("nw, seed", [(4000, 7), (1111, 8)])
+def test_grid_sort_is_a_bijection_into_compact_clusters(nb, nw, seed):
+    """The grid sort: every atom has exactly one cluster slot, padding slots
+    close a cluster, the atoms of a cluster share one xy grid column, and a
+    column's clusters hold its atoms in z order."""
+    b = synth.water_box(nw, seed)
+    n = b.n_atoms
+    d = to_dev(b)
+    pl = nb.Pairlist(n)
+    pl.search(d["coords"], b.box, 1.0, d["excl_off"], d["excl_idx"])
+    assert pl.status() == 0
+    perm = pl.export(nb.NB_LIST_OUTER)["perm"].reshape(-1, 8)
+    st = pl.stats()
+    pl.close()
+    assert perm.shape[0] == st["n_clusters"]
+    real = perm >= 0
+    assert np.array_equal(np.sort(perm[real]), np.arange(n)), "not a permutation of the atoms"
+    # padding only after the real atoms of a cluster, and no cluster without atoms
+    assert (np.diff(real.astype(np.int8), axis=1) <= 0).all()
+    assert real[:, 0].all()
+    # one xy column per cluster (a cubic box: ncx = ncy)
+    ncx = int(round(np.sqrt(st["n_columns"])))
+    assert ncx * ncx == st["n_columns"]
+    w = b.box[:2].astype(np.float64) / ncx
+    y = oracle.image_f32(b.coords, b.coords, b.box).astype(np.float64)
+    cols = []
+    for c in range(perm.shape[0]):
+        a = perm[c][real[c]]
+        xy = y[a, :2]
+        assert (xy.max(axis=0) - xy.min(axis=0) <= w + 1e-5).all(), f"cluster {c} spans columns"
+        z = y[a, 2]
+        assert (np.diff(z) >= -1e-6).all(), f"cluster {c} not z-sorted"
+        cols.append(tuple(np.floor(xy.mean(axis=0) / w).astype(int)))
+    # clusters of one column, in slot order, cover disjoint rising z ranges
+    last_top = {}
+    for c, col in enumerate(cols):
+        a = perm[c][real[c]]
+        z = y[a, 2]
+        if col in last_top:
+            assert z.min() >= last_top[col] - 1e-6, f"column {col}: cluster {c} out of z order"
+        last_top[col] = z.max()
+
+
 def test_list_covers_rlist(nb):
     """Every pair within rlist (FP32 contract) has its mask bit in the outer list."""
     b = synth.water_box(4000, 7)
