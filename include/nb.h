@@ -162,9 +162,12 @@ int nb_pairlist_destroy(nb_pairlist *pl);
  *   excl_off device int[n_atoms+1], excl_idx device int[excl_off[n]]:
  *            symmetric exclusion lists in original atom indices (both
  *            directions listed; self need not be). Both NULL = none.
- * The list keeps each cluster pair (ci <= cj) once, with a periodic shift
- * and a 64-bit mask of atom pairs that are real, not excluded and not
- * duplicated. Mask bit a*8+b is atom a of ci with atom b of cj.
+ * The list keeps each cluster pair (ci <= cj) under each periodic shift
+ * that brings it within rlist at most once, with a 64-bit mask of atom
+ * pairs that are real, not excluded and not duplicated. Mask bit a*8+b is
+ * atom a of ci with atom b of cj. A cluster pair can appear under two
+ * shifts when rlist is close to half a box edge; an atom pair still has at
+ * most one image within rlist (every edge exceeds 2*rlist).
  * After the search the forces use the outer list until nb_prune runs.
  * Device errors: NB_DEV_LIST_OVERFLOW, NB_DEV_COLUMN_OVERFLOW,
  * NB_DEV_NONFINITE, NB_DEV_EXCL_OVERFLOW.
