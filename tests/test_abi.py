@@ -59,3 +59,35 @@ def test_kernels_built_for_sm_103a_only():
     flags = " ".join(build.NVCC_FLAGS)
     assert "arch=compute_103a,code=sm_103a" in flags
     assert flags.count("-gencode") == 1
+
+
+def header_defines():
+    text = open(os.path.join(ROOT, "include", "nb.h")).read()
+    return {m.group(1): int(m.group(2), 0)
+            for m in re.finditer(r"^#define (NB_\w+) (0x[0-9a-fA-F]+|\d+)u?\b", text, flags=re.M)}
+
+
+def header_struct_fields(name):
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "nb.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", text).group(1)
+    return [m.group(2) for m in re.finditer(r"^\s*(int|unsigned|float|long long|size_t)\s+(\w+);", body, flags=re.M)]
+
+
+def test_binding_constants_match_the_header():
+    from paper_2405_01420_gb300 import nb
+    defs = header_defines()
+    shared = [k for k in defs if hasattr(nb, k)]
+    assert len(shared) >= 25, shared
+    wrong = {k: (defs[k], getattr(nb, k)) for k in shared if defs[k] != getattr(nb, k)}
+    assert not wrong, wrong
+
+
+def test_binding_structs_match_the_header():
+    from paper_2405_01420_gb300 import nb
+    assert [f for f, _ in nb.nb_stats._fields_] == header_struct_fields("nb_stats")
+    assert [f for f, _ in nb.nb_config._fields_] == header_struct_fields("nb_config")
+    assert header_struct_fields("nb_tracker") == ["error_word", "max_disp2_search", "max_disp2_prune"]
+    # the tracker copy is three 4-byte words, decoded in this order
+    words = __import__("numpy").array([5, 0x3F800000, 0x40000000], dtype="int32")
+    t = nb.decode_tracker(words)
+    assert t["error_word"] == 5 and t["max_disp_search"] == 1.0 and abs(t["max_disp_prune"] - 2 ** 0.5) < 1e-6
