@@ -77,10 +77,16 @@ def test_clock_record_without_samples(tmp_path):
 
 
 def test_traffic_record_only_while_the_sources_match(tmp_path, monkeypatch):
+    import hashlib
     rec = json.load(open(os.path.join(ROOT, "profiles", "force_kernel_traffic.json")))
-    for f in rec["source_files"] + ["profiles/force_kernel_traffic.json"]:
+    h = hashlib.sha256()
+    for f in rec["source_files"]:
         (tmp_path / os.path.dirname(f)).mkdir(parents=True, exist_ok=True)
         shutil.copy(os.path.join(ROOT, f), tmp_path / f)
+        h.update(open(tmp_path / f, "rb").read())
+    rec["source_sha256"] = h.hexdigest()  # a record taken on exactly these sources
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+    json.dump(rec, open(tmp_path / "profiles" / "force_kernel_traffic.json", "w"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.load_traffic() == rec["bytes_per_launch_96k"]
     with open(tmp_path / rec["source_files"][0], "a") as fh:
