@@ -380,22 +380,25 @@ extern "C" int nb_prune(nb_pairlist *pl, const float *coords, float r_inner, voi
     return ok();
 }
 
-extern "C" int nb_forces_part(nb_pairlist *pl, int part, const float *coords, const float *q, const int *type,
-                              int ntype, const float *ljparams, float rc, float beta, float *forces, double *energies,
-                              void *stream) {
+// nb_forces and nb_forces_part; `who` names the entry point in error messages.
+static int forces_impl(const char *who, nb_pairlist *pl, int part, const float *coords, const float *q,
+                       const int *type, int ntype, const float *ljparams, float rc, float beta, float *forces,
+                       double *energies, void *stream) {
     if (part != NB_PART_ALL && part != NB_PART_LOCAL && part != NB_PART_NONLOCAL)
-        return fail(NB_ERR_ARG, "nb_forces: part = %d", part);
+        return fail(NB_ERR_ARG, "%s: part = %d", who, part);
     if (!pl || !coords || !q || !type || !ljparams || (!forces && part != NB_PART_LOCAL))
-        return fail(NB_ERR_ARG, "nb_forces: NULL argument");
-    if (!pl->searched) return fail(NB_ERR_STATE, "nb_forces: no search yet");
-    if (ntype < 1 || ntype > NB_MAX_TYPES) return fail(NB_ERR_ARG, "nb_forces: ntype = %d not in [1, %d]", ntype, NB_MAX_TYPES);
+        return fail(NB_ERR_ARG, "%s: NULL argument", who);
+    if (!pl->searched) return fail(NB_ERR_STATE, "%s: no search yet", who);
+    if (ntype < 1 || ntype > NB_MAX_TYPES)
+        return fail(NB_ERR_ARG, "%s: ntype = %d not in [1, %d]", who, ntype, NB_MAX_TYPES);
     const float rmax = pl->has_inner ? pl->r_inner : pl->rlist;
     if (!(rc > 0.0f) || !(rc <= rmax))
-        return fail(NB_ERR_ARG, "nb_forces: rc = %g must be in (0, %g] (list radius)", rc, rmax);
+        return fail(NB_ERR_ARG, "%s: rc = %g must be in (0, %g] (list radius)", who, rc, rmax);
     if (pl->coul_kind == NB_COUL_EWALD && (!(beta >= 0.0f) || !((double)beta * rc <= 3.2)))
-        return fail(NB_ERR_ARG, "nb_forces: beta*rc = %g must be in [0, 3.2]", (double)beta * rc);
+        return fail(NB_ERR_ARG, "%s: beta*rc = %g must be in [0, 3.2]", who, (double)beta * rc);
     if ((pl->coul_flags & NB_COUL_EXCL_CORR) && !pl->has_excl)
-        return fail(NB_ERR_STATE, "nb_forces: NB_COUL_EXCL_CORR needs a search with exclusion lists made while it was set");
+        return fail(NB_ERR_STATE, "%s: NB_COUL_EXCL_CORR needs a search with exclusion lists made while it was set",
+                    who);
     DeviceGuard g(pl->device);
     cudaStream_t s = (cudaStream_t)stream;
     // Without a halo the local part is the whole computation and the
@@ -424,10 +427,18 @@ extern "C" int nb_forces_part(nb_pairlist *pl, int part, const float *coords, co
     return ok();
 }
 
+extern "C" int nb_forces_part(nb_pairlist *pl, int part, const float *coords, const float *q, const int *type,
+                              int ntype, const float *ljparams, float rc, float beta, float *forces, double *energies,
+                              void *stream) {
+    return forces_impl("nb_forces_part", pl, part, coords, q, type, ntype, ljparams, rc, beta, forces, energies,
+                       stream);
+}
+
 extern "C" int nb_forces(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,
                          const float *ljparams, float rc, float beta, float *forces, double *energies,
                          void *stream) {
-    return nb_forces_part(pl, NB_PART_ALL, coords, q, type, ntype, ljparams, rc, beta, forces, energies, stream);
+    return forces_impl("nb_forces", pl, NB_PART_ALL, coords, q, type, ntype, ljparams, rc, beta, forces, energies,
+                       stream);
 }
 
 extern "C" int nb_backward(nb_pairlist *pl, const float *coords, const float *q, const int *type, int ntype,

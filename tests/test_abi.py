@@ -91,3 +91,49 @@ def test_binding_structs_match_the_header():
     words = __import__("numpy").array([5, 0x3F800000, 0x40000000], dtype="int32")
     t = nb.decode_tracker(words)
     assert t["error_word"] == 5 and t["max_disp_search"] == 1.0 and abs(t["max_disp_prune"] - 2 ** 0.5) < 1e-6
+
+
+# Host-side argument checks of every entry point that takes a pair list: a NULL list (or NULL
+# arguments) returns NB_ERR_ARG with a message naming the function, before any CUDA call.
+NULL_CALLS = [
+    ("nb_search", [None, None, None, 1.0, None, None, None]),
+    ("nb_prune", [None, None, 1.0, None]),
+    ("nb_forces", [None, None, None, None, 1, None, 1.0, 1.0, None, None, None]),
+    ("nb_forces_part", [None, 0, None, None, None, 1, None, 1.0, 1.0, None, None, None]),
+    ("nb_backward", [None, None, None, None, 1, None, 1.0, 1.0, None, None, None, None, None]),
+    ("nb_status", [None, None, 0, None]),
+    ("nb_pairlist_stats", [None, None, None]),
+    ("nb_tracker_enqueue", [None, None, None]),
+    ("nb_pairlist_export", [None, 0, None, None, None, None, 0, None, None, 0, None, None]),
+    ("nb_pairlist_export_tiles", [None, None, None, None, 0, None, None]),
+    ("nb_set_timing_events", [None, None, None]),
+    ("nb_set_force_shape", [None, 0, 0, 0]),
+    ("nb_set_coulomb", [None, 0, 0.0, 0]),
+    ("nb_set_flags", [None, 0]),
+    ("nb_set_home", [None, 1]),
+]
+
+
+@pytest.mark.parametrize("name, args", NULL_CALLS, ids=[c[0] for c in NULL_CALLS])
+def test_null_pair_list_is_an_argument_error(lib, name, args):
+    from paper_2405_01420_gb300 import nb
+    restype, argtypes = nb.SIGNATURES[name]
+    fn = getattr(lib, name)
+    fn.restype, fn.argtypes = restype, argtypes
+    lib.nb_last_error.restype = ctypes.c_char_p
+    assert fn(*args) == nb.NB_ERR_ARG
+    assert lib.nb_last_error().decode().startswith(name)
+
+
+def test_destroy_of_null_is_a_no_op(lib):
+    lib.nb_pairlist_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.nb_pairlist_destroy(None) == 0
+
+
+def test_batch_create_argument_errors(lib):
+    from paper_2405_01420_gb300 import nb
+    restype, argtypes = nb.SIGNATURES["nb_batch_create"]
+    lib.nb_batch_create.restype, lib.nb_batch_create.argtypes = restype, argtypes
+    h = ctypes.c_void_p()
+    assert lib.nb_batch_create(ctypes.byref(h), 0, None, None, None) == nb.NB_ERR_ARG
+    assert h.value is None
