@@ -137,3 +137,32 @@ def test_batch_create_argument_errors(lib):
     h = ctypes.c_void_p()
     assert lib.nb_batch_create(ctypes.byref(h), 0, None, None, None) == nb.NB_ERR_ARG
     assert h.value is None
+
+
+def test_noalloc_argument_checks_run_on_the_host(lib):
+    """nb_forces_noalloc rejects bad sizes, pointers and radii before any CUDA call."""
+    import numpy as np
+    from paper_2405_01420_gb300 import nb
+    restype, argtypes = nb.SIGNATURES["nb_forces_noalloc"]
+    f = lib.nb_forces_noalloc
+    f.restype, f.argtypes = restype, argtypes
+    lib.nb_last_error.restype = ctypes.c_char_p
+    box = np.array([3.0, 3.0, 3.0], np.float32)
+    small_box = np.array([1.5, 3.0, 3.0], np.float32)
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every case fails on the host first
+    word = ctypes.c_uint(0)
+
+    def call(n, b, ntype=1, rc=0.9, beta=3.0, eo=None, ei=None, forces=dummy):
+        return f(n, dummy, b.ctypes.data_as(ctypes.c_void_p), dummy, dummy, ntype, dummy, rc, beta, eo, ei, forces,
+                 None, ctypes.byref(word), None)
+
+    assert call(0, box) == nb.NB_ERR_ARG
+    assert call(nb.NB_NOALLOC_MAX_ATOMS + 1, box) == nb.NB_ERR_CAPACITY
+    assert call(10, box, forces=None) == nb.NB_ERR_ARG
+    assert call(10, box, eo=dummy) == nb.NB_ERR_ARG  # one exclusion array without the other
+    assert call(10, box, ntype=0) == nb.NB_ERR_ARG
+    assert call(10, box, ntype=33) == nb.NB_ERR_ARG
+    assert call(10, box, rc=0.0) == nb.NB_ERR_ARG
+    assert call(10, box, beta=4.0) == nb.NB_ERR_ARG  # beta * rc > 3.2
+    assert call(10, small_box) == nb.NB_ERR_ARG      # an edge not above 2 rc
+    assert lib.nb_last_error().decode().startswith("nb_forces_noalloc")
