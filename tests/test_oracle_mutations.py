@@ -25,6 +25,9 @@ MUTATIONS = {
     "exclusions_ignored": ("if (is_excluded(i, j, excl_off, excl_idx)) continue;\n                    const", "const"),
     "min_image_uses_floor": ("v -= box[k] * rint(v / box[k]);", "v -= box[k] * floor(v / box[k]);"),
     "coulomb_constant_dropped": ("double qq = ORACLE_COULOMB_F * qi * qj;", "double qq = qi * qj;"),
+    # the FP32 contract's image of a displaced position (search frame x0 != current frame x)
+    "fp32_image_uses_floor": ("float k = rintf((x - w0) / L);", "float k = floorf((x - w0) / L);"),
+    "fp32_image_sign_slip": ("return x - k * L;", "return x + k * L;"),
 }
 
 # mistakes in the force adjoint, caught by tests/test_oracle_adjoint.py
@@ -50,14 +53,28 @@ COUL_MUTATIONS = {
     "ewald_shift_sign": ("*phi = A - shift;", "*phi = A + shift;"),
 }
 
+# mistakes in the smooth-PME spread and gather, caught by tests/test_oracle_pme.py
+PME_MUTATIONS = {
+    "bspline_recursion_denominator": ("(n - u) / (n - 1) * oracle_bspline", "(n - u) / n * oracle_bspline"),
+    "bspline_derivative_sign": ("return oracle_bspline(n - 1, u) - oracle_bspline(n - 1, u - 1.0);",
+                                "return oracle_bspline(n - 1, u - 1.0) - oracle_bspline(n - 1, u);"),
+    "pme_scaled_coordinate_off": ("double u = s * K;", "double u = s * (K - 1);"),
+    "spread_grid_index_off_by_one": ("for (int j = 0; j < order; ++j) w[a][j] = oracle_bspline(order, u[a] - (base[a] - j));",
+                                     "for (int j = 0; j < order; ++j) w[a][j] = oracle_bspline(order, u[a] - (base[a] - j) + 1.0);"),
+    "gather_missing_grid_scale": ("* K[a] / box[a];", ";"),
+    "gather_force_sign": ("f[a] -= q[i] * t[a];", "f[a] += q[i] * t[a];"),
+    "gather_wrong_axis_derivative": ("w[0][j0] * dw[1][j1] * w[2][j2] * ph", "w[0][j0] * w[1][j1] * dw[2][j2] * ph"),
+}
+
 PIN_FILES = {**{k: "test_oracle_pins.py" for k in MUTATIONS},
+             **{k: "test_oracle_pme.py" for k in PME_MUTATIONS},
              **{k: "test_oracle_adjoint.py" for k in ADJOINT_MUTATIONS},
              **{k: "test_oracle_coul.py" for k in COUL_MUTATIONS}}
 
 
 @pytest.mark.parametrize("name", sorted(PIN_FILES))
 def test_pins_catch_mutation(name, tmp_path):
-    old, new = {**MUTATIONS, **ADJOINT_MUTATIONS, **COUL_MUTATIONS}[name]
+    old, new = {**MUTATIONS, **ADJOINT_MUTATIONS, **COUL_MUTATIONS, **PME_MUTATIONS}[name]
     pins = PIN_FILES[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"

@@ -303,6 +303,107 @@ def test_pairs_f32_differs_from_f64_only_at_the_cutoff(box512):
     assert len(p32 ^ p64) <= 5
 
 
+def _walk_across_faces(b, n_frames=12, sigma=0.02, seed=11):
+    """A random walk fast enough that a few percent of the atoms cross a box face per frame."""
+    return synth.random_walk_frames(b, n_frames, sigma, seed)
+
+
+def _unwrap_randomly(x, L, seed):
+    """Add a random whole number of box edges (-2..2) to every coordinate of x."""
+    m = np.random.default_rng(seed).integers(-2, 3, size=x.shape)
+    return (x.astype(np.float64) + m * L).astype(np.float32), m
+
+
+def test_image_f32_is_the_image_nearest_the_search_position(box512):
+    """Brute force over whole box shifts: y is the image of x nearest to x0 wrapped into [0, L).
+
+    For each coordinate the periodic images x - k L (k = -6..6) are formed in
+    FP64 and the one nearest to the search frame's position, wrapped into
+    [0, L) in FP64, is taken; the FP32 image must equal it to a few ulp of the
+    largest magnitude involved. Frames of a walk whose atoms cross the faces
+    and the same frames shifted by random whole box edges make x - x0 reach
+    every case: no shift, a face crossing either way, and unwrapped input.
+    """
+    b = box512
+    L32 = b.box.astype(np.float32)
+    L = L32.astype(np.float64)
+    frames = _walk_across_faces(b)
+    x0 = b.coords
+    crossings = 0
+    for t, xt in enumerate(frames[[0, 5, 11]]):
+        for x0_in, x_in in ((x0, xt), (_unwrap_randomly(x0, L, 100 + t)[0], _unwrap_randomly(xt, L, 200 + t)[0])):
+            y = oracle.image_f32(x0_in, x_in, L32).astype(np.float64)
+            w0 = x0_in.astype(np.float64)
+            w0 = w0 - L * np.floor(w0 / L)
+            k = np.arange(-6, 7, dtype=np.float64)
+            cand = x_in.astype(np.float64)[..., None] - k * L[None, :, None]
+            best = np.take_along_axis(cand, np.abs(cand - w0[..., None]).argmin(-1)[..., None], -1)[..., 0]
+            scale = np.maximum(np.abs(x_in.astype(np.float64)), L)
+            assert np.all(np.abs(y - best) <= 4 * np.spacing(scale.astype(np.float32)).astype(np.float64))
+            assert np.all(np.abs(y - w0) <= 0.5 * L + 1e-5)
+        crossings += int((np.abs(xt.astype(np.float64) - x0) > 0.5 * L).sum())
+    assert crossings > 20, "the walk should carry atoms across the faces"
+
+
+def test_pairs_f32_on_a_walk_across_the_faces(box512):
+    """Displaced frames: the FP32 set relative to the search frame is the current frame's FP64 set.
+
+    Pairs are within rc at the current frame whatever image the positions
+    are given in, so the contract's set, taken against the search frame x0,
+    may differ from the FP64 minimum-image set of the current frame only for
+    pairs whose FP64 distance is within 1e-5 nm of rc. That holds for wrapped
+    frames of a walk whose atoms cross the faces, and for the same frames
+    (and search frame) shifted by random whole box edges.
+    """
+    b = box512
+    rc = 0.9
+    L = b.box.astype(np.float64)
+    frames = _walk_across_faces(b)
+    for t in (3, 11):
+        xt = frames[t]
+        p64 = set(map(tuple, oracle.pairs_f64(xt, b.box, rc, b.excl_off, b.excl_idx).tolist()))
+        x64 = xt.astype(np.float64)
+        for x0_in, x_in in ((b.coords, xt), (_unwrap_randomly(b.coords, L, 300 + t)[0],
+                                             _unwrap_randomly(xt, L, 400 + t)[0])):
+            p32 = set(map(tuple, oracle.pairs_f32(x0_in, x_in, b.box, rc, b.excl_off, b.excl_idx).tolist()))
+            assert len(p32) > 100000
+            for (i, j) in p32 ^ p64:
+                d = x64[i] - x64[j]
+                d -= L * np.round(d / L)
+                assert abs(math.sqrt((d * d).sum()) - rc) < 1e-5, (t, i, j)
+            assert len(p32 ^ p64) <= 5
+
+
+def test_pairs_f32_invariant_under_whole_box_shifts(box512):
+    """Exact invariance: adding k L to any input coordinate changes neither the images nor the set.
+
+    Coordinates and the box edge are rounded to multiples of 2^-16 nm, so
+    that every x + k L (|k| <= 2) and every image is exactly representable in
+    FP32; the contract's images of the shifted inputs must then equal those
+    of the original inputs bit for bit, for the search frame and a displaced
+    frame alike, and so must the pair set.
+    """
+    b = box512
+    q = 2.0 ** -16
+    L32 = (np.round(b.box.astype(np.float64) / q) * q).astype(np.float32)
+    L = L32.astype(np.float64)
+
+    def grid(x):
+        return np.clip(np.round(x.astype(np.float64) / q) * q, 0.0, L - q).astype(np.float32)
+
+    x0 = grid(b.coords)
+    xt = grid(_walk_across_faces(b)[7])
+    y = oracle.image_f32(x0, xt, L32)
+    p = oracle.pairs_f32(x0, xt, L32, 0.9, b.excl_off, b.excl_idx)
+    for s in range(3):
+        x0s, m0 = _unwrap_randomly(x0, L, 500 + s)
+        xts, m = _unwrap_randomly(xt, L, 600 + s)
+        assert np.array_equal(x0s.astype(np.float64), x0 + m0 * L)  # the shifts are exact
+        assert np.array_equal(xts.astype(np.float64), xt + m * L)
+        assert np.array_equal(oracle.image_f32(x0s, xts, L32), y)
+        assert np.array_equal(oracle.pairs_f32(x0s, xts, L32, 0.9, b.excl_off, b.excl_idx), p)
+
+
 def test_pair_count_matches_density(box512):
     """Half-pairs per atom within rc ~ rho (2/3) pi rc^3, minus one excluded pair per atom."""
     b = synth.water_box(32000, 2)
