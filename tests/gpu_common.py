@@ -83,6 +83,22 @@ def expand_tile_pairs(tiles, perm, y, box, r_cut):
     return np.stack([i, j], axis=1).astype(np.int64)
 
 
+def assert_same_pairs(got, ref, n_atoms):
+    """Two [P, 2] (i < j) pair arrays hold the same pairs, and ``got`` none twice.
+
+    Compares sorted int64 keys i * n + j, which scales to tens of millions
+    of pairs where Python sets do not.
+    """
+    kg = np.sort(np.asarray(got, np.int64)[:, 0] * n_atoms + np.asarray(got, np.int64)[:, 1])
+    kr = np.sort(np.asarray(ref, np.int64)[:, 0] * n_atoms + np.asarray(ref, np.int64)[:, 1])
+    assert kg.size == 0 or (np.diff(kg) > 0).all(), "an atom pair is listed twice"
+    if not np.array_equal(kg, kr):
+        extra = np.setdiff1d(kg, kr)[:5]
+        missing = np.setdiff1d(kr, kg)[:5]
+        raise AssertionError(f"pair sets differ ({kg.size} vs {kr.size}): extra {[(k // n_atoms, k % n_atoms) for k in extra]}"
+                             f", missing {[(k // n_atoms, k % n_atoms) for k in missing]}")
+
+
 def pair_set(arr):
     return set(map(tuple, np.asarray(arr).tolist()))
 

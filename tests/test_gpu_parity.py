@@ -10,8 +10,8 @@ import torch
 
 import oracle
 import synth
-from gpu_common import (E_TOL, compare_forces, expand_counted_pairs, expand_tile_pairs, oracle_ref, pair_set, rel,
-                        to_dev)
+from gpu_common import (E_TOL, assert_same_pairs, compare_forces, expand_counted_pairs, expand_tile_pairs, oracle_ref,
+                        pair_set, rel, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -204,10 +204,11 @@ def test_cluster_tiles_and_gathered_tiles_agree(nb, want_energy):
         assert pl.status() == 0
         out.append((F.cpu().numpy(), None if E is None else E.cpu().numpy(), pl.stats()["pairs_last"]))
         pl.close()
-    Fo, elj, ec, npairs = oracle_ref(b, rc, beta)
+    Fo, elj, ec, _ = oracle_ref(b, rc, beta)
+    n32 = oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx, count_only=True)
     for F, E, np_ in out:
         compare_forces(F, Fo)
-        assert np_ == npairs
+        assert np_ == n32
         if want_energy:
             assert rel(E[0], elj) <= E_TOL and rel(E[1], ec) <= E_TOL
 
@@ -282,9 +283,16 @@ def test_production_box_96k(nb):
     Fo, elj, ec, n64 = oracle_ref(b, rc, beta)
     compare_forces(F.cpu().numpy(), Fo)
     check_energies(E, elj, ec)
-    n32 = oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx, count_only=True)
-    assert pl.stats()["pairs_last"] == n32
-    assert abs(n32 - n64) <= 5
+    ref = oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx)
+    assert pl.stats()["pairs_last"] == len(ref)
+    assert abs(len(ref) - n64) <= 5
+    # the pair sets themselves, bit for bit: the 8 x 8 inner list and the gathered tiles the
+    # force kernel reads, each expanded under the FP32 contract at rc
+    y = oracle.image_f32(b.coords, b.coords, b.box)
+    inner = pl.export(nb.NB_LIST_INNER)
+    assert_same_pairs(expand_counted_pairs(inner, y, b.box, rc), ref, b.n_atoms)
+    tiles = pl.export_tiles()
+    assert_same_pairs(expand_tile_pairs(tiles, inner["perm"], y, b.box, rc), ref, b.n_atoms)
     pl.close()
 
 
@@ -308,7 +316,9 @@ def test_million_atom_box_sampled(nb):
     Fg = F.cpu().numpy()[atoms].astype(np.float64)
     rms = np.sqrt((Fs ** 2).sum(1).mean())
     assert np.sqrt(((Fg - Fs) ** 2).sum(1)).max() <= 1e-4 * rms
-    assert abs(pl.stats()["pairs_last"] - n64) <= 20
+    n32 = oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx, count_only=True)
+    assert pl.stats()["pairs_last"] == n32
+    assert abs(n32 - n64) <= 20
     pl.close()
 
 
