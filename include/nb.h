@@ -388,6 +388,27 @@ int nb_set_coulomb(nb_pairlist *pl, int kind, float eps_rf, unsigned flags);
 int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_sm);
 
 /*
+ * FP32 throughput probe (measurement only; no counterpart in the paper).
+ * The force kernel is bound by FP32 arithmetic, and this call measures the
+ * rate its roofline divides by: a grid of blocks_per_sm (1..8) blocks of
+ * 256 threads per SM, each thread running 8 independent fused
+ * multiply-add chains for iters x 16 steps, as scalar FFMA (packed = 0) or
+ * as two-wide FFMA2 (packed != 0, two fused multiply-adds per instruction).
+ *
+ *   out      DEVICE float[out_len], caller-owned; each thread writes its
+ *            chains' sum (so nothing is optimised away). out_len must be at
+ *            least SMs x blocks_per_sm x 256, else NB_ERR_ARG.
+ *   flops    HOST double*: receives the launch's FP32 operations, counting
+ *            a fused multiply-add as 2.
+ *
+ * The launch is queued on stream and not waited for: time it with events
+ * recorded around the call. Returns NB_ERR_ARG for bad arguments and
+ * NB_ERR_CUDA if the launch fails.
+ */
+int nb_fp32_peak_probe(int packed, int blocks_per_sm, int iters, float *out, size_t out_len, double *flops,
+                       void *stream);
+
+/*
  * Search and forces without any device allocation (no counterpart in the
  * paper; it exists for callers that cannot allocate device memory).
  *
@@ -410,7 +431,18 @@ int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_s
  *   rc, beta as for nb_forces (beta*rc <= 3.2).
  *   error_word  HOST unsigned* or NULL: if given, the call synchronises the
  *            stream and stores the device error word (NB_DEV_* bits) of
- *            this call; if NULL the call does not synchronise.
+ *            this call; if NULL the call does not synchronise, and the errors
+ *            the kernels find (a list overflow, non-finite coordinates, an LJ
+ *            type out of range, too many exclusions in a cluster) are lost:
+ *            there is no pair list to ask with nb_status, and the next call
+ *            clears the word. Trust the results only when error_word is given
+ *            and comes back 0.
+ *
+ * The pair list has room for NB_NOALLOC_MAX_ATOMS^2 / 64 entries (one per
+ * cluster pair of a full half list, twice over), enough for a water-density
+ * box at the largest cutoff the call accepts (rc just below half the
+ * shortest box edge). A list that still overflows sets NB_DEV_LIST_OVERFLOW
+ * in the error word and its forces are incomplete.
  *
  * The first call on each device looks up the array's device address with
  * cudaGetSymbolAddress (with that device current); make that first call
@@ -420,7 +452,7 @@ int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_s
  * it and give wrong results.
  */
 #define NB_NOALLOC_MAX_ATOMS 4096
-#define NB_NOALLOC_SCRATCH_BYTES 2518528
+#define NB_NOALLOC_SCRATCH_BYTES 5074432
 int nb_forces_noalloc(int n_atoms, const float *coords, const float *box, const float *q, const int *type,
                       int ntype, const float *ljparams, float rc, float beta, const int *excl_off,
                       const int *excl_idx, float *forces, double *energies, unsigned *error_word,

@@ -20,7 +20,11 @@ constexpr int kMaxClus = (kMaxAtoms + NB_CLUSTER - 1) / NB_CLUSTER;  // clusters
 constexpr int kMaxCols = kMaxClus;                                    // grid columns
 constexpr int kMaxNc = kMaxClus + kMaxCols;                           // clusters incl. padding
 constexpr int kMaxSlots = kMaxNc * NB_CLUSTER;
-constexpr size_t kCapEntries = (size_t)kMaxClus * 200;               // list entries
+// List entries: one per cluster pair of a full half list, twice over. In a
+// cubic 4,096-atom water box with rc one float below L/2 (the largest cutoff
+// the call takes) the half list holds about 1.1 entries per cluster pair (a
+// pair can be listed under two shifts), so this leaves room to spare.
+constexpr size_t kCapEntries = (size_t)kMaxClus * kMaxClus;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
