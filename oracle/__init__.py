@@ -16,6 +16,9 @@ Functions:
 * ``image_f32`` - the FP32 positions that contract uses.
 * ``force_vjp`` - adjoint of the forces: dL/dx, dL/dq, dL/dC given dL/dF.
 * ``force_matching`` - loss (1/3N) sum |F - T|^2 and its gradients.
+* ``bspline``, ``pme_spread``, ``pme_gather`` - smooth-PME cardinal
+  B-splines, charge spreading onto the mesh and force gathering from a mesh
+  potential (Essmann et al. 1995).
 
 Parity: pinned by the CPU tests in ``tests/test_oracle_*.py``.
 """
@@ -83,6 +86,14 @@ def _load():
             lib.oracle_force_vjp_coul.restype = I
             lib.oracle_energy_forces_coul_list.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, D, I, P, LL, P, P]
             lib.oracle_energy_forces_coul_list.restype = I
+            lib.oracle_bspline.argtypes = [I, D]
+            lib.oracle_bspline.restype = D
+            lib.oracle_bspline_deriv.argtypes = [I, D]
+            lib.oracle_bspline_deriv.restype = D
+            lib.oracle_pme_spread.argtypes = [I, P, P, P, P, I, P, P]
+            lib.oracle_pme_spread.restype = I
+            lib.oracle_pme_gather.argtypes = [I, P, P, P, P, I, P, P, P, P]
+            lib.oracle_pme_gather.restype = I
             _lib = lib
     return _lib
 
@@ -320,3 +331,42 @@ def energy_forces_coul_pairs(x, q, type_, lj, box, rc, beta, pairs, excl_off=Non
     if rcode != 0:
         raise ValueError(f"oracle_energy_forces_coul_list failed with code {rcode}")
     return F, float(E[0]), float(E[1])
+
+
+def bspline(order: int, u: float, deriv: bool = False) -> float:
+    """Cardinal B-spline M_order(u), or its derivative dM/du."""
+    lib = _load()
+    return float((lib.oracle_bspline_deriv if deriv else lib.oracle_bspline)(int(order), float(u)))
+
+
+def pme_spread(x, q, box, K, order=4, abs_sums=False):
+    """Charge grid Q [K0, K1, K2] of smooth PME; with ``abs_sums`` also the spread of |q|."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    K = np.ascontiguousarray(np.asarray(K, dtype=np.int32))
+    Q = np.empty(tuple(int(k) for k in K), dtype=np.float64)
+    Qa = np.empty_like(Q) if abs_sums else None
+    rcode = lib.oracle_pme_spread(x.shape[0], _p(x), _p(_f64(q)), _p(_f64(box)), _p(K), int(order), _p(Q), _p(Qa))
+    if rcode != 0:
+        raise ValueError(f"oracle_pme_spread failed with code {rcode}")
+    return (Q, Qa) if abs_sums else Q
+
+
+def pme_gather(x, q, box, K, phi, order=4, abs_sums=False):
+    """Forces F [N, 3] = -q grad psi and potentials psi [N] interpolated from the
+    mesh potential ``phi`` [K0, K1, K2]; with ``abs_sums`` also the per-component
+    sums of |terms| [N, 3]."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 3)
+    K = np.ascontiguousarray(np.asarray(K, dtype=np.int32))
+    phi = _f64(phi)
+    assert phi.shape == tuple(int(k) for k in K)
+    n = x.shape[0]
+    F = np.empty((n, 3), dtype=np.float64)
+    psi = np.empty(n, dtype=np.float64)
+    Fa = np.empty((n, 3), dtype=np.float64) if abs_sums else None
+    rcode = lib.oracle_pme_gather(n, _p(x), _p(_f64(q)), _p(_f64(box)), _p(K), int(order), _p(phi), _p(F), _p(psi),
+                                  _p(Fa))
+    if rcode != 0:
+        raise ValueError(f"oracle_pme_gather failed with code {rcode}")
+    return (F, psi, Fa) if abs_sums else (F, psi)

@@ -900,3 +900,120 @@ int oracle_energy_forces_coul_list(int n, const double *x, const double *q, cons
     E[1] = ec;
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Smooth particle-mesh Ewald: charge spreading and force gathering.
+ *
+ * The paper names PME the rate limiter after the short-range kernel
+ * (§III-A, Fig. 2) and gives no formulas. This follows the smooth PME of
+ * Essmann et al. (J. Chem. Phys. 103, 8577, 1995), orthorhombic box:
+ *
+ *   scaled fractional coordinate  u_a = K_a * (x_a / L_a wrapped into [0, 1))
+ *   cardinal B-spline of order n  M_2(u) = 1 - |u - 1| on [0, 2], else 0;
+ *                                  M_n(u) = u/(n-1) M_{n-1}(u)
+ *                                         + (n-u)/(n-1) M_{n-1}(u-1)
+ *                                  dM_n/du = M_{n-1}(u) - M_{n-1}(u-1)
+ *   spread   Q(k) = sum_i q_i sum_{images} prod_a M_n(u_ia - k_a - m_a K_a)
+ *   gather   psi_i = sum_k prod_a M_n(u_ia - k_a) phi(k)   (interpolated potential)
+ *            F_ia  = -q_i dpsi_i/dx_ia
+ *                  = -q_i (K_a/L_a) sum_k M_n'(u_ia - k_a) prod_{b!=a} M_n(u_ib - k_b) phi(k)
+ *
+ * for a grid potential phi (in smooth PME, phi = theta_rec convolved with Q;
+ * that FFT solve is not part of these functions). Grids are K0 x K1 x K2
+ * with the last index fastest. An atom reaches the points k_a = floor(u_a) - j,
+ * j = 0..n-1 (mod K_a): M_n vanishes outside (0, n). Everything in FP64.
+ * ------------------------------------------------------------------------ */
+double oracle_bspline(int n, double u) {
+    if (n <= 2) return (u >= 0.0 && u <= 2.0) ? 1.0 - fabs(u - 1.0) : 0.0;
+    return u / (n - 1) * oracle_bspline(n - 1, u) + (n - u) / (n - 1) * oracle_bspline(n - 1, u - 1.0);
+}
+
+double oracle_bspline_deriv(int n, double u) { return oracle_bspline(n - 1, u) - oracle_bspline(n - 1, u - 1.0); }
+
+/* u in [0, K) for one coordinate */
+static double pme_scaled(double x, double L, int K) {
+    double s = x / L;
+    s -= floor(s);
+    double u = s * K;
+    if (u >= K) u -= K;
+    if (u < 0.0) u = 0.0;
+    return u;
+}
+
+static int pme_mod(int k, int K) { return ((k % K) + K) % K; }
+
+/*
+ * Q[K0*K1*K2] = spread of the charges; Qabs (optional) the same spread of
+ * |q_i| (the scale of the rounding of each grid value). Returns 0, or -1 on
+ * bad arguments.
+ */
+int oracle_pme_spread(int n, const double *x, const double *q, const double *box, const int *K, int order, double *Q,
+                      double *Qabs) {
+    if (order < 2 || order > 16 || K[0] < 1 || K[1] < 1 || K[2] < 1) return -1;
+    size_t ng = (size_t)K[0] * K[1] * K[2];
+    memset(Q, 0, sizeof(double) * ng);
+    if (Qabs) memset(Qabs, 0, sizeof(double) * ng);
+    for (int i = 0; i < n; ++i) {
+        double u[3], w[3][16];
+        int base[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = pme_scaled(x[3 * i + a], box[a], K[a]);
+            base[a] = (int)floor(u[a]);
+            for (int j = 0; j < order; ++j) w[a][j] = oracle_bspline(order, u[a] - (base[a] - j));
+        }
+        for (int j0 = 0; j0 < order; ++j0)
+            for (int j1 = 0; j1 < order; ++j1)
+                for (int j2 = 0; j2 < order; ++j2) {
+                    size_t idx = ((size_t)pme_mod(base[0] - j0, K[0]) * K[1] + pme_mod(base[1] - j1, K[1])) * K[2] +
+                                 pme_mod(base[2] - j2, K[2]);
+                    double wt = w[0][j0] * w[1][j1] * w[2][j2];
+                    Q[idx] += q[i] * wt;
+                    if (Qabs) Qabs[idx] += fabs(q[i]) * wt;
+                }
+    }
+    return 0;
+}
+
+/*
+ * Forces F[3n] = -q_i grad psi_i for the grid potential phi, psi[n]
+ * (optional) the interpolated potential of each atom, Fabs[3n] (optional)
+ * the sum of |terms| of each force component. Returns 0, or -1.
+ */
+int oracle_pme_gather(int n, const double *x, const double *q, const double *box, const int *K, int order,
+                      const double *phi, double *F, double *psi, double *Fabs) {
+    if (order < 2 || order > 16 || K[0] < 1 || K[1] < 1 || K[2] < 1) return -1;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+        double u[3], w[3][16], dw[3][16];
+        int base[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = pme_scaled(x[3 * i + a], box[a], K[a]);
+            base[a] = (int)floor(u[a]);
+            for (int j = 0; j < order; ++j) {
+                w[a][j] = oracle_bspline(order, u[a] - (base[a] - j));
+                dw[a][j] = oracle_bspline_deriv(order, u[a] - (base[a] - j)) * K[a] / box[a];
+            }
+        }
+        double f[3] = {0, 0, 0}, fa[3] = {0, 0, 0}, p = 0.0;
+        for (int j0 = 0; j0 < order; ++j0)
+            for (int j1 = 0; j1 < order; ++j1)
+                for (int j2 = 0; j2 < order; ++j2) {
+                    size_t idx = ((size_t)pme_mod(base[0] - j0, K[0]) * K[1] + pme_mod(base[1] - j1, K[1])) * K[2] +
+                                 pme_mod(base[2] - j2, K[2]);
+                    double ph = phi[idx];
+                    double t[3] = {dw[0][j0] * w[1][j1] * w[2][j2] * ph, w[0][j0] * dw[1][j1] * w[2][j2] * ph,
+                                   w[0][j0] * w[1][j1] * dw[2][j2] * ph};
+                    p += w[0][j0] * w[1][j1] * w[2][j2] * ph;
+                    for (int a = 0; a < 3; ++a) {
+                        f[a] -= q[i] * t[a];
+                        fa[a] += fabs(q[i] * t[a]);
+                    }
+                }
+        for (int a = 0; a < 3; ++a) {
+            F[3 * i + a] = f[a];
+            if (Fabs) Fabs[3 * i + a] = fa[a];
+        }
+        if (psi) psi[i] = p;
+    }
+    return 0;
+}
