@@ -78,14 +78,14 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the backward, batched, halo and million legs")
-    ap.add_argument("--legs", default="backward,batched,halo,million",
-                    help="comma-separated extra legs to run after the 96,000-atom one (default: all four)")
+    ap.add_argument("--legs", default="peak,small,pme,backward,batched,halo,million",
+                    help="comma-separated extra legs to run after the 96,000-atom one (default: all)")
     ap.add_argument("--no-tune", action="store_true",
                     help="default force launch shape and gathered tiles instead of autotuning them (for profiler "
                          "runs: under a profiler the tuner's timings, and so its choices, are not the bench's)")
     args = ap.parse_args()
     args.leg_set = set() if args.no_extras else {leg.strip() for leg in args.legs.split(",") if leg.strip()}
-    unknown = args.leg_set - {"backward", "batched", "halo", "million"}
+    unknown = args.leg_set - {"peak", "small", "pme", "backward", "batched", "halo", "million"}
     if unknown:
         ap.error(f"unknown legs: {sorted(unknown)}")
     return args
@@ -269,6 +269,211 @@ def _median_ms(fn, reps: int, stream):
         ts.append(a.elapsed_time(b))
     ts.sort()
     return ts[len(ts) // 2]
+
+
+def measure_fp32_peak(dev, reps: int = 12, iters: int = 8192) -> dict:
+    """FP32 rate of independent fused multiply-add chains on every SM (nb_fp32_peak_probe).
+
+    Scalar FFMA and packed FFMA2 forms, 8 blocks of 256 threads per SM, each
+    launch about 15 ms; three untimed launches, then ``reps`` launches timed
+    with events on the launching stream while nvidia-smi samples the clocks.
+    A fused multiply-add counts as 2 flops.
+    """
+    import torch
+
+    from paper_2405_01420_gb300 import nb
+    stream = torch.cuda.current_stream(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.empty(sms * 8 * 256, dtype=torch.float32, device=dev)
+    res = {}
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    for packed in (False, True):
+        flops = 0.0
+        for _ in range(3):
+            flops = nb.nb_fp32_peak_probe(out, packed=packed, iters=iters, stream=stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nb.nb_fp32_peak_probe(out, packed=packed, iters=iters, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        ts.sort()
+        res["ffma2" if packed else "ffma"] = {"tflops_best": flops / ts[0] / 1e12,
+                                              "tflops_median": flops / ts[len(ts) // 2] / 1e12,
+                                              "ms_per_launch": 1e3 * ts[len(ts) // 2]}
+    clocks = sampler.stop()
+    best = max(v["tflops_median"] for v in res.values())
+    return {"tflops": best, "forms": res, "clocks": clocks, "iters": iters, "reps": reps,
+            "how": f"{sms} SMs x 8 blocks x 256 threads, 8 independent FMA chains per thread, "
+                   f"{iters} x 16 steps per chain; median of {reps} event-timed launches; FMA = 2 flops"}
+
+
+def bench_small(dev, reps: int = 200, with_oracle: bool = True) -> dict:
+    """The smallest configuration: 1,536 atoms (512 waters), rc = rlist = 0.9 nm.
+
+    One call sequence = nb_search + nb_forces (forces and energies). Timed
+    two ways with events on the launching stream: as issued from Python one
+    call after the other, and as one replay of a CUDA graph that captured the
+    two calls. The oracle (FP64, all host cores) computes the same
+    evaluation, timed beside it. Median and p99 of ``reps`` sequences.
+    """
+    import torch
+
+    from paper_2405_01420_gb300 import nb
+    import oracle
+    rc = 0.9
+    beta = synth.ewald_beta(rc)
+    b = synth.water_box(512, 1)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    x, q, t, lj, eo, ei = d(b.coords), d(b.q), d(b.type), d(b.ljparams), d(b.excl_off), d(b.excl_idx)
+    stream = torch.cuda.current_stream(dev)
+    counter = nb.Pairlist(b.n_atoms, count_pairs=True)
+    counter.search(x, b.box, rc, eo, ei)
+    counter.forces(x, q, t, lj, rc, beta)
+    pairs = counter.stats()["pairs_last"]
+    assert counter.status() == 0
+    counter.close()
+
+    pl = nb.Pairlist(b.n_atoms)
+    F = torch.empty((b.n_atoms, 3), dtype=torch.float32, device=dev)
+    E = torch.empty(2, dtype=torch.float64, device=dev)
+
+    def seq(s=None):
+        pl.search(x, b.box, rc, eo, ei, stream=s)
+        pl.forces(x, q, t, lj, rc, beta, F, E, stream=s)
+
+    def timed(fn):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            ts.append(1e3 * a.elapsed_time(e))
+        return _percentile(ts, 50), _percentile(ts, 99)
+
+    plain50, plain99 = timed(seq)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            seq(side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph50, graph99 = timed(g.replay)
+    # the host's view of one replay: launch, then wait for the result
+    host = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        g.replay()
+        torch.cuda.synchronize()
+        host.append(1e6 * (time.perf_counter() - t0))
+    assert pl.status() == 0
+    Fo, elj, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                          b.excl_idx)
+    e = E.cpu().numpy()
+    assert abs(e[0] - elj) <= 1e-6 * abs(elj) and abs(e[1] - ec) <= 1e-6 * abs(ec)
+    pl.close()
+    out = {"workload": "water1.5k: 1,536-atom water box (512 waters, L 2.484 nm), rc = rlist = 0.9 nm; "
+                       "one nb_search + one nb_forces (forces and energies)",
+           "pairs": pairs, "plain_p50_us": plain50, "plain_p99_us": plain99, "graph_p50_us": graph50,
+           "graph_p99_us": graph99, "graph_host_wall_p50_us": _percentile(host, 50), "reps": reps,
+           "paper_context": "19.2 us: the paper's minimum NBNXM walltime, smallest Grappa input (about 1.5k "
+                            "atoms) on one MI250X GCD (Sec. III-A, Fig. 2); force kernel only, not a search"}
+    if with_oracle:
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            oracle.pairs_f64(b.coords, b.box, rc, b.excl_off, b.excl_idx)
+            oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off, b.excl_idx)
+            ts.append(1e6 * (time.perf_counter() - t0))
+        out["oracle_us"] = statistics.median(ts)
+        out["oracle_cores"] = oracle.threads()
+        out["oracle_sample"] = "pair set (FP64 brute force) + one FP64 force+energy evaluation, median of 5"
+    return out
+
+
+def pme_mesh(box, spacing: float = 0.12) -> tuple:
+    """Mesh with at most ``spacing`` nm between points; sizes with no prime factor above 7."""
+    def fft_size(n):
+        while True:
+            m = n
+            for p in (2, 3, 5, 7):
+                while m % p == 0:
+                    m //= p
+            if m == 1:
+                return n
+            n += 1
+    return tuple(fft_size(int(np.ceil(float(L) / spacing))) for L in box)
+
+
+def bench_pme(dev, reps: int = 50) -> dict:
+    """PME charge spreading and force gathering on the 96,000-atom box (84^3 mesh, order 4).
+
+    Ten calls of one kind are captured in a CUDA graph; a replay is timed
+    with events on the launching stream (median of ``reps``) and divided by
+    ten, so the device time per call excludes the host's launch overhead.
+    Inputs are resident; the mesh (2.4 MB) and the atoms (1.9 MB) stay in L2
+    between calls. The gather reads a random mesh potential (its cost does
+    not depend on the values).
+    """
+    import torch
+
+    from paper_2405_01420_gb300 import nb
+    b = synth.water_box(N_WATERS, 2)
+    K = pme_mesh(b.box)
+    x = torch.from_numpy(b.coords).to(dev)
+    q = torch.from_numpy(b.q).to(dev)
+    grid = torch.empty(K, dtype=torch.float32, device=dev)
+    phi = torch.randn(K, generator=torch.Generator(device=dev).manual_seed(1), device=dev)
+    F = torch.empty((b.n_atoms, 3), dtype=torch.float32, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(5):
+        nb.nb_pme_spread(x, q, b.box, K, grid)
+        nb.nb_pme_gather(x, q, b.box, K, phi, F, energy=E)
+    torch.cuda.synchronize()
+
+    def per_call_ms(call, calls=10):
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                for _ in range(calls):
+                    call(side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            g.replay()
+        return _median_ms(g.replay, reps, stream) / calls
+
+    spread_ms = per_call_ms(lambda st: nb.nb_pme_spread(x, q, b.box, K, grid, stream=st))
+    gather_ms = per_call_ms(lambda st: nb.nb_pme_gather(x, q, b.box, K, phi, F, energy=E, stream=st))
+    n = b.n_atoms
+    cells = int(np.prod(K))
+    # algorithmic bytes: spread reads x, q (16 B per atom) and writes the mesh once; gather reads x, q and
+    # the mesh once and writes the forces (12 B per atom)
+    spread_bytes = 16 * n + 4 * cells
+    gather_bytes = 16 * n + 4 * cells + 12 * n
+    return {"workload": f"96,000-atom water box, {K[0]}x{K[1]}x{K[2]} mesh (0.117 nm), B-spline order 4; "
+                        "spread = mesh cleared + charges spread; gather = forces + energy from a mesh potential",
+            "mesh": list(K), "spread_us": 1e3 * spread_ms, "gather_us": 1e3 * gather_ms,
+            "spread_atoms_per_s": n / (spread_ms / 1e3), "gather_atoms_per_s": n / (gather_ms / 1e3),
+            "spread_mesh_updates_per_s": 64 * n / (spread_ms / 1e3),
+            "spread_algorithmic_gbs": spread_bytes / (spread_ms / 1e3) / 1e9,
+            "gather_algorithmic_gbs": gather_bytes / (gather_ms / 1e3) / 1e9, "reps": reps}
 
 
 def bench_backward(dev, reps: int = 30):
@@ -794,6 +999,10 @@ def run_ours(args, rank, world, local):
     assert eng.check() == 0
 
     legs = args.leg_set
+    fp32_peak = measure_fp32_peak(dev) if "peak" in legs else None
+    small = bench_small(dev, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline)) \
+        if "small" in legs else None
+    pme = bench_pme(dev) if "pme" in legs else None
     backward = bench_backward(dev) if "backward" in legs else None
     batched = bench_batch(dev) if "batched" in legs else None
     halo = bench_halo(dev) if "halo" in legs else None
@@ -811,16 +1020,24 @@ def run_ours(args, rank, world, local):
         return
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak_max = sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peak_nominal = sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     achieved = FLOPS_PER_PAIR * pairs_per_eval / (kern_ms_per_launch / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
+    nominal_basis = f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x 2070 MHz (max SM clock)"
+    if fp32_peak is not None:
+        peak, basis = fp32_peak["tflops"], ("measured: FP32 FMA-chain probe (nb_fp32_peak_probe), the faster of "
+                                            "FFMA and FFMA2, in this run; see fp32_peak")
+    else:
+        peak, basis = peak_nominal, nominal_basis
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": load_traffic(),
             "kernel": "k_force_vt (gathered 4x8 tiles after the prune; LJ + Ewald real-space, energies on)",
-            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x 2070 MHz (max SM clock)",
+            "peak_basis": basis, "peak_nominal": peak_nominal, "peak_nominal_basis": nominal_basis,
+            "frac_nominal": achieved / peak_nominal,
+            "peak_measured": None if fp32_peak is None else fp32_peak["tflops"],
             "kernel_us_per_launch": 1e3 * kern_ms_per_launch}
     if clocks and clocks.get("sm_mhz"):
         peak_clk = sms * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12
-        roof["frac_at_measured_clock"] = achieved / peak_clk
+        roof["frac_nominal_at_measured_clock"] = achieved / peak_clk
     # our kernels per call: a search 6 (system table, 4 grid-sort kernels, search; the exclusion list only
     # with the excluded-pair correction, which this workload leaves off), a prune 4 (its gather, prune,
     # length offsets, length scatter), an evaluation 3 (gather, force, scatter)
@@ -837,10 +1054,13 @@ def run_ours(args, rank, world, local):
         "force_shape": {"threads": shape[0], "chunk": shape[1], "blocks_per_sm": shape[2], "tuned_ms": shape_times,
                         "tile_form": tile_form, "tile_form_ms": tile_times},
         "roofline": roof,
+        "fp32_peak": fp32_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": n_launch_search * searches + n_launch_prune * prunes + n_launch_force * args.evals,
+        "small": small,
+        "pme": pme,
         "backward": backward,
         "batched": batched,
         "million": million,

@@ -388,6 +388,46 @@ int nb_set_coulomb(nb_pairlist *pl, int kind, float eps_rf, unsigned flags);
 int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_sm);
 
 /*
+ * Smooth particle-mesh Ewald: charge spreading and force gathering.
+ *
+ * §III-A (Fig. 2 and the kernel list after it) names PME as the next
+ * rate-limiting GPU work after the short-range kernel; the paper prints no
+ * formulas, and these calls follow the smooth PME of Essmann et al.
+ * (J. Chem. Phys. 103, 8577, 1995) with cardinal B-splines of order 4 in an
+ * orthorhombic box. The FFT solve between them (Q -> phi) is not part of
+ * this library: phi is whatever mesh potential the caller supplies (in
+ * smooth PME, the reciprocal-space kernel convolved with Q).
+ *
+ *   u_a      = K_a x_a / L_a, the scaled fractional coordinate (any image of
+ *              x is accepted; u is taken modulo K_a)
+ *   M(u)     = the cubic cardinal B-spline, nonzero on (0, 4)
+ *   Q(k)     = sum_i q_i prod_a M(u_ia - k_a)            (k_a taken mod K_a)
+ *   psi_i    = sum_k prod_a M(u_ia - k_a) phi(k)
+ *   F_ia     = -q_i dpsi_i/dx_ia
+ *            = -q_i (K_a / L_a) sum_k M'(u_ia - k_a) prod_{b != a} M(u_ib - k_b) phi(k)
+ *   energy   = (1/2) sum_i q_i psi_i   (= (1/2) sum_k Q(k) phi(k))
+ *
+ * Mesh layout: float[K0 * K1 * K2], index (k0 * K1 + k1) * K2 + k2 (the z
+ * index fastest), device memory owned by the caller. Atoms in the caller's
+ * order: coords float[3 n_atoms], q float[n_atoms], device. box is a HOST
+ * float[3] (edges > 0). order must be 4 and each K_a in [4, 4096], else
+ * NB_ERR_ARG; n_atoms = 0 is allowed. Arithmetic is FP32 with the scaled
+ * coordinates formed as a two-float product (fractional parts exact to
+ * about 2^-24 at any K); mesh values are summed with FP32 atomics, so their
+ * last bits depend on the order the atoms land in. Non-finite coordinates
+ * give NaN in the mesh or the forces, never an access outside the mesh.
+ * Both calls are queued on stream and do not synchronise.
+ */
+/* grid (DEVICE float[K0*K1*K2]) is overwritten with Q. */
+int nb_pme_spread(int n_atoms, const float *coords, const float *q, const float *box, int K0, int K1, int K2,
+                  int order, float *grid, void *stream);
+/* phi: DEVICE float[K0*K1*K2]. forces: DEVICE float[3 n_atoms], overwritten
+ * (accumulate = 0) or added to (accumulate != 0). energy: DEVICE double[1]
+ * or NULL; overwritten with (1/2) sum_i q_i psi_i, summed in FP64. */
+int nb_pme_gather(int n_atoms, const float *coords, const float *q, const float *box, int K0, int K1, int K2,
+                  int order, const float *phi, float *forces, int accumulate, double *energy, void *stream);
+
+/*
  * FP32 throughput probe (measurement only; no counterpart in the paper).
  * The force kernel is bound by FP32 arithmetic, and this call measures the
  * rate its roofline divides by: a grid of blocks_per_sm (1..8) blocks of

@@ -114,6 +114,9 @@ SIGNATURES = {
     "nb_backward": (_I, [_P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P, _P]),
     "nb_forces_noalloc": (_I, [_I, _P, _P, _P, _P, _I, _P, _F, _F, _P, _P, _P, _P,
                                ctypes.POINTER(ctypes.c_uint), _P]),
+    "nb_fp32_peak_probe": (_I, [_I, _I, _I, _P, _SZ, ctypes.POINTER(ctypes.c_double), _P]),
+    "nb_pme_spread": (_I, [_I, _P, _P, _P, _I, _I, _I, _I, _P, _P]),
+    "nb_pme_gather": (_I, [_I, _P, _P, _P, _I, _I, _I, _I, _P, _P, _I, _P, _P]),
 }
 
 NB_NOALLOC_MAX_ATOMS = 4096
@@ -325,6 +328,50 @@ def nb_forces_noalloc(coords, box, q, type_, ljparams, rc, beta, forces, energie
         _dev(energies, torch.float64, 2, "energies", True), ctypes.byref(word) if read_error_word else None,
         _stream(stream)))
     return int(word.value) if read_error_word else None
+
+
+def nb_fp32_peak_probe(out, packed: bool = True, blocks_per_sm: int = 8, iters: int = 4096, stream=None) -> float:
+    """Queue the FP32 fused multiply-add probe on ``stream``; returns the FP32
+    operations it performs (a fused multiply-add counted as 2). ``out`` is a
+    float32 device tensor with at least SMs x blocks_per_sm x 256 elements."""
+    flops = ctypes.c_double(0.0)
+    _check(load_library().nb_fp32_peak_probe(int(bool(packed)), int(blocks_per_sm), int(iters),
+                                             _dev(out, torch.float32, None, "out"), out.numel(),
+                                             ctypes.byref(flops), _stream(stream)))
+    return float(flops.value)
+
+
+def _mesh(K):
+    K = tuple(int(k) for k in K)
+    if len(K) != 3:
+        raise ValueError("K must give three mesh dimensions")
+    return K
+
+
+def nb_pme_spread(coords, q, box, K, grid, order: int = 4, stream=None) -> None:
+    """Smooth-PME charge spreading: ``grid`` (float32 [K0, K1, K2], device) is
+    overwritten with Q(k) = sum_i q_i prod_a M4(u_ia - k_a)."""
+    n = coords.numel() // 3
+    K = _mesh(K)
+    box_h = (ctypes.c_float * 3)(*[float(v) for v in box])
+    _check(load_library().nb_pme_spread(
+        n, _dev(coords, torch.float32, 3 * n, "coords"), _dev(q, torch.float32, n, "q"), box_h, *K, int(order),
+        _dev(grid, torch.float32, K[0] * K[1] * K[2], "grid"), _stream(stream)))
+
+
+def nb_pme_gather(coords, q, box, K, phi, forces, order: int = 4, accumulate: bool = False, energy=None,
+                  stream=None) -> None:
+    """Smooth-PME force gathering from the mesh potential ``phi``: forces
+    (float32 [N, 3], device) set to, or with ``accumulate`` added to,
+    -q grad psi; ``energy`` (float64 [1], device, optional) set to
+    (1/2) sum_i q_i psi_i."""
+    n = coords.numel() // 3
+    K = _mesh(K)
+    box_h = (ctypes.c_float * 3)(*[float(v) for v in box])
+    _check(load_library().nb_pme_gather(
+        n, _dev(coords, torch.float32, 3 * n, "coords"), _dev(q, torch.float32, n, "q"), box_h, *K, int(order),
+        _dev(phi, torch.float32, K[0] * K[1] * K[2], "phi"), _dev(forces, torch.float32, 3 * n, "forces"),
+        int(bool(accumulate)), _dev(energy, torch.float64, 1, "energy", True), _stream(stream)))
 
 
 def nb_pairlist_export_tiles(pl, stream=None) -> dict:

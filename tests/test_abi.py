@@ -166,3 +166,36 @@ def test_noalloc_argument_checks_run_on_the_host(lib):
     assert call(10, box, beta=4.0) == nb.NB_ERR_ARG  # beta * rc > 3.2
     assert call(10, small_box) == nb.NB_ERR_ARG      # an edge not above 2 rc
     assert lib.nb_last_error().decode().startswith("nb_forces_noalloc")
+
+
+def test_pme_argument_checks_run_on_the_host(lib):
+    """nb_pme_spread / nb_pme_gather reject bad orders, mesh sizes, boxes and
+    pointers before any CUDA call."""
+    import numpy as np
+    from paper_2405_01420_gb300 import nb
+    lib.nb_last_error.restype = ctypes.c_char_p
+    sp, ga = lib.nb_pme_spread, lib.nb_pme_gather
+    sp.restype, sp.argtypes = nb.SIGNATURES["nb_pme_spread"]
+    ga.restype, ga.argtypes = nb.SIGNATURES["nb_pme_gather"]
+    box = np.array([3.0, 3.0, 3.0], np.float32)
+    bad_box = np.array([3.0, 0.0, 3.0], np.float32)
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every case fails on the host first
+
+    def spread(n=10, b=box, K=(16, 16, 16), order=4, grid=dummy, x=dummy):
+        return sp(n, x, dummy, b.ctypes.data_as(ctypes.c_void_p), *K, order, grid, None)
+
+    def gather(n=10, b=box, K=(16, 16, 16), order=4, phi=dummy, forces=dummy):
+        return ga(n, dummy, dummy, b.ctypes.data_as(ctypes.c_void_p), *K, order, phi, forces, 0, None, None)
+
+    for call, name in ((spread, "nb_pme_spread"), (gather, "nb_pme_gather")):
+        assert call(n=-1) == nb.NB_ERR_ARG
+        assert call(order=5) == nb.NB_ERR_ARG
+        assert "order 4" in lib.nb_last_error().decode()
+        assert call(K=(3, 16, 16)) == nb.NB_ERR_ARG
+        assert call(K=(16, 16, 4097)) == nb.NB_ERR_ARG
+        assert call(b=bad_box) == nb.NB_ERR_ARG
+        assert lib.nb_last_error().decode().startswith(name)
+    assert spread(grid=None) == nb.NB_ERR_ARG
+    assert spread(x=None) == nb.NB_ERR_ARG
+    assert gather(phi=None) == nb.NB_ERR_ARG
+    assert gather(forces=None) == nb.NB_ERR_ARG

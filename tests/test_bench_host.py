@@ -23,7 +23,7 @@ def test_defaults_run_every_leg_on_one_gpu(monkeypatch):
     a = parse(monkeypatch)
     assert (a.gpus, a.steps, a.warmup, a.impl, a.evals) == (1, 20, 3, "ours", 100)
     assert a.warmup >= 3
-    assert a.leg_set == {"backward", "batched", "halo", "million"}
+    assert a.leg_set == {"peak", "small", "pme", "backward", "batched", "halo", "million"}
     assert not a.no_tune
 
 
