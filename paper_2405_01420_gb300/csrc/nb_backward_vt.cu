@@ -9,8 +9,11 @@
 //  - i side: registers over the whole half, reduced across the warp at its
 //    end (reduce-scatter), one vector atomic per row.
 //  - dL/dC6, dL/dC12: per-lane FP32 accumulators for each (row, j type),
-//    reduced across the warp once per half and added in FP64 to the
-//    unsymmetrised [ntype][ntype][2] accumulator.
+//    kept in shared memory (one column per lane, so a lane's adds never
+//    meet another lane's bank), reduced across the warp once per half by a
+//    skewed read (lane k sums row k, starting at bank k) and added in FP64
+//    to the unsymmetrised [ntype][ntype][2] accumulator. In registers they
+//    took 32 of them and held the kernel at 4 warps per scheduler.
 // Group g + 1's j data (coordinates and charge, g, type, mask word) are
 // copied into shared memory with cp.async while group g computes.
 #include "nb_pair.cuh"
@@ -20,6 +23,7 @@ namespace {
 
 constexpr int kBvtThreads = 128;
 constexpr int kBvtWarps = kBvtThreads / 32;
+constexpr int kBvtCtasPerSm = 5;  // 102 registers per thread
 
 struct BvtParams {
     const float4 *xq;
@@ -43,6 +47,7 @@ struct BvtParams {
     int pad_slot;  // never holds an atom: far away, q = 0, type 0
     int nreg;      // regions of gathered tiles (2 with a halo: local, non-local)
     int reg_stride;  // 2 nc_max
+    int nseg;      // work items per half: its groups of tiles split into nseg ranges
 };
 
 struct BvtStage {
@@ -70,9 +75,11 @@ __device__ __forceinline__ int stage_adj(const BvtParams &p, BvtStage &st, int t
 }
 
 template <int NT, int COUL>
-__global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
+__global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtParams p) {
+    constexpr int kAcc = 4 * NT * 2;  // (row a, j type t, C6 / C12) accumulators per lane
     extern __shared__ float4 s_lj[];  // (C6, C12, 0, 0)
     __shared__ BvtStage s_st[kBvtWarps][2];
+    __shared__ float s_acc[kBvtWarps][kAcc][32];  // [value][lane]
     __shared__ float4 s_shift[kBvtWarps][27];
     __shared__ float4 s_xi[kBvtWarps][4];  // (x, y, z, f q)
     __shared__ float4 s_gi[kBvtWarps][4];
@@ -94,19 +101,27 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nhalf = 2u * (unsigned)p.st->nc;
-    const unsigned nwork = nhalf * (unsigned)p.nreg;
+    const unsigned nwork = nhalf * (unsigned)p.nreg * (unsigned)p.nseg;
     int shift_sys = -1;
+    float(*acc)[32] = s_acc[warp];
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) acc[k][lane] = 0.0f;
 
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= nwork) break;
-        const unsigned reg = w / nhalf, hw = w - reg * nhalf;
+        // work item w: range seg of the groups of half hw of region reg
+        const unsigned unit = w / (unsigned)p.nseg, seg = w - unit * (unsigned)p.nseg;
+        const unsigned reg = unit / nhalf, hw = unit - reg * nhalf;
         const int ci = p.order ? p.order[hw >> 1] : (int)(hw >> 1);
         const int h = (int)(hw & 1u);
         const size_t hidx = (size_t)reg * p.reg_stride + 2 * ci + h;
-        const int t0 = p.half_start[hidx], t1 = t0 + p.half_len[hidx];
+        const int th = p.half_start[hidx], nth = p.half_len[hidx];
+        const int gh = (nth + 3) >> 2;  // groups of the half
+        const int t0 = th + 4 * (int)(((long long)gh * seg) / p.nseg);
+        const int t1 = min(th + nth, th + 4 * (int)(((long long)gh * (seg + 1)) / p.nseg));
         if (t1 <= t0) continue;
         const int csys = p.clus_sys[ci];
         if (csys != shift_sys) {
@@ -122,13 +137,8 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
             s_tr[warp][lane] = p.tsort[ibase + lane] * p.ntype;
         }
         float4 bi[4];
-        float acc[4][NT][2];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            bi[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int t = 0; t < NT; ++t) acc[a][t][0] = acc[a][t][1] = 0.0f;
-        }
+        for (int a = 0; a < 4; ++a) bi[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         const int ngroups = (t1 - t0 + 3) >> 2;
         cp_async_wait_all();
         __syncwarp();
@@ -151,12 +161,9 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
                 float d6, d12;
                 nb_pair_adj<true, COUL>(xi, xi.w, s_gi[warp][a], xj, qj_f, gj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
                                   ((mrow >> (8 * a)) & 1u) != 0u, p.cc, p.k2, bi[a], bj, d6, d12);
-#pragma unroll
-                for (int t = 0; t < NT; ++t) {  // one-hot by the j atom's type
-                    const float oh = (tj == t) ? 1.0f : 0.0f;
-                    acc[a][t][0] = fmaf(oh, d6, acc[a][t][0]);
-                    acc[a][t][1] = fmaf(oh, d12, acc[a][t][1]);
-                }
+                // the lane's own column: tj < ntype <= NT (the gather keeps types in range)
+                acc[(a * NT + tj) * 2 + 0][lane] += d6;
+                acc[(a * NT + tj) * 2 + 1][lane] += d12;
             }
             if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
                 atomicAdd(p.bsort + slot, bj);
@@ -181,30 +188,27 @@ __global__ void __launch_bounds__(kBvtThreads, 4) k_backward_vt(BvtParams p) {
             const float rq = __shfl_down_sync(0xffffffffu, r[0], 6);
             if ((lane & 7) == 0) atomicAdd(p.bsort + ibase + (lane >> 3), make_float4(r[0], ry, rz, rq));
         }
-        // LJ gradients: value (a NT + t) 2 + c
-        {
-            constexpr int kN = 8 * NT;
-            constexpr int kShift = NT == 4 ? 0 : (NT == 2 ? 1 : 2);  // lane -> value: lane >> kShift
-            float r[kN];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int t = 0; t < NT; ++t) {
-                    r[(a * NT + t) * 2 + 0] = acc[a][t][0];
-                    r[(a * NT + t) * 2 + 1] = acc[a][t][1];
-                }
-            reduce_scatter<kN>(r, lane);
-            const int k = lane >> kShift;
-            const int a = k / (2 * NT), t = (k >> 1) % NT, c = k & 1;
-            if ((lane & ((1 << kShift) - 1)) == 0 && t < p.ntype)
-                atomicAdd(&p.glj_acc[2 * (s_tr[warp][a] + t) + c], (double)r[0]);
+        // LJ gradients: value k = (a NT + t) 2 + c, summed over the 32 lane columns by lane k,
+        // which starts at column k so that the 32 lanes read 32 different banks; each value is
+        // cleared as it is read
+        __syncwarp();
+        if (lane < kAcc) {
+            float sum = 0.0f;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                const int col = (i + lane) & 31;
+                sum += acc[lane][col];
+                acc[lane][col] = 0.0f;
+            }
+            const int a = lane / (2 * NT), t = (lane >> 1) % NT, c = lane & 1;
+            if (t < p.ntype && sum != 0.0f) atomicAdd(&p.glj_acc[2 * (s_tr[warp][a] + t) + c], (double)sum);
         }
         __syncwarp();
     }
 }
 
 template <int NT, int COUL>
-cudaError_t launch_bvt(nb_pairlist *pl, const BvtParams &p, cudaStream_t s) {
+cudaError_t launch_bvt(nb_pairlist *pl, BvtParams p, cudaStream_t s) {
     const size_t smem = sizeof(float4) * (size_t)p.ntype * p.ntype;
     static int per_sm = 0;
     if (per_sm == 0) {
@@ -213,7 +217,9 @@ cudaError_t launch_bvt(nb_pairlist *pl, const BvtParams &p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    const int blocks = min(pl->num_sms * per_sm, (2 * p.nreg * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
+    // small systems: each half's groups split into up to 8 ranges (one work item each)
+    p.nseg = nb_work_split(pl->num_sms * per_sm * kBvtWarps, 2 * p.nreg * pl->nc_max);
+    const int blocks = min(pl->num_sms * per_sm, (2 * p.nreg * pl->nc_max * p.nseg + kBvtWarps - 1) / kBvtWarps);
     return nb_launch_pdl(k_backward_vt<NT, COUL>, max(blocks, 1), kBvtThreads, smem, s, p);
 }
 

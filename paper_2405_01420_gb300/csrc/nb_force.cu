@@ -138,6 +138,7 @@ struct ForceParams {
     int part;                        // NB_PART_*: ALL computes every pair
     const unsigned char *clus_home;  // with a part: bit b = slot b of the cluster holds a home atom
     int finalize;                    // move the displacement maxima of this evaluation to last_*
+    int nseg;                        // work items per i-cluster: its list split into nseg ranges
 };
 
 
@@ -199,21 +200,27 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
     int cur_sys = -1;
     unsigned cnt = 0;
 
+    const unsigned nwork = (unsigned)nc * (unsigned)p.nseg;
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        const int ci = (w < (unsigned)nc && p.order) ? p.order[w] : (int)w;
-        const int csys = (w < (unsigned)nc) ? p.clus_sys[ci] : -1;
+        // work item w: range seg of the list of the i-cluster at position idx of the order
+        const unsigned idx = w / (unsigned)p.nseg, seg = w - idx * (unsigned)p.nseg;
+        const int ci = (w < nwork && p.order) ? p.order[idx] : (int)idx;
+        const int csys = (w < nwork) ? p.clus_sys[ci] : -1;
         if (ENERGY && csys != cur_sys) {
             if (cur_sys >= 0) flush_energies(ecd, eljd, lane, p.energies + 2 * cur_sys);
             ecd = 0.0;
             eljd = 0.0;
             cur_sys = csys;
         }
-        if (w >= (unsigned)nc) break;
+        if (w >= nwork) break;
         const float4 *shift = p.sys_shift + 27 * csys;
-        const int k0 = p.ci_start[ci], k1 = k0 + p.ci_len[ci];
+        const int kc = p.ci_start[ci], len = p.ci_len[ci];
+        const int k0 = kc + (int)(((long long)len * seg) / p.nseg);
+        const int k1 = kc + (int)(((long long)len * (seg + 1)) / p.nseg);
+        if (k1 <= k0) continue;
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
         const float qi1 = xi1.w * NB_COULOMB_F, qi2 = xi2.w * NB_COULOMB_F;
         const int tr1 = p.tsort[ci * NB_CLUSTER + a1] * p.ntype;
@@ -438,7 +445,10 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     }
     int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
     int blocks = pl->num_sms * use;
-    blocks = min(blocks, (pl->nc_max + threads / 32 - 1) / (threads / 32));
+    // A system with fewer i-clusters than the grid has warps would leave most SMs idle with
+    // one warp per cluster: its lists are then split into up to 8 ranges, one work item each.
+    p.nseg = nb_work_split(blocks * (threads / 32), pl->nc_max);
+    blocks = min(blocks, (pl->nc_max * p.nseg + threads / 32 - 1) / (threads / 32));
     blocks = max(blocks, 1);
     return nb_launch_pdl(fn, blocks, threads, smem, s, p);
 }

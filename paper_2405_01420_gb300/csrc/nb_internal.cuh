@@ -169,6 +169,15 @@ __device__ __forceinline__ int nb_shift_z(int s) { return s % 3 - 1; }
 int nb_record_error(int code, const char *msg);
 
 // ---------------------------------------------------------------------------
+// Work items per unit (an i-cluster or a half cluster) of the force and
+// adjoint kernels: 1 when there are at least as many units as the grid has
+// warps, else up to 8 so that a small system still reaches every SM.
+inline int nb_work_split(int grid_warps, int units) {
+    if (units <= 0) return 1;
+    const int k = grid_warps / units;
+    return k < 1 ? 1 : (k > 8 ? 8 : k);
+}
+
 // Programmatic dependent launch. A kernel launched with nb_launch_pdl may be
 // scheduled while the work before it in the stream is still running: its
 // blocks fill SMs that the predecessor's tail leaves idle, so the launch

@@ -73,7 +73,10 @@ def test_batch_matches_oracle_and_plain(nb, batch):
         F1, E1 = p1.forces(dev(b.coords), dev(b.q), dev(b.type), lj, rc, beta)
         np.testing.assert_allclose(F[off[k]:off[k + 1]], F1.cpu().numpy(), rtol=0,
                                    atol=1e-5 * np.abs(Fo).max())
-        assert rel(E[k, 0], E1[0].item()) <= 1e-7 and rel(E[k, 1], E1[1].item()) <= 1e-7
+        # A small system alone splits its i-clusters' lists over more warps than the batch does,
+        # so the two sum their FP32 pair energies in different orders: both meet the oracle's bar.
+        assert rel(E1[0].item(), elj) <= E_TOL and rel(E1[1].item(), ec) <= E_TOL, k
+        assert rel(E[k, 0], E1[0].item()) <= E_TOL and rel(E[k, 1], E1[1].item()) <= E_TOL
         p1.close()
     assert pl.stats()["pairs_last"] == total_pairs
     # prune on top of the batch list
