@@ -77,7 +77,7 @@ def parse_args():
     ap.add_argument("--evals", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the backward, batched, halo and million legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip every extra leg (see --legs)")
     ap.add_argument("--legs", default="peak,small,pme,backward,batched,halo,million",
                     help="comma-separated extra legs to run after the 96,000-atom one (default: all)")
     ap.add_argument("--no-tune", action="store_true",
@@ -319,8 +319,10 @@ def bench_small(dev, reps: int = 200, with_oracle: bool = True) -> dict:
     One call sequence = nb_search + nb_forces (forces and energies). Timed
     two ways with events on the launching stream: as issued from Python one
     call after the other, and as one replay of a CUDA graph that captured the
-    two calls. The oracle (FP64, all host cores) computes the same
-    evaluation, timed beside it. Median and p99 of ``reps`` sequences.
+    two calls; and the force call alone (gather, force kernel, permute-back
+    on the searched list) as a graph replay. The oracle (FP64, all host
+    cores) computes the same evaluation, timed beside it. Median and p99 of
+    ``reps`` sequences.
     """
     import torch
 
@@ -372,6 +374,15 @@ def bench_small(dev, reps: int = 200, with_oracle: bool = True) -> dict:
     stream.wait_stream(side)
     torch.cuda.synchronize()
     graph50, graph99 = timed(g.replay)
+    # the force call alone (gather, force kernel, permute-back) on the searched list, as a graph
+    gf = torch.cuda.CUDAGraph()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(gf, stream=side):
+            pl.forces(x, q, t, lj, rc, beta, F, E, stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    forces50, forces99 = timed(gf.replay)
     # the host's view of one replay: launch, then wait for the result
     host = []
     for _ in range(reps):
@@ -388,7 +399,8 @@ def bench_small(dev, reps: int = 200, with_oracle: bool = True) -> dict:
     out = {"workload": "water1.5k: 1,536-atom water box (512 waters, L 2.484 nm), rc = rlist = 0.9 nm; "
                        "one nb_search + one nb_forces (forces and energies)",
            "pairs": pairs, "plain_p50_us": plain50, "plain_p99_us": plain99, "graph_p50_us": graph50,
-           "graph_p99_us": graph99, "graph_host_wall_p50_us": _percentile(host, 50), "reps": reps,
+           "graph_p99_us": graph99, "graph_host_wall_p50_us": _percentile(host, 50),
+           "forces_only_graph_p50_us": forces50, "forces_only_graph_p99_us": forces99, "reps": reps,
            "paper_context": "19.2 us: the paper's minimum NBNXM walltime, smallest Grappa input (about 1.5k "
                             "atoms) on one MI250X GCD (Sec. III-A, Fig. 2); force kernel only, not a search"}
     if with_oracle:
@@ -605,22 +617,41 @@ def bench_million(dev, n_evals: int = 50, with_oracle: bool = True):
     return out
 
 
-def bench_halo(dev, reps: int = 30):
+def bench_halo(dev, reps: int = 30) -> dict:
     """Local / non-local split with a synthetic halo exchange (96,000 atoms).
 
-    Waters with the oxygen at x >= 0.75 L are halo atoms (numbered last).
-    Each evaluation copies the halo atoms' coordinates from pinned host
-    memory (the receive of a halo exchange), then computes forces and
-    energies. Sequential: copy, then nb_forces. Overlapped: the local part
-    runs on the compute stream while the copy runs on a second stream; the
-    non-local part waits for the copy. Median wall time per evaluation.
+    Two halo shapes of a domain decomposition with a halo of width rlist:
+    ``slab`` (the waters whose oxygen lies within rlist of the upper x face,
+    one neighbour domain) and ``shell`` (within rlist of any of the three
+    upper faces, as in an eighth-shell decomposition). Halo atoms are
+    numbered last. Each evaluation copies the halo atoms' coordinates from
+    pinned host memory (the receive of a halo exchange), then computes
+    forces and energies. Sequential: copy, then nb_forces. Overlapped: the
+    local part runs on the compute stream while the copy runs on a second
+    stream; the non-local part waits for the copy. Also timed on their own:
+    the copy, the unsplit forces, the local part and the non-local part.
+    Each schedule is captured in a CUDA graph (the copy a memcpy node, the
+    wait a graph edge) and replayed: medians over ``reps`` replays, events on
+    the compute stream, so host launch overhead is not counted.
     """
+    out = {}
+    for shape in ("slab", "shell"):
+        out[shape] = _halo_case(dev, shape, reps)
+    return out
+
+
+def _halo_case(dev, shape: str, reps: int) -> dict:
     import torch
     from paper_2405_01420_gb300 import nb
     b = synth.water_box(N_WATERS, 2)
-    o_x = b.coords[0::3, 0]
-    home = np.flatnonzero(o_x < 0.75 * b.box[0])
-    halo = np.flatnonzero(o_x >= 0.75 * b.box[0])
+    L = b.box.astype(np.float64)
+    o = b.coords[0::3].astype(np.float64)
+    if shape == "slab":
+        is_halo = o[:, 0] >= L[0] - RLIST
+    else:
+        is_halo = (o >= L - RLIST).any(axis=1)
+    home = np.flatnonzero(~is_halo)
+    halo = np.flatnonzero(is_halo)
     atoms = (3 * np.concatenate([home, halo])[:, None] + np.arange(3)[None, :]).reshape(-1)
     x = np.ascontiguousarray(b.coords[atoms])
     n_home = 3 * len(home)
@@ -647,29 +678,65 @@ def bench_halo(dev, reps: int = 30):
     side = torch.cuda.Stream(dev)
     halo_dev = xd[n_home:]
 
-    def sequential():
+    def copy():
         halo_dev.copy_(halo_host, non_blocking=True)
+
+    def forces():
         nb.nb_forces(pl.handle, xd, q, t, lj, RC, beta, F, E)
 
-    def overlapped():
-        side.wait_stream(main)
-        with torch.cuda.stream(side):
-            halo_dev.copy_(halo_host, non_blocking=True)
+    def local():
         nb.nb_forces_part(pl.handle, nb.NB_PART_LOCAL, xd, q, t, lj, RC, beta, None, E)
-        main.wait_stream(side)
+
+    def nonlocal_():
         nb.nb_forces_part(pl.handle, nb.NB_PART_NONLOCAL, xd, q, t, lj, RC, beta, F, E)
+
+    def sequential():
+        copy()
+        forces()
+
+    def overlapped():
+        cur = torch.cuda.current_stream(dev)  # the compute stream (the capturing one inside a graph)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            copy()
+        local()
+        cur.wait_stream(side)
+        nonlocal_()
 
     for _ in range(5):
         sequential()
         overlapped()
     torch.cuda.synchronize()
-    t_seq = _median_ms(sequential, reps, main)
-    t_ovl = _median_ms(overlapped, reps, main)
+
+    def graph_ms(fn):
+        # captured once and replayed: the device time without the host's launch overhead
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(main)
+        with torch.cuda.graph(g, stream=cap):
+            fn()
+        main.wait_stream(cap)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            g.replay()
+        return _median_ms(g.replay, reps, main)
+
+    t_copy = graph_ms(copy)
+    t_forces = graph_ms(forces)
+    t_local = graph_ms(local)
+    t_nonlocal = graph_ms(lambda: (local(), nonlocal_())) - t_local
+    t_seq = graph_ms(sequential)
+    t_ovl = graph_ms(overlapped)
     assert pl.status() == 0
     pl.close()
-    return {"workload": "96,000-atom water box, waters with O at x >= 0.75 L as halo atoms "
-                        f"({N - n_home} atoms, {12 * (N - n_home)} B of coordinates copied from pinned host "
-                        "memory per evaluation), rc 1.0 / r_inner 1.04 nm, after a prune",
+    desc = ("waters with O within rlist of the upper x face" if shape == "slab"
+            else "waters with O within rlist of any upper face (eighth shell)")
+    return {"workload": f"96,000-atom water box, {desc} as halo atoms ({N - n_home} atoms, "
+                        f"{12 * (N - n_home)} B of coordinates copied from pinned host memory per evaluation), "
+                        "rc 1.0 / r_inner 1.04 nm, after a prune",
+            "halo_atoms": N - n_home, "us_copy": 1e3 * t_copy, "us_forces": 1e3 * t_forces,
+            "us_local": 1e3 * t_local, "us_nonlocal": 1e3 * t_nonlocal,
+            "us_split_cost": 1e3 * (t_local + t_nonlocal - t_forces),
             "us_sequential": 1e3 * t_seq, "us_overlapped": 1e3 * t_ovl, "saving": 1.0 - t_ovl / t_seq}
 
 

@@ -337,7 +337,10 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
     // ordering the clusters by list length waits for the first force or adjoint call on this list: a
     // prune that comes first orders them by its own (pruned) work instead
     pl->sorted = 0;
-    pl->sort_pending = !(pl->flags & NB_FLAG_NO_LIST_SORT);
+    // A system small enough that the force kernel splits every list four ways or more has no
+    // launch tail for the ordering to shorten: its three kernels would only add latency.
+    const bool small = (long long)pl->nc_max * 4 <= (long long)pl->num_sms * 32;
+    pl->sort_pending = !(pl->flags & NB_FLAG_NO_LIST_SORT) && !small;
     pl->searched = 1;
     pl->has_inner = 0;
     pl->has_vtiles = 0;

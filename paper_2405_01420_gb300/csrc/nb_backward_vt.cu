@@ -16,14 +16,14 @@
 //    took 32 of them and held the kernel at 4 warps per scheduler.
 // Group g + 1's j data (coordinates and charge, g, type, mask word) are
 // copied into shared memory with cp.async while group g computes.
-#include "nb_pair.cuh"
+#include "nb_pair_x2.cuh"
 #include "nb_warp.cuh"
 
 namespace {
 
 constexpr int kBvtThreads = 128;
 constexpr int kBvtWarps = kBvtThreads / 32;
-constexpr int kBvtCtasPerSm = 5;  // 102 registers per thread
+constexpr int kBvtCtasPerSm = 6;  // 85 registers per thread (80 used, no spills)
 
 struct BvtParams {
     const float4 *xq;
@@ -42,12 +42,12 @@ struct BvtParams {
     const int *clus_sys;
     int ntype;
     nb_coul cc;
+    nb_coul2 cc2;  // the same constants in packed form
     float k2;  // 2 (2 beta/sqrt(pi)) beta^2
     float stale_prune2;
     int pad_slot;  // never holds an atom: far away, q = 0, type 0
     int nreg;      // regions of gathered tiles (2 with a halo: local, non-local)
     int reg_stride;  // 2 nc_max
-    int nseg;      // work items per half: its groups of tiles split into nseg ranges
 };
 
 struct BvtStage {
@@ -77,13 +77,17 @@ __device__ __forceinline__ int stage_adj(const BvtParams &p, BvtStage &st, int t
 template <int NT, int COUL>
 __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtParams p) {
     constexpr int kAcc = 4 * NT * 2;  // (row a, j type t, C6 / C12) accumulators per lane
-    extern __shared__ float4 s_lj[];  // (C6, C12, 0, 0)
+    // dynamic: the ntype x ntype LJ table (C6, C12, 0, 0), then per warp, by j type t, the half's
+    // row pairs' (C6_a, C6_b, C12_a, C12_b) at [2t + k]
+    extern __shared__ float4 s_lj[];
     __shared__ BvtStage s_st[kBvtWarps][2];
     __shared__ float s_acc[kBvtWarps][kAcc][32];  // [value][lane]
     __shared__ float4 s_shift[kBvtWarps][27];
     __shared__ float4 s_xi[kBvtWarps][4];  // (x, y, z, f q)
     __shared__ float4 s_gi[kBvtWarps][4];
     __shared__ int s_tr[kBvtWarps][4];     // LJ table row of each i row
+    __shared__ float4 s_xp[kBvtWarps][2][2];  // row pair k: (x_a, x_b, y_a, y_b), (z_a, z_b, fq_a, fq_b)
+    __shared__ float4 s_gp[kBvtWarps][2][2];  // row pair k: (gx_a, gx_b, gy_a, gy_b), (gz_a, gz_b, 0, 0)
     nb_pdl_wait();
     nb_pdl_release();
     const int nt2 = p.ntype * p.ntype;
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nhalf = 2u * (unsigned)p.st->nc;
-    const unsigned nwork = nhalf * (unsigned)p.nreg * (unsigned)p.nseg;
+    const unsigned nwork = nhalf * (unsigned)p.nreg;
     int shift_sys = -1;
     float(*acc)[32] = s_acc[warp];
 #pragma unroll
@@ -112,16 +116,11 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= nwork) break;
-        // work item w: range seg of the groups of half hw of region reg
-        const unsigned unit = w / (unsigned)p.nseg, seg = w - unit * (unsigned)p.nseg;
-        const unsigned reg = unit / nhalf, hw = unit - reg * nhalf;
+        const unsigned reg = w / nhalf, hw = w - reg * nhalf;
         const int ci = p.order ? p.order[hw >> 1] : (int)(hw >> 1);
         const int h = (int)(hw & 1u);
         const size_t hidx = (size_t)reg * p.reg_stride + 2 * ci + h;
-        const int th = p.half_start[hidx], nth = p.half_len[hidx];
-        const int gh = (nth + 3) >> 2;  // groups of the half
-        const int t0 = th + 4 * (int)(((long long)gh * seg) / p.nseg);
-        const int t1 = min(th + nth, th + 4 * (int)(((long long)gh * (seg + 1)) / p.nseg));
+        const int t0 = p.half_start[hidx], t1 = t0 + p.half_len[hidx];
         if (t1 <= t0) continue;
         const int csys = p.clus_sys[ci];
         if (csys != shift_sys) {
@@ -136,37 +135,67 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
             s_gi[warp][lane] = p.gsort[ibase + lane];
             s_tr[warp][lane] = p.tsort[ibase + lane] * p.ntype;
         }
-        float4 bi[4];
+        // rows (2k, 2k + 1) of the half in .x, .y of row pair k
+        float2 bix[2], biy[2], biz[2], biq[2];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) bi[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 2; ++k) bix[k] = biy[k] = biz[k] = biq[k] = make_float2(0.f, 0.f);
         const int ngroups = (t1 - t0 + 3) >> 2;
         cp_async_wait_all();
         __syncwarp();
+        if (lane < 2) {
+            const float4 a = s_xi[warp][2 * lane], b = s_xi[warp][2 * lane + 1];
+            s_xp[warp][lane][0] = make_float4(a.x, b.x, a.y, b.y);
+            s_xp[warp][lane][1] = make_float4(a.z, b.z, a.w, b.w);
+            const float4 ga = s_gi[warp][2 * lane], gb = s_gi[warp][2 * lane + 1];
+            s_gp[warp][lane][0] = make_float4(ga.x, gb.x, ga.y, gb.y);
+            s_gp[warp][lane][1] = make_float4(ga.z, gb.z, 0.0f, 0.0f);
+        }
+        float4 *s_ljp = s_lj + nt2 + 2 * p.ntype * warp;
+        for (int t = lane; t < p.ntype; t += 32) {
+            const float4 c0 = s_lj[s_tr[warp][0] + t], c1 = s_lj[s_tr[warp][1] + t];
+            const float4 c2 = s_lj[s_tr[warp][2] + t], c3 = s_lj[s_tr[warp][3] + t];
+            s_ljp[2 * t + 0] = make_float4(c0.x, c1.x, c0.y, c1.y);
+            s_ljp[2 * t + 1] = make_float4(c2.x, c3.x, c2.y, c3.y);
+        }
+        __syncwarp();
+        const float2 nk2 = nb_f2(-p.k2);
         for (int g = 0; g < ngroups; ++g) {
             const BvtStage &cs = s_st[warp][g & 1];
             const float4 xj = cs.xj[lane];
             const float4 gj = cs.gj[lane];
             const int tj = cs.tj[lane];
-            const unsigned mrow = cs.m[lane] >> (lane & 7);
+            const unsigned mrow = cs.m[lane] >> (lane & 7);  // bit 8a: row a
             const float4 S = s_shift[warp][(unsigned)v >> 27];
             const int slot = v & 0x07ffffff;
-            const float qj_f = xj.w * NB_COULOMB_F;
-            float4 bj = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float2 nxjx = nb_f2(-xj.x), nxjy = nb_f2(-xj.y), nxjz = nb_f2(-xj.z);
+            const float2 ngjx = nb_f2(-gj.x), ngjy = nb_f2(-gj.y), ngjz = nb_f2(-gj.z);
+            const float2 qj = nb_f2(xj.w), qj_f = nb_f2(xj.w * NB_COULOMB_F);
+            const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z);
+            float2 vjx = make_float2(0.f, 0.f), vjy = vjx, vjz = vjx, bjq = vjx;
             int vn = 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                if (a == 2)  // next group's copies overlap rows 2 and 3 (past the last group: pad copies)
+            for (int k = 0; k < 2; ++k) {
+                if (k == 1)  // next group's copies overlap row pair 1 (past the last group: pad copies)
                     vn = stage_adj(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
-                const float4 xi = s_xi[warp][a];
-                float d6, d12;
-                nb_pair_adj<true, COUL>(xi, xi.w, s_gi[warp][a], xj, qj_f, gj, s_lj[s_tr[warp][a] + tj], S.x, S.y, S.z,
-                                  ((mrow >> (8 * a)) & 1u) != 0u, p.cc, p.k2, bi[a], bj, d6, d12);
-                // the lane's own column: tj < ntype <= NT (the gather keeps types in range)
-                acc[(a * NT + tj) * 2 + 0][lane] += d6;
-                acc[(a * NT + tj) * 2 + 1][lane] += d12;
+                const float4 xa = s_xp[warp][k][0], xb = s_xp[warp][k][1];
+                const float4 ga = s_gp[warp][k][0], gb = s_gp[warp][k][1];
+                const float4 lj = s_ljp[2 * tj + k];
+                float2 d6, d12;
+                nb_pair_adj_x2<COUL>(make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xb.x, xb.y),
+                                     make_float2(xb.z, xb.w), make_float2(ga.x, ga.y), make_float2(ga.z, ga.w),
+                                     make_float2(gb.x, gb.y), nxjx, nxjy, nxjz, qj, qj_f, ngjx, ngjy, ngjz, Sx, Sy, Sz,
+                                     make_float2(lj.x, lj.y), make_float2(lj.z, lj.w),
+                                     ((mrow >> (16 * k)) & 1u) != 0u, ((mrow >> (16 * k + 8)) & 1u) != 0u, p.cc.rc2,
+                                     p.cc2, nk2, bix[k], biy[k], biz[k], biq[k], vjx, vjy, vjz, bjq, d6, d12);
+                // the lane's own columns: tj < ntype <= NT (the gather keeps types in range)
+                acc[((2 * k) * NT + tj) * 2 + 0][lane] += d6.x;
+                acc[((2 * k) * NT + tj) * 2 + 1][lane] += d12.x;
+                acc[((2 * k + 1) * NT + tj) * 2 + 0][lane] += d6.y;
+                acc[((2 * k + 1) * NT + tj) * 2 + 1][lane] += d12.y;
             }
             if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
-                atomicAdd(p.bsort + slot, bj);
+                atomicAdd(p.bsort + slot, make_float4(-(vjx.x + vjx.y), -(vjy.x + vjy.y), -(vjz.x + vjz.y),
+                                                      bjq.x + bjq.y));
             v = vn;
             cp_async_wait_all();
             __syncwarp();
@@ -176,11 +205,15 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
         {
             float r[16];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                r[4 * a + 0] = bi[a].x;
-                r[4 * a + 1] = bi[a].y;
-                r[4 * a + 2] = bi[a].z;
-                r[4 * a + 3] = bi[a].w;
+            for (int k = 0; k < 2; ++k) {
+                r[8 * k + 0] = bix[k].x;
+                r[8 * k + 1] = biy[k].x;
+                r[8 * k + 2] = biz[k].x;
+                r[8 * k + 3] = biq[k].x;
+                r[8 * k + 4] = bix[k].y;
+                r[8 * k + 5] = biy[k].y;
+                r[8 * k + 6] = biz[k].y;
+                r[8 * k + 7] = biq[k].y;
             }
             reduce_scatter<16>(r, lane);
             const float ry = __shfl_down_sync(0xffffffffu, r[0], 2);
@@ -209,17 +242,15 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
 
 template <int NT, int COUL>
 cudaError_t launch_bvt(nb_pairlist *pl, BvtParams p, cudaStream_t s) {
-    const size_t smem = sizeof(float4) * (size_t)p.ntype * p.ntype;
+    const size_t smem = sizeof(float4) * ((size_t)p.ntype * p.ntype + 2 * (size_t)p.ntype * kBvtWarps);
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_vt<NT, COUL>, kBvtThreads,
-                                                                      sizeof(float4) * 16);
+                                                                      sizeof(float4) * (16 + 8 * kBvtWarps));
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    // small systems: each half's groups split into up to 8 ranges (one work item each)
-    p.nseg = nb_work_split(pl->num_sms * per_sm * kBvtWarps, 2 * p.nreg * pl->nc_max);
-    const int blocks = min(pl->num_sms * per_sm, (2 * p.nreg * pl->nc_max * p.nseg + kBvtWarps - 1) / kBvtWarps);
+    const int blocks = min(pl->num_sms * per_sm, (2 * p.nreg * pl->nc_max + kBvtWarps - 1) / kBvtWarps);
     return nb_launch_pdl(k_backward_vt<NT, COUL>, max(blocks, 1), kBvtThreads, smem, s, p);
 }
 
@@ -244,6 +275,7 @@ cudaError_t nb_launch_backward_vt(nb_pairlist *pl, int ntype, const float *ljpar
     p.clus_sys = pl->clus_sys;
     p.ntype = ntype;
     const int coul = nb_fill_coul(p.cc, rc, beta, pl->coul_kind, pl->eps_rf, pl->coul_flags);
+    p.cc2 = nb_pack_coul(p.cc);
     p.k2 = (float)(2.0 * (2.0 * beta / 1.7724538509055159) * (double)beta * beta);
     p.stale_prune2 = stale_prune2;
     p.pad_slot = pl->nc_max * NB_CLUSTER;

@@ -138,7 +138,6 @@ struct ForceParams {
     int part;                        // NB_PART_*: ALL computes every pair
     const unsigned char *clus_home;  // with a part: bit b = slot b of the cluster holds a home atom
     int finalize;                    // move the displacement maxima of this evaluation to last_*
-    int nseg;                        // work items per i-cluster: its list split into nseg ranges
 };
 
 
@@ -200,13 +199,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
     int cur_sys = -1;
     unsigned cnt = 0;
 
-    const unsigned nwork = (unsigned)nc * (unsigned)p.nseg;
+    const unsigned nseg = nb_work_split(gridDim.x * kWarps, (unsigned)nc);
+    const unsigned nwork = (unsigned)nc * nseg;
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         // work item w: range seg of the list of the i-cluster at position idx of the order
-        const unsigned idx = w / (unsigned)p.nseg, seg = w - idx * (unsigned)p.nseg;
+        const unsigned idx = nseg == 1u ? w : w / nseg, seg = w - idx * nseg;
         const int ci = (w < nwork && p.order) ? p.order[idx] : (int)idx;
         const int csys = (w < nwork) ? p.clus_sys[ci] : -1;
         if (ENERGY && csys != cur_sys) {
@@ -217,9 +217,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
         }
         if (w >= nwork) break;
         const float4 *shift = p.sys_shift + 27 * csys;
-        const int kc = p.ci_start[ci], len = p.ci_len[ci];
-        const int k0 = kc + (int)(((long long)len * seg) / p.nseg);
-        const int k1 = kc + (int)(((long long)len * (seg + 1)) / p.nseg);
+        const int kc = p.ci_start[ci];
+        int r0, r1;
+        nb_piece(p.ci_len[ci], seg, nseg, r0, r1);
+        const int k0 = kc + r0, k1 = kc + r1;
         if (k1 <= k0) continue;
         const float4 xi1 = p.xq[ci * NB_CLUSTER + a1], xi2 = p.xq[ci * NB_CLUSTER + a2];
         const float qi1 = xi1.w * NB_COULOMB_F, qi2 = xi2.w * NB_COULOMB_F;
@@ -445,10 +446,8 @@ cudaError_t nb_launch_force(nb_pairlist *pl, int ntype, const float *ljparams, f
     }
     int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
     int blocks = pl->num_sms * use;
-    // A system with fewer i-clusters than the grid has warps would leave most SMs idle with
-    // one warp per cluster: its lists are then split into up to 8 ranges, one work item each.
-    p.nseg = nb_work_split(blocks * (threads / 32), pl->nc_max);
-    blocks = min(blocks, (pl->nc_max * p.nseg + threads / 32 - 1) / (threads / 32));
+    // no more blocks than work items: at most NB_MAX_SPLIT per i-cluster
+    blocks = min(blocks, (pl->nc_max * NB_MAX_SPLIT + threads / 32 - 1) / (threads / 32));
     blocks = max(blocks, 1);
     return nb_launch_pdl(fn, blocks, threads, smem, s, p);
 }

@@ -57,7 +57,6 @@ struct VtParams {
     int reg0, nreg;           // regions of gathered tiles to compute (0 local or all, 1 non-local)
     int reg_stride;           // 2 nc_max: halves per region in half_start / half_len
     int finalize;             // move the displacement maxima of this evaluation to last_*
-    int nseg;                 // work items per half: its groups of tiles split into nseg ranges
 };
 
 __device__ __forceinline__ void flush_energies_vt(double ec, double elj, int lane, double *out) {
@@ -144,7 +143,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     // shifts at [3t + 2]
     float4 *s_lj2 = s_lj + nt2 + 3 * p.ntype * warp;
     const unsigned nhalf = 2u * (unsigned)p.st->nc;  // halves per region
-    const unsigned nwork = nhalf * (unsigned)p.nreg * (unsigned)p.nseg;
+    const unsigned nwork = nhalf * (unsigned)p.nreg;
     double ecd = 0.0, eljd = 0.0;
     int cur_sys = -1;
     unsigned cnt = 0;
@@ -153,9 +152,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        // work item w: range seg of the groups of half hw of region reg
-        const unsigned unit = w / (unsigned)p.nseg, seg = w - unit * (unsigned)p.nseg;
-        const unsigned reg = w < nwork ? unit / nhalf : 0u, hw = unit - reg * nhalf;
+        const unsigned reg = w < nwork ? w / nhalf : 0u, hw = w - reg * nhalf;
         const int ci = (w < nwork && p.order) ? p.order[hw >> 1] : (int)(hw >> 1);
         const int h = (int)(hw & 1u);
         const int csys = (w < nwork) ? p.clus_sys[ci] : -1;
@@ -167,10 +164,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         }
         if (w >= nwork) break;
         const size_t hidx = (size_t)(p.reg0 + (int)reg) * p.reg_stride + 2 * ci + h;
-        const int th = p.half_start[hidx], nth = p.half_len[hidx];
-        const int gh = (nth + 3) >> 2;  // groups of the half
-        const int t0 = th + 4 * (int)(((long long)gh * seg) / p.nseg);
-        const int t1 = min(th + nth, th + 4 * (int)(((long long)gh * (seg + 1)) / p.nseg));
+        const int t0 = p.half_start[hidx], t1 = t0 + p.half_len[hidx];
         if (t1 <= t0) continue;
         if (csys != shift_sys) {
             if (lane < 27) s_shift[warp][lane] = p.sys_shift[27 * csys + lane];
@@ -334,8 +328,6 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     const int per_sm = occ.per_sm;
     const int use = pl->force_blocks_per_sm > 0 ? min(pl->force_blocks_per_sm, per_sm) : per_sm;
     int blocks = pl->num_sms * use;
-    // small systems: each half's groups split into up to 8 ranges (one work item each)
-    p.nseg = nb_work_split(blocks * (threads / 32), 2 * p.nreg * pl->nc_max);
-    blocks = min(blocks, (2 * p.nreg * pl->nc_max * p.nseg + threads / 32 - 1) / (threads / 32));
+    blocks = min(blocks, (2 * p.nreg * pl->nc_max + threads / 32 - 1) / (threads / 32));
     return nb_launch_pdl(fn, max(blocks, 1), threads, smem, s, p);
 }

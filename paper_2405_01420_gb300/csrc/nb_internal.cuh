@@ -170,12 +170,30 @@ int nb_record_error(int code, const char *msg);
 
 // ---------------------------------------------------------------------------
 // Work items per unit (an i-cluster or a half cluster) of the force and
-// adjoint kernels: 1 when there are at least as many units as the grid has
-// warps, else up to 8 so that a small system still reaches every SM.
-inline int nb_work_split(int grid_warps, int units) {
-    if (units <= 0) return 1;
-    const int k = grid_warps / units;
-    return k < 1 ? 1 : (k > 8 ? 8 : k);
+// adjoint kernels: 1 when the grid has no more warps than there are units,
+// else up to NB_MAX_SPLIT, so that a small system still reaches every SM
+// (each unit's list is then split into nseg ranges, one work item each).
+// Splitting larger systems to shorten the launch's tail costs more than it
+// saves: every piece repeats the row setup and the reductions. The kernels
+// take the unit count from the device (the clusters of the last search).
+#define NB_MAX_SPLIT 8
+__host__ __device__ inline unsigned nb_work_split(unsigned grid_warps, unsigned units) {
+    if (units == 0u) return 1u;
+    const unsigned k = grid_warps / units;
+    return k < 1u ? 1u : (k > NB_MAX_SPLIT ? NB_MAX_SPLIT : k);
+}
+
+// Range [r0, r1) of piece seg of nseg of a range of len items (32-bit; no
+// division when nseg is 1, the case of every system large enough to fill
+// the GPU).
+__device__ __forceinline__ void nb_piece(int len, unsigned seg, unsigned nseg, int &r0, int &r1) {
+    if (nseg == 1u) {
+        r0 = 0;
+        r1 = len;
+    } else {
+        r0 = (int)(((unsigned)len * seg) / nseg);
+        r1 = (int)(((unsigned)len * (seg + 1u)) / nseg);
+    }
 }
 
 // Programmatic dependent launch. A kernel launched with nb_launch_pdl may be

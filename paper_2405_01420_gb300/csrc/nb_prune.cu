@@ -46,7 +46,8 @@ struct PruneParams {
 };
 
 // Ring of staged j atoms per warp, half and part: it holds up to 31 atoms
-// left from full tiles plus one pass of kSub entries (8 atoms each).
+// left from full tiles plus one pass of kSub entries (8 atoms each); a chunk
+// whose atoms fit goes in one pass of all 32 entries.
 template <int NPART>
 struct Ring {
     static constexpr int kSub = NPART == 1 ? 16 : 8;
@@ -196,47 +197,71 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
                 loc_lo = hjw & rows_lo;
                 loc_hi = hjw & rows_hi;
             }
+            if (TILES) {
+                // In entry order (atoms of one entry stay together, so a tile draws on few
+                // clusters): an exclusive scan of the per-entry atom counts places each lane's
+                // atoms in its set's ring; once 32 atoms are staged, 4 full tiles leave together.
+                // The counts of two sets share one scan (16-bit fields; a set gains at most 256).
+                unsigned mhr[kSets], colr[kSets];
+                int cr[kSets], inclr[kSets], totr[kSets];
 #pragma unroll
-            for (int r = 0; r < (TILES ? kSets : 0); ++r) {
-                // in entry order (atoms of one entry stay together, so a tile
-                // draws on few clusters), kSub entries at a time: an exclusive
-                // scan of the per-entry counts places each lane's atoms; once
-                // 32 atoms are staged, 4 full tiles leave together
-                const int h = r & 1, part = r >> 1;
-                unsigned mh = lane < cnt ? (h ? mine.y : mine.x) : 0u;
-                if (NPART == 2) mh &= part ? ~(h ? loc_hi : loc_lo) : (h ? loc_hi : loc_lo);
-                const unsigned colh = (mh | (mh >> 8) | (mh >> 16) | (mh >> 24)) & 0xffu;
-                const unsigned sbase = (unsigned)(e.x * NB_CLUSTER) | ((unsigned)e.y << 27);
+                for (int r = 0; r < kSets; ++r) {
+                    const int h = r & 1, part = r >> 1;
+                    unsigned mh = lane < cnt ? (h ? mine.y : mine.x) : 0u;
+                    if (NPART == 2) mh &= part ? ~(h ? loc_hi : loc_lo) : (h ? loc_hi : loc_lo);
+                    mhr[r] = mh;
+                    colr[r] = (mh | (mh >> 8) | (mh >> 16) | (mh >> 24)) & 0xffu;
+                    cr[r] = __popc(colr[r]);
+                }
 #pragma unroll
-                for (int sp = 0; sp < 32 / kSub; ++sp) {
-                    const unsigned col = lane / kSub == sp ? colh : 0u;
-                    const int c = __popc(col);
-                    int incl = c;
+                for (int r = 0; r < kSets; r += 2) {
+                    int v = cr[r] | (cr[r + 1] << 16);
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
+                        const int u = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += u;
                     }
-                    const int total = __shfl_sync(0xffffffffu, incl, 31);
-                    if (total == 0) continue;
-                    const int pos0 = head[r] + fill[r] + incl - c;
+                    const int t = __shfl_sync(0xffffffffu, v, 31);
+                    inclr[r] = v & 0xffff;
+                    inclr[r + 1] = v >> 16;
+                    totr[r] = t & 0xffff;
+                    totr[r + 1] = t >> 16;
+                }
+                const unsigned sbase = (unsigned)(e.x * NB_CLUSTER) | ((unsigned)e.y << 27);
 #pragma unroll
-                    for (int bb = 0; bb < 8; ++bb) {
-                        if ((col >> bb) & 1u) {
-                            const int idx = (pos0 + __popc(col & ((1u << bb) - 1u))) & (kStage - 1);
-                            s_rslot[warp][r][idx] = (int)(sbase + (unsigned)bb);
-                            s_rmask[warp][r][idx] = mh;
+                for (int r = 0; r < kSets; ++r) {
+                    if (totr[r] == 0) continue;
+                    // one pass over all 32 entries while the ring has room (nearly always: fill
+                    // <= 31 and a chunk adds 8 atoms per entry at most, about 4.5 on water);
+                    // else kSub entries at a time, flushing in between
+                    const int ngroups = fill[r] + totr[r] <= kStage ? 1 : 32 / kSub;
+                    const int gsize = 32 / ngroups;
+                    for (int sp = 0; sp < ngroups; ++sp) {
+                        const int before = sp == 0 ? 0 : __shfl_sync(0xffffffffu, inclr[r], sp * gsize - 1);
+                        const int upto = __shfl_sync(0xffffffffu, inclr[r], sp * gsize + gsize - 1);
+                        if (lane / gsize == sp) {
+                            int k = head[r] + fill[r] + inclr[r] - cr[r] - before;
+                            const unsigned col = colr[r];
+#pragma unroll
+                            for (int bb = 0; bb < 8; ++bb) {
+                                if ((col >> bb) & 1u) {
+                                    const int idx = k & (kStage - 1);
+                                    s_rslot[warp][r][idx] = (int)(sbase + (unsigned)bb);
+                                    s_rmask[warp][r][idx] = mhr[r];
+                                    ++k;
+                                }
+                            }
                         }
-                    }
-                    fill[r] += total;
-                    __syncwarp();
-                    while (fill[r] >= 32) {
-                        flush_tiles<kStage>(s_rslot[warp][r], s_rmask[warp][r], head[r],
-                                            2 * NPART * k0 + r * n + ntile[r], 4, lane, p);
+                        fill[r] += upto - before;
                         __syncwarp();
-                        head[r] += 32;
-                        fill[r] -= 32;
-                        ntile[r] += 4;
+                        while (fill[r] >= 32) {
+                            flush_tiles<kStage>(s_rslot[warp][r], s_rmask[warp][r], head[r],
+                                                2 * NPART * k0 + r * n + ntile[r], 4, lane, p);
+                            __syncwarp();
+                            head[r] += 32;
+                            fill[r] -= 32;
+                            ntile[r] += 4;
+                        }
                     }
                 }
             }
