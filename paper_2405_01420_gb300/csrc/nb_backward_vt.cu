@@ -15,7 +15,8 @@
 //    to the unsymmetrised [ntype][ntype][2] accumulator. In registers they
 //    took 32 of them and held the kernel at 4 warps per scheduler.
 // Group g + 1's j data (coordinates and charge, g, type, mask word) are
-// copied into shared memory with cp.async while group g computes.
+// copied into shared memory with cp.async from the start of group g, their
+// slot words loaded one group earlier still.
 #include "nb_pair_x2.cuh"
 #include "nb_warp.cuh"
 
@@ -23,7 +24,7 @@ namespace {
 
 constexpr int kBvtThreads = 128;
 constexpr int kBvtWarps = kBvtThreads / 32;
-constexpr int kBvtCtasPerSm = 6;  // 85 registers per thread (80 used, no spills)
+constexpr int kBvtCtasPerSm = 5;  // 102 registers per thread (6 CTAs at 80 were slower: a longer tail)
 
 struct BvtParams {
     const float4 *xq;
@@ -57,21 +58,27 @@ struct BvtStage {
     unsigned m[32];
 };
 
-// Issues the copies of the lane's j atom in group g of the half with tiles
-// [t0, t1) (t0 < t1); returns its slot word. Past the end: the pad slot and
-// a zero-filled mask, with the loads reading tile t0 so that no lane branches.
-__device__ __forceinline__ int stage_adj(const BvtParams &p, BvtStage &st, int t0, int t1, int g, int lane) {
+// The lane's slot word of group g of the half with tiles [t0, t1): its j
+// atom's slot and shift, or the pad slot past the end (the load then reads
+// tile t0, so that no lane branches).
+__device__ __forceinline__ int slot_word_adj(const BvtParams &p, int t0, int t1, int g, int lane) {
     const int tile = t0 + 4 * g + (lane >> 3);
     const bool live = tile < t1;
     const int tc = live ? tile : t0;
     const int w = p.vt_slot[8 * (size_t)tc + (lane & 7)];
-    const int v = live ? w : (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-    cp_async4_zfill(&st.m[lane], p.vt_mask + tc, live ? 4u : 0u);
+    return live ? w : (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+}
+
+// Issues the copies of group g (slot word v) into st: the tile's mask word
+// (zero-filled past the end), the j atom's coordinates and charge, g, type.
+__device__ __forceinline__ void stage_adj(const BvtParams &p, BvtStage &st, int v, int t0, int t1, int g, int lane) {
+    const int tile = t0 + 4 * g + (lane >> 3);
+    const bool live = tile < t1;
+    cp_async4_zfill(&st.m[lane], p.vt_mask + (live ? tile : t0), live ? 4u : 0u);
     const int slot = v & 0x07ffffff;
     cp_async16(&st.xj[lane], p.xq + slot);
     cp_async16(&st.gj[lane], p.gsort + slot);
     cp_async4(&st.tj[lane], p.tsort + slot);
-    return v;
 }
 
 template <int NT, int COUL>
@@ -128,7 +135,9 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
             shift_sys = csys;
         }
         const int ibase = ci * NB_CLUSTER + 4 * h;
-        int v = stage_adj(p, s_st[warp][0], t0, t1, 0, lane);
+        int v = slot_word_adj(p, t0, t1, 0, lane);
+        stage_adj(p, s_st[warp][0], v, t0, t1, 0, lane);
+        int vnext = slot_word_adj(p, t0, t1, 1, lane);
         if (lane < 4) {
             const float4 x = p.xq[ibase + lane];
             s_xi[warp][lane] = make_float4(x.x, x.y, x.z, x.w * NB_COULOMB_F);
@@ -172,11 +181,12 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
             const float2 qj = nb_f2(xj.w), qj_f = nb_f2(xj.w * NB_COULOMB_F);
             const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z);
             float2 vjx = make_float2(0.f, 0.f), vjy = vjx, vjz = vjx, bjq = vjx;
-            int vn = 0;
+            // the next group's copies overlap this whole group, and the slot word after it is
+            // loaded a group ahead (past the last group: pad copies)
+            stage_adj(p, s_st[warp][(g + 1) & 1], vnext, t0, t1, g + 1, lane);
+            const int vafter = slot_word_adj(p, t0, t1, g + 2, lane);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (k == 1)  // next group's copies overlap row pair 1 (past the last group: pad copies)
-                    vn = stage_adj(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xa = s_xp[warp][k][0], xb = s_xp[warp][k][1];
                 const float4 ga = s_gp[warp][k][0], gb = s_gp[warp][k][1];
                 const float4 lj = s_ljp[2 * tj + k];
@@ -196,7 +206,8 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
             if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
                 atomicAdd(p.bsort + slot, make_float4(-(vjx.x + vjx.y), -(vjy.x + vjy.y), -(vjz.x + vjz.y),
                                                       bjq.x + bjq.y));
-            v = vn;
+            v = vnext;
+            vnext = vafter;
             cp_async_wait_all();
             __syncwarp();
         }

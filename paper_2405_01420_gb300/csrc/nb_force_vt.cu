@@ -19,7 +19,8 @@
 //    pairs, same rounding per pair as nb_pair). The kernel is bound by
 //    instruction issue, and packing halves the issue slots of the FP32 work.
 //  - j data (coordinates and charge, type, mask word) of group g + 1 are
-//    copied into shared memory with cp.async while group g computes; the
+//    copied into shared memory with cp.async from the start of group g
+//    (their slot words were loaded one group earlier still); the
 //    shift vectors come from a per-warp shared copy of the system's 27; the
 //    row pairs' positions and charges and their LJ coefficients by j type
 //    sit in per-warp shared tables, already in packed order.
@@ -77,22 +78,27 @@ struct VtStage {
     unsigned m[32];
 };
 
-// Issues the copies of group g of the half with tiles [t0, t1) (t0 < t1)
-// into st (one j atom per lane); returns the lane's slot word. Lanes past
-// the end take the pad slot (never occupied, q = 0) and a zero-filled mask;
-// their loads read tile t0 instead, so that no lane branches.
-__device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, int t0, int t1, int g,
-                                           int lane) {
+// The lane's slot word of group g of the half with tiles [t0, t1): its j
+// atom's slot and shift, or the pad slot past the end (the load then reads
+// tile t0, so that no lane branches).
+__device__ __forceinline__ int slot_word(const VtParams &p, int t0, int t1, int g, int lane) {
     const int tile = t0 + 4 * g + (lane >> 3);
     const bool live = tile < t1;
     const int tc = live ? tile : t0;
     const int w = p.vt_slot[8 * (size_t)tc + (lane & 7)];
-    const int v = live ? w : (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-    cp_async4_zfill(&st.m[lane], p.vt_mask + tc, live ? 4u : 0u);
+    return live ? w : (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
+}
+
+// Issues the copies of group g (slot word v) into st: the tile's mask word
+// (zero-filled past the end), the j atom's coordinates and charge, its type.
+__device__ __forceinline__ void stage_copies(const VtParams &p, VtStage &st, int v, int t0, int t1, int g,
+                                             int lane) {
+    const int tile = t0 + 4 * g + (lane >> 3);
+    const bool live = tile < t1;
+    cp_async4_zfill(&st.m[lane], p.vt_mask + (live ? tile : t0), live ? 4u : 0u);
     const int slot = v & 0x07ffffff;
     cp_async16(&st.xj[lane], p.xq + slot);
     cp_async4(&st.tj[lane], p.tsort + slot);
-    return v;
 }
 
 // j-stationary kernel over gathered tiles. A warp takes one half i-cluster
@@ -102,7 +108,8 @@ __device__ __forceinline__ int stage_group(const VtParams &p, VtStage &st, int t
 // and go out with one 16-byte vector atomic per lane (fsort is float4 per
 // slot); i forces stay in registers for the whole half and are reduced
 // across the warp at its end. Group g + 1 is copied (cp.async) into the
-// other buffer while group g is computed.
+// other buffer while group g is computed, and group g + 2's slot words load
+// meanwhile.
 // Dynamic shared memory: the ntype x ntype LJ table, then per warp 3 float4
 // per j type (see s_lj2).
 // 768 / THREADS resident CTAs per SM leave 80 registers per thread: the 4
@@ -171,7 +178,9 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             shift_sys = csys;
         }
         const int ibase = ci * NB_CLUSTER + 4 * h;
-        int v = stage_group(p, s_st[warp][0], t0, t1, 0, lane);
+        int v = slot_word(p, t0, t1, 0, lane);
+        stage_copies(p, s_st[warp][0], v, t0, t1, 0, lane);
+        int vnext = slot_word(p, t0, t1, 1, lane);
         if (lane < 4) {
             const float4 x = p.xq[ibase + lane];
             s_xi[warp][lane] = make_float4(x.x, x.y, x.z, x.w * NB_COULOMB_F);
@@ -208,11 +217,12 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z);
             const float4 nsh = s_lj2[3 * tj + 2];
             float2 gjx = make_float2(0.f, 0.f), gjy = gjx, gjz = gjx;
-            int vn = 0;
+            // the next group's copies overlap this whole group, and the slot word after it is
+            // loaded a group ahead (past the last group: pad copies)
+            stage_copies(p, s_st[warp][(g + 1) & 1], vnext, t0, t1, g + 1, lane);
+            const int vafter = slot_word(p, t0, t1, g + 2, lane);
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (k == 1)  // next group's copies overlap rows 2 and 3 (past the last group: pad copies)
-                    vn = stage_group(p, s_st[warp][(g + 1) & 1], t0, t1, g + 1, lane);
                 const float4 xa = s_xp[warp][k][0], xb = s_xp[warp][k][1];
                 const int c2 = nb_pair_x2<ENERGY, COUL>(
                     make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xb.x, xb.y),
@@ -225,7 +235,8 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
             if (slot != p.pad_slot)  // all padding lanes share one slot: no atomics there
                 atomicAdd(reinterpret_cast<float4 *>(p.fsort) + slot,
                           make_float4(-(gjx.x + gjx.y), -(gjy.x + gjy.y), -(gjz.x + gjz.y), 0.0f));
-            v = vn;
+            v = vnext;
+            vnext = vafter;
             cp_async_wait_all();
             __syncwarp();
         }
