@@ -118,10 +118,15 @@ __global__ void __launch_bounds__(kBvtThreads, kBvtCtasPerSm) k_backward_vt(BvtP
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k][lane] = 0.0f;
 
-    for (;;) {
-        unsigned w = 0;
-        if (lane == 0) w = atomicAdd(&p.st->work, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
+    const unsigned nwarps = gridDim.x * kBvtWarps;
+    for (unsigned it = 0;; ++it) {
+        // a warp's first work item is its own index in the grid, later ones come from the counter
+        unsigned w = blockIdx.x * kBvtWarps + warp;
+        if (it > 0) {
+            unsigned a = 0;
+            if (lane == 0) a = atomicAdd(&p.st->work, 1u);
+            w = __shfl_sync(0xffffffffu, a, 0) + nwarps;
+        }
         if (w >= nwork) break;
         const unsigned reg = w / nhalf, hw = w - reg * nhalf;
         const int ci = p.order ? p.order[hw >> 1] : (int)(hw >> 1);

@@ -8,8 +8,8 @@
 //            displacement since the search and since the last prune. The
 //            prune's gather (snapshot) records the positions of the prune
 //            and clears the list-length histogram the prune fills.
-// k_force    persistent grid, one warp per i-cluster taken from a work
-//            counter. List entries and their j-cluster data are staged in
+// k_force    persistent grid, one warp per i-cluster (each warp's first
+//            from its grid index, later ones from a work counter). List entries and their j-cluster data are staged in
 //            shared memory 16 at a time. Lane l owns j-atom b = l & 7 and i-atoms l >> 3 and
 //            (l >> 3) + 4, i.e. exactly mask bits l (low word) and 32 + l
 //            (high word). i-forces stay in registers for the whole list of
@@ -201,10 +201,16 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_force(ForceParams p
 
     const unsigned nseg = nb_work_split(gridDim.x * kWarps, (unsigned)nc);
     const unsigned nwork = (unsigned)nc * nseg;
-    for (;;) {
-        unsigned w = 0;
-        if (lane == 0) w = atomicAdd(&p.st->work, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
+    const unsigned nwarps = gridDim.x * kWarps;
+    for (unsigned it = 0;; ++it) {
+        // a warp's first work item is its own index in the grid, later ones come from the
+        // counter: thousands of warps do not start on one contended atomic
+        unsigned w = blockIdx.x * kWarps + warp;
+        if (it > 0) {
+            unsigned a = 0;
+            if (lane == 0) a = atomicAdd(&p.st->work, 1u);
+            w = __shfl_sync(0xffffffffu, a, 0) + nwarps;
+        }
         // work item w: range seg of the list of the i-cluster at position idx of the order
         const unsigned idx = nseg == 1u ? w : w / nseg, seg = w - idx * nseg;
         const int ci = (w < nwork && p.order) ? p.order[idx] : (int)idx;

@@ -138,10 +138,15 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lanebit = 1u << lane;
     const int nc = p.st->nc;
-    for (;;) {
-        unsigned w = 0;
-        if (lane == 0) w = atomicAdd(&p.st->work_prune, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
+    const unsigned nwarps = gridDim.x * kPruneWarps;
+    for (unsigned it = 0;; ++it) {
+        // a warp's first i-cluster is its own index in the grid, later ones come from the counter
+        unsigned w = blockIdx.x * kPruneWarps + warp;
+        if (it > 0) {
+            unsigned a = 0;
+            if (lane == 0) a = atomicAdd(&p.st->work_prune, 1u);
+            w = __shfl_sync(0xffffffffu, a, 0) + nwarps;
+        }
         if (w >= (unsigned)nc) break;
         const int ci = (int)w;
         const float4 *shift = p.sys_shift + 27 * p.clus_sys[ci];
