@@ -247,14 +247,28 @@ int pme_check(const char *who, int n, const float *coords, const float *q, const
 }
 
 // One wave of resident blocks (the kernels stride over the atoms), or fewer
-// for a small system.
-int pme_blocks(int n, const void *kernel) {
-    int dev = 0, sms = 152, per_sm = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+// for a small system. The SM count and the kernel's occupancy are looked up
+// once per device and kernel (kind 0 spread, 1 gather).
+constexpr int kMaxDevices = 64;
+int g_pme_sms[kMaxDevices] = {};
+int g_pme_per_sm[kMaxDevices][2] = {};
+
+int pme_blocks(int n, const void *kernel, int kind) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    if (g_pme_sms[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        g_pme_sms[dev] = sms;
+    }
+    if (g_pme_per_sm[dev][kind] == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        g_pme_per_sm[dev][kind] = per_sm;
+    }
     const long long want = ((long long)n * kLanesPerAtom + kThreads - 1) / kThreads;
-    return (int)std::max(1LL, std::min(want, (long long)sms * per_sm));
+    return (int)std::max(1LL, std::min(want, (long long)g_pme_sms[dev] * g_pme_per_sm[dev][kind]));
 }
 
 }  // namespace
@@ -269,7 +283,7 @@ extern "C" int nb_pme_spread(int n_atoms, const float *coords, const float *q, c
     const size_t cells = (size_t)K0 * K1 * K2;
     cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(float) * cells, s);
     if (e == cudaSuccess && n_atoms > 0) {
-        k_pme_spread<<<pme_blocks(n_atoms, (const void *)k_pme_spread), kThreads, 0, s>>>(n_atoms, coords, q, ax, grid);
+        k_pme_spread<<<pme_blocks(n_atoms, (const void *)k_pme_spread, 0), kThreads, 0, s>>>(n_atoms, coords, q, ax, grid);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nb_record_error(NB_ERR_CUDA, cudaGetErrorString(e));
@@ -287,7 +301,7 @@ extern "C" int nb_pme_gather(int n_atoms, const float *coords, const float *q, c
     cudaError_t e = cudaSuccess;
     if (energy) e = cudaMemsetAsync(energy, 0, sizeof(double), s);
     if (e == cudaSuccess && n_atoms > 0) {
-        k_pme_gather<<<pme_blocks(n_atoms, (const void *)k_pme_gather), kThreads, 0, s>>>(
+        k_pme_gather<<<pme_blocks(n_atoms, (const void *)k_pme_gather, 1), kThreads, 0, s>>>(
             n_atoms, coords, q, ax, phi, forces, accumulate ? 1 : 0, energy);
         e = cudaGetLastError();
     }
