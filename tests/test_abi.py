@@ -199,3 +199,19 @@ def test_pme_argument_checks_run_on_the_host(lib):
     assert spread(x=None) == nb.NB_ERR_ARG
     assert gather(phi=None) == nb.NB_ERR_ARG
     assert gather(forces=None) == nb.NB_ERR_ARG
+
+
+def test_peak_probe_argument_checks_run_on_the_host(lib):
+    """nb_fp32_peak_probe rejects NULL pointers and bad launch sizes before any CUDA call."""
+    from paper_2405_01420_gb300 import nb
+    f = lib.nb_fp32_peak_probe
+    f.restype, f.argtypes = nb.SIGNATURES["nb_fp32_peak_probe"]
+    lib.nb_last_error.restype = ctypes.c_char_p
+    flops = ctypes.c_double(0.0)
+    dummy = ctypes.c_void_p(16)  # never dereferenced
+    assert f(1, 8, 16, None, 1 << 20, ctypes.byref(flops), None) == nb.NB_ERR_ARG
+    assert f(1, 8, 16, dummy, 1 << 20, None, None) == nb.NB_ERR_ARG
+    assert f(1, 0, 16, dummy, 1 << 20, ctypes.byref(flops), None) == nb.NB_ERR_ARG
+    assert f(1, 9, 16, dummy, 1 << 20, ctypes.byref(flops), None) == nb.NB_ERR_ARG
+    assert f(1, 8, 0, dummy, 1 << 20, ctypes.byref(flops), None) == nb.NB_ERR_ARG
+    assert lib.nb_last_error().decode().startswith("nb_fp32_peak_probe")
