@@ -1058,9 +1058,23 @@ def run_ours(args, rank, world, local):
             ts.append(1e3 * a.elapsed_time(b))
         return statistics.median(ts)
 
+    # the same force call without energies (what an MD step that does not report energies runs):
+    # the force kernel alone, events around it on 20 calls
+    ev_f = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e_ in ev_f:
+        e_.record(stream)
+    nb.nb_set_timing_events(eng.pl.handle, *ev_f)
+    f_only = []
+    for _ in range(20):
+        nb.nb_forces(eng.pl.handle, x_last, q, typ, lj, RC, beta, forces, None)
+        torch.cuda.synchronize()
+        f_only.append(ev_f[0].elapsed_time(ev_f[1]))
+    nb.nb_set_timing_events(eng.pl.handle, None, None)
+    forces_only_us = 1e3 * statistics.median(f_only)
     search_us = _call_us(lambda: eng.pl.search(x_last, box.box, RLIST, eo, ei))
     prune_us = _call_us(lambda: eng.pl.prune(x_last, R_INNER))
     list_side = {"search_us_per_call": search_us, "prune_us_per_call": prune_us,
+                 "force_kernel_no_energy_us": forces_only_us,
                  "list_us_per_eval": (search_us * searches + prune_us * prunes) / args.evals,
                  "pair_slots_per_eval": slots, "slot_efficiency": pairs_per_eval / slots if slots else None}
     assert eng.check() == 0
