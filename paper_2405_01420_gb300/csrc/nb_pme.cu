@@ -105,14 +105,16 @@ __global__ void __launch_bounds__(kThreads) k_pme_spread(int n, const float *__r
                                                          const float *__restrict__ q, pme_axes ax,
                                                          float *__restrict__ grid) {
     const int c = threadIdx.x & (kLanesPerAtom - 1);
-    const int stride = gridDim.x * (kThreads / kLanesPerAtom);
-    for (int i = blockIdx.x * (kThreads / kLanesPerAtom) + (threadIdx.x >> 2); i < n; i += stride) {
+    // unsigned: n < 2^31 and the stride is below 2^17, so i + stride never wraps
+    const unsigned stride = gridDim.x * (kThreads / kLanesPerAtom);
+    for (unsigned i = blockIdx.x * (kThreads / kLanesPerAtom) + (threadIdx.x >> 2); i < (unsigned)n; i += stride) {
         const float qi = __ldg(q + i);
+        const float *xi = coords + 3 * (size_t)i;
         float w[3];
         int base[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            pme_scaled(__ldg(coords + 3 * i + a), ax.s_hi[a], ax.s_lo[a], ax.Kf[a], ax.invK[a], ax.K[a], w[a],
+            pme_scaled(__ldg(xi + a), ax.s_hi[a], ax.s_lo[a], ax.Kf[a], ax.invK[a], ax.K[a], w[a],
                        base[a]);
         float mx[4], my[4], mz[4];
         pme_w4(w[0], mx);
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_pme_gather(int n, const float *__r
                                                          const float *__restrict__ phi, float *__restrict__ forces,
                                                          int accumulate, double *__restrict__ energy) {
     const int c = threadIdx.x & (kLanesPerAtom - 1);
-    const int stride = gridDim.x * (kThreads / kLanesPerAtom);
+    const long long stride = (long long)gridDim.x * (kThreads / kLanesPerAtom);
     double e_acc = 0.0;
     // every lane group runs the same number of iterations, so the shuffles below see all 32 lanes
     const long long n_round = ((long long)n + stride - 1) / stride * stride;
