@@ -254,3 +254,36 @@ def test_pme_argument_errors(nb):
         nb.nb_pme_spread(xd, qd, box, (3, 16, 16), torch.empty(3 * 16 * 16, device="cuda"))
     with pytest.raises(ValueError):
         nb.nb_pme_spread(xd, qd, box, (16, 16, 17), grid)  # grid of the wrong size
+
+
+def test_pme_million_atoms(nb):
+    """1,000,002 atoms on a 180^3 mesh: the spread conserves the charge and is the
+    gather's adjoint (sum Q phi = 2 E over the GPU's own outputs), and the gathered
+    forces of 3,000 sampled atoms match the oracle (the gather is per atom, so the
+    oracle needs only those atoms)."""
+    b = synth.water_box(333334, 3)
+    K = mesh_for(b.box)
+    assert K == (180, 180, 180)
+    x = torch.from_numpy(b.coords).cuda()
+    q = torch.from_numpy(b.q).cuda()
+    grid = torch.empty(K, dtype=torch.float32, device="cuda")
+    nb.nb_pme_spread(x, q, b.box, K, grid)
+    Q = grid.double()
+    qsum = float(np.abs(b.q.astype(np.float64)).sum())
+    assert abs(float(Q.sum()) - float(b.q.astype(np.float64).sum())) <= 1e-6 * qsum
+    phi = torch.randn(K, generator=torch.Generator(device="cuda").manual_seed(3), device="cuda")
+    F = torch.empty((b.n_atoms, 3), dtype=torch.float32, device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    nb.nb_pme_gather(x, q, b.box, K, phi, F, energy=E)
+    torch.cuda.synchronize()
+    qphi = float((Q * phi.double()).sum())
+    # both sides sum 64 M terms of size ~|q| |phi|; FP32 weights and atomics: 1e-5 of sum |q| |phi|
+    scale = float((torch.from_numpy(np.abs(b.q)).cuda().double().sum()) * phi.abs().max().double())
+    assert abs(2.0 * float(E.item()) - qphi) <= 1e-5 * scale
+    rng = np.random.default_rng(6)
+    atoms = np.sort(rng.choice(b.n_atoms, 3000, replace=False))
+    phi_h = phi.cpu().numpy().astype(np.float32)
+    Fo, _, Fa = oracle.pme_gather(b.coords[atoms], b.q[atoms], b.box, K, phi_h, 4, abs_sums=True)
+    tol = gather_tol(b.coords[atoms], b.q[atoms], b.box, K, phi_h, Fa)
+    Fg = F.cpu().numpy()[atoms].astype(np.float64)
+    assert (np.abs(Fg - Fo) <= tol).all(), np.max(np.abs(Fg - Fo) - tol)
