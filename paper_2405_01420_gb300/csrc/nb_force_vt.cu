@@ -28,8 +28,10 @@
 //    16-byte vector atomic per lane (fsort is float4 per slot).
 //  - i forces stay in registers over the whole half and are reduced across
 //    the warp at its end, one vector atomic per row.
-//  - Energies: FP32 per lane over a half, FP64 across halves, FP64 atomics
-//    per system when the warp moves to another system or finishes.
+//  - Energies: FP32 over a half (per lane, then across the warp), FP64
+//    across halves in a per-warp shared pair (no registers held across
+//    halves), FP64 atomics per system when the warp moves to another
+//    system or finishes.
 //  - Every half comes from the work counter, the first too: taking each
 //    warp's first half from its grid index instead was 1 us slower at
 //    96,000 atoms (the counter spreads the largest halves over the SMs as
@@ -64,15 +66,13 @@ struct VtParams {
     int finalize;             // move the displacement maxima of this evaluation to last_*
 };
 
-__device__ __forceinline__ void flush_energies_vt(double ec, double elj, int lane, double *out) {
-    for (int o = 16; o > 0; o >>= 1) {
-        ec += __shfl_xor_sync(0xffffffffu, ec, o);
-        elj += __shfl_xor_sync(0xffffffffu, elj, o);
-    }
-    if (lane == 0 && out) {
-        atomicAdd(&out[0], elj);
-        atomicAdd(&out[1], ec);
-    }
+// Adds a warp's energies of one system (Coulomb in e[0], LJ in e[1]) to
+// that system's pair (E_LJ, E_C) and clears them; lane 0 only.
+__device__ __forceinline__ void flush_energies_vt(double *e, double *out) {
+    atomicAdd(&out[0], e[1]);
+    atomicAdd(&out[1], e[0]);
+    e[0] = 0.0;
+    e[1] = 0.0;
 }
 
 // Per-lane staging of one group of 32 gathered j atoms (4 tiles of 8).
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     __shared__ float4 s_xi[kWarps][4];
     __shared__ int s_tr[kWarps][4];
     __shared__ float4 s_xp[kWarps][2][2];  // row pair k: (x_a, x_b, y_a, y_b), (z_a, z_b, fq_a, fq_b)
+    __shared__ double s_e[kWarps][2];      // the warp's energies of its current system: Coulomb, LJ
     nb_pdl_wait();  // launched with nb_launch_pdl: the gather has completed from here on
     nb_pdl_release();
     const int nt2 = p.ntype * p.ntype;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
     float4 *s_lj2 = s_lj + nt2 + 3 * p.ntype * warp;
     const unsigned nhalf = 2u * (unsigned)p.st->nc;  // halves per region
     const unsigned nwork = nhalf * (unsigned)p.nreg;
-    double ecd = 0.0, eljd = 0.0;
+    if (ENERGY && lane == 0) s_e[warp][0] = s_e[warp][1] = 0.0;
     int cur_sys = -1;
     unsigned cnt = 0;
 
@@ -168,9 +169,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         const int h = (int)(hw & 1u);
         const int csys = (w < nwork) ? p.clus_sys[ci] : -1;
         if (ENERGY && csys != cur_sys) {
-            if (cur_sys >= 0) flush_energies_vt(ecd, eljd, lane, p.energies + 2 * cur_sys);
-            ecd = 0.0;
-            eljd = 0.0;
+            if (cur_sys >= 0 && lane == 0) flush_energies_vt(s_e[warp], p.energies + 2 * cur_sys);
             cur_sys = csys;
         }
         if (w >= nwork) break;
@@ -264,8 +263,16 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p)
         if ((lane & 7) == 0)
             atomicAdd(reinterpret_cast<float4 *>(p.fsort) + ibase + (lane >> 3), make_float4(r[0], ry, rz, 0.0f));
         if (ENERGY) {
-            ecd += (double)(ec2.x + ec2.y);
-            eljd += (double)(elj2.x + elj2.y);
+            float ec = ec2.x + ec2.y, el = elj2.x + elj2.y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ec += __shfl_xor_sync(0xffffffffu, ec, o);
+                el += __shfl_xor_sync(0xffffffffu, el, o);
+            }
+            if (lane == 0) {
+                s_e[warp][0] += (double)ec;
+                s_e[warp][1] += (double)el;
+            }
         }
         __syncwarp();
     }

@@ -56,18 +56,18 @@ struct Ring {
 };
 
 // Writes ntiles (<= 4) gathered tiles from the 8 ntiles staged atoms at ring
-// position head: lane l takes atom l, i.e. column p = l & 7 of tile l >> 3.
+// position head (each a (slot word, mask word) pair): lane l takes atom l, i.e. column p = l & 7 of tile l >> 3.
 // Each staged atom keeps its entry's 4 x 8 mask word of the half; its column
 // b in that word is the low 3 bits of its slot, so its rows (bits b, 8 + b,
 // 16 + b, 24 + b) shifted to column p are its part of the tile's mask, and
 // the 8 lanes of a tile OR theirs together.
 template <int STAGE>
-__device__ __forceinline__ void flush_tiles(const int *ring_slot, const unsigned *ring_mask, int head, int vt,
-                                            int ntiles, int lane, const PruneParams &p) {
-    const int idx = (head + lane) & (STAGE - 1);
-    const int v = ring_slot[idx];
+__device__ __forceinline__ void flush_tiles(const uint2 *ring, int head, int vt, int ntiles, int lane,
+                                            const PruneParams &p) {
+    const uint2 a = ring[(head + lane) & (STAGE - 1)];  // (slot word, mask word)
+    const int v = (int)a.x;
     const int pcol = lane & 7, t = lane >> 3;
-    unsigned c = ((ring_mask[idx] >> ((unsigned)v & 7u)) & 0x01010101u) << pcol;
+    unsigned c = ((a.y >> (a.x & 7u)) & 0x01010101u) << pcol;
     c |= __shfl_xor_sync(0xffffffffu, c, 1);
     c |= __shfl_xor_sync(0xffffffffu, c, 2);
     c |= __shfl_xor_sync(0xffffffffu, c, 4);
@@ -85,7 +85,10 @@ __device__ __forceinline__ void flush_tiles(const int *ring_slot, const unsigned
 // distinct finite floats rounds to a nonzero value of its sign (subnormals
 // are kept), and equal values give +0. So one packed subtraction decides two
 // pairs, and a funnel shift moves each sign bit into the row's mask byte; j
-// atoms are taken from 7 down to 0 so that atom b ends at bit b.
+// atoms are taken from 7 down to 0 so that atom b ends at bit b. Without
+// SHIFT (every entry of the chunk at the center image) the addition of
+// S = 0 is left out: it changes no difference but the sign of a zero.
+template <bool SHIFT>
 __device__ __forceinline__ uint2 test_entry(const int4 e, const float2 (&rx)[4], const float2 (&ry)[4],
                                             const float2 (&rz)[4], const float4 *xj, const float4 S, float r2cut) {
     const float2 Sx = nb_f2(S.x), Sy = nb_f2(S.y), Sz = nb_f2(S.z), nr2cut = nb_f2(-r2cut);
@@ -96,9 +99,12 @@ __device__ __forceinline__ uint2 test_entry(const int4 e, const float2 (&rx)[4],
         const float2 nx = nb_f2(-x.x), ny = nb_f2(-x.y), nz = nb_f2(-x.z);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float2 dx = __fadd2_rn(__fadd2_rn(rx[k], nx), Sx);
-            const float2 dy = __fadd2_rn(__fadd2_rn(ry[k], ny), Sy);
-            const float2 dz = __fadd2_rn(__fadd2_rn(rz[k], nz), Sz);
+            float2 dx = __fadd2_rn(rx[k], nx), dy = __fadd2_rn(ry[k], ny), dz = __fadd2_rn(rz[k], nz);
+            if (SHIFT) {
+                dx = __fadd2_rn(dx, Sx);
+                dy = __fadd2_rn(dy, Sy);
+                dz = __fadd2_rn(dz, Sz);
+            }
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const float2 t = __fadd2_rn(r2, nr2cut);
             ma[k] = __funnelshift_l(__float_as_uint(t.x), ma[k], 1);
@@ -122,8 +128,7 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
     // the j clusters of a chunk's entries; one float4 of padding per entry keeps the lanes'
     // 16-byte reads of one atom index free of bank conflicts
     __shared__ float4 s_xj[kPruneWarps][32][NB_CLUSTER + 1];
-    __shared__ int s_rslot[kPruneWarps][kSets][kStage];
-    __shared__ unsigned s_rmask[kPruneWarps][kSets][kStage];
+    __shared__ uint2 s_ring[kPruneWarps][kSets][kStage];  // staged atoms: (slot word, entry's mask word)
     nb_pdl_wait();  // launched with nb_launch_pdl: the prune's gather has completed from here on
     nb_pdl_release();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -189,7 +194,11 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
             cp_async_wait_all();
             __syncwarp();
             uint2 mine = make_uint2(0u, 0u);
-            if (lane < cnt) mine = test_entry(e, rx, ry, rz, s_xj[warp][lane], shift[e.y], p.r2cut);
+            if (__any_sync(0xffffffffu, e.y != NB_SHIFT_CENTER)) {
+                if (lane < cnt) mine = test_entry<true>(e, rx, ry, rz, s_xj[warp][lane], shift[e.y], p.r2cut);
+            } else if (lane < cnt) {
+                mine = test_entry<false>(e, rx, ry, rz, s_xj[warp][lane], make_float4(0.f, 0.f, 0.f, 0.f), p.r2cut);
+            }
             const bool keep = lane < cnt && (mine.x | mine.y) != 0u;
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             if (keep)
@@ -250,9 +259,7 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
 #pragma unroll
                             for (int bb = 0; bb < 8; ++bb) {
                                 if ((col >> bb) & 1u) {
-                                    const int idx = k & (kStage - 1);
-                                    s_rslot[warp][r][idx] = (int)(sbase + (unsigned)bb);
-                                    s_rmask[warp][r][idx] = mhr[r];
+                                    s_ring[warp][r][k & (kStage - 1)] = make_uint2(sbase + (unsigned)bb, mhr[r]);
                                     ++k;
                                 }
                             }
@@ -260,8 +267,8 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
                         fill[r] += upto - before;
                         __syncwarp();
                         while (fill[r] >= 32) {
-                            flush_tiles<kStage>(s_rslot[warp][r], s_rmask[warp][r], head[r],
-                                                2 * NPART * k0 + r * n + ntile[r], 4, lane, p);
+                            flush_tiles<kStage>(s_ring[warp][r], head[r], 2 * NPART * k0 + r * n + ntile[r], 4,
+                                                lane, p);
                             __syncwarp();
                             head[r] += 32;
                             fill[r] -= 32;
@@ -278,13 +285,11 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
             if (fill[r] > 0) {
                 const int nt = (fill[r] + 7) >> 3;
                 if (lane >= fill[r] && lane < 8 * nt) {
-                    const int idx = (head[r] + lane) & (kStage - 1);
-                    s_rslot[warp][r][idx] = (int)((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27));
-                    s_rmask[warp][r][idx] = 0u;
+                    s_ring[warp][r][(head[r] + lane) & (kStage - 1)] =
+                        make_uint2((unsigned)p.pad_slot | ((unsigned)NB_SHIFT_CENTER << 27), 0u);
                 }
                 __syncwarp();
-                flush_tiles<kStage>(s_rslot[warp][r], s_rmask[warp][r], head[r], 2 * NPART * k0 + r * n + ntile[r], nt,
-                                    lane, p);
+                flush_tiles<kStage>(s_ring[warp][r], head[r], 2 * NPART * k0 + r * n + ntile[r], nt, lane, p);
                 ntile[r] += nt;
             }
             if (lane == 0) {
