@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kBvtThreads = 128;
 constexpr int kBvtWarps = kBvtThreads / 32;
-constexpr int kBvtCtasPerSm = 5;  // 102 registers per thread (6 CTAs at 80 were slower: a longer tail)
+constexpr int kBvtCtasPerSm = 4;  // up to 128 registers (115 used); 5 CTAs at 102 were 1.3 us slower at 24k atoms, 6 at 80 slower still
 
 struct BvtParams {
     const float4 *xq;

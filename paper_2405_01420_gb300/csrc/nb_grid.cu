@@ -4,10 +4,10 @@
 //    count atoms per column.
 // 2. k_col_scan: exclusive scans of atoms and of 8-atom clusters per column.
 // 3. k_col_scatter: bucket (z, atom) keys by column.
-// 4. k_col_sort: one CTA per column sorts its keys by z (bitonic, shared
-//    memory), packs runs of 8 into clusters, pads the last one, and writes
-//    the slot <-> atom maps, the search-frame positions and per-cluster
-//    bounding boxes.
+// 4. k_col_sort: sorts each column's keys by z (bitonic: in one warp's
+//    registers up to 256 atoms, else by a CTA in shared memory), packs runs
+//    of 8 into clusters, pads the last one, and writes the slot <-> atom
+//    maps, the search-frame positions and per-cluster bounding boxes.
 //
 // Layout in HBM after the sort (slot = 8 * cluster + lane):
 //   perm[slot] (int), xref[slot] (float4), bbox[2c], bbox[2c+1] (float4).
@@ -136,47 +136,82 @@ __global__ void k_col_scatter(int n, const float4 *__restrict__ xw, const int *_
     keys[col_atom_start[atom_col[i]] + atom_slot[i]] = k;
 }
 
-// One CTA per column. Shared memory: NB_MAX_COL_ATOMS keys.
-__global__ void __launch_bounds__(256) k_col_sort(
-    const int *__restrict__ col_count, const int *__restrict__ col_atom_start,
-    const int *__restrict__ col_clus_start, const unsigned long long *__restrict__ keys,
-    const float4 *__restrict__ xw, const int *__restrict__ col_sys, int *__restrict__ perm,
-    int *__restrict__ pos, float4 *__restrict__ xref, float4 *__restrict__ xprune, float4 *__restrict__ xq,
-    int *__restrict__ tsort, float4 *__restrict__ bbox, int *__restrict__ clus_sys, const nb_sys *__restrict__ sys,
-    int *__restrict__ ztab) {
-    __shared__ unsigned long long sk[NB_MAX_COL_ATOMS];
-    int col = blockIdx.x;
-    int cnt = min(col_count[col], NB_MAX_COL_ATOMS);  // overflow already flagged by the scan
-    int a0 = col_atom_start[col];
-    int p2 = 1;
-    while (p2 < cnt) p2 <<= 1;
-    for (int k = threadIdx.x; k < p2; k += blockDim.x) sk[k] = (k < cnt) ? keys[a0 + k] : ~0ull;
-    __syncthreads();
-    for (int size = 2; size <= p2; size <<= 1) {
+struct ColSortParams {
+    const int *col_count;
+    const int *col_atom_start;
+    const int *col_clus_start;
+    const unsigned long long *keys;
+    const float4 *xw;
+    const int *col_sys;
+    int *perm;
+    int *pos;
+    float4 *xref;
+    float4 *xprune;
+    float4 *xq;
+    int *tsort;
+    float4 *bbox;
+    int *clus_sys;
+    const nb_sys *sys;
+    int *ztab;
+    int ncol;
+    int cpc;  // columns per CTA, 1 .. kSortWarps: warp w < cpc takes column cpc * blockIdx.x + w
+};
+
+constexpr int kSortWarps = 8;       // columns per CTA, one per warp
+constexpr int kWarpSortKeys = 256;  // a column up to this size is sorted in one warp's registers
+
+// Compare-exchange: a <= b afterwards if up, a >= b otherwise.
+__device__ __forceinline__ void cmpx(unsigned long long &a, unsigned long long &b, bool up) {
+    const bool swap = (a > b) == up;
+    const unsigned long long t = a;
+    a = swap ? b : a;
+    b = swap ? t : b;
+}
+
+// Bitonic sort, ascending, of the 256 keys of a warp: key 8 lane + j in v[j].
+// Strides below 8 pair two registers of one lane; a stride s >= 8 pairs lane
+// l with lane l ^ (s / 8), and each of the two keeps the lower or the higher
+// of its exchanged keys.
+__device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&v)[8], int lane) {
+#pragma unroll
+    for (int size = 2; size <= kWarpSortKeys; size <<= 1) {
+#pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int k = threadIdx.x; k < p2; k += blockDim.x) {
-                int partner = k ^ stride;
-                if (partner > k) {
-                    bool up = ((k & size) == 0);
-                    unsigned long long u = sk[k], v = sk[partner];
-                    if ((u > v) == up) {
-                        sk[k] = v;
-                        sk[partner] = u;
-                    }
+            if (stride >= 8) {
+                const int lm = stride >> 3;
+                const bool up = ((8 * lane) & size) == 0;
+                const bool keep_lo = up == ((lane & lm) == 0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[j], lm);
+                    v[j] = keep_lo ? (o < v[j] ? o : v[j]) : (o > v[j] ? o : v[j]);
                 }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if ((j ^ stride) > j) cmpx(v[j], v[j ^ stride], ((8 * lane + j) & size) == 0);
             }
-            __syncthreads();
         }
     }
-    int c0 = col_clus_start[col];
-    int ncl = (cnt + NB_CLUSTER - 1) / NB_CLUSTER;
-    int s0 = c0 * NB_CLUSTER;
+}
+
+// The rest of a column once its cnt keys are sorted by z in sk: its z index,
+// its slot <-> atom maps, search-frame positions and padding, and its
+// clusters' bounding boxes. G threads (t = 0 .. G - 1) take part, G a
+// multiple of 32: the 8 slots of a cluster are 8 aligned lanes of a warp,
+// which reduce the bounding box over its real atoms with shuffles.
+template <int G>
+__device__ __forceinline__ void finish_column(const ColSortParams &p, const unsigned long long *sk, int cnt,
+                                              int col, int t) {
+    const int c0 = p.col_clus_start[col];
+    const int ncl = (cnt + NB_CLUSTER - 1) / NB_CLUSTER;
+    const int s0 = c0 * NB_CLUSTER;
     const float4 pad = make_float4(NB_PAD_COORD, NB_PAD_COORD, NB_PAD_COORD, 0.0f);
-    const int csys = col_sys[col];
+    const int csys = p.col_sys[col];
     // the column's z index: per bin k, the first cluster whose upper z bound (its last atom's z; the
     // keys are sorted by z) reaches k Lz / NB_ZBINS
-    if (threadIdx.x <= NB_ZBINS) {
-        const float zb = (float)threadIdx.x * (sys[csys].box.z / (float)NB_ZBINS);
+    for (int zb_k = t; zb_k <= NB_ZBINS; zb_k += G) {
+        const float zb = (float)zb_k * (p.sys[csys].box.z / (float)NB_ZBINS);
         int a = 0, b = ncl;
         while (a < b) {
             const int m = (a + b) >> 1;
@@ -186,30 +221,28 @@ __global__ void __launch_bounds__(256) k_col_sort(
             else
                 a = m + 1;
         }
-        ztab[col * (NB_ZBINS + 1) + threadIdx.x] = c0 + a;
+        p.ztab[col * (NB_ZBINS + 1) + zb_k] = c0 + a;
     }
-    // one thread per slot; the 8 slots of a cluster are 8 aligned lanes of a warp, which reduce the
-    // cluster's bounding box over its real atoms with shuffles (every lane of a warp takes part)
     const int nslots = ncl * NB_CLUSTER;
-    for (int k0 = 0; k0 < nslots; k0 += blockDim.x) {
-        const int k = k0 + (int)threadIdx.x;
+    for (int k0 = 0; k0 < nslots; k0 += G) {
+        const int k = k0 + t;
         const int slot = s0 + k;
         float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f), hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.0f);
         if (k < cnt) {
-            int atom = (int)(sk[k] & 0xffffffffu);
-            float4 w = xw[atom];
-            perm[slot] = atom;
-            pos[atom] = slot;
-            xref[slot] = w;
-            xprune[slot] = w;
+            const int atom = (int)(sk[k] & 0xffffffffu);
+            const float4 w = p.xw[atom];
+            p.perm[slot] = atom;
+            p.pos[atom] = slot;
+            p.xref[slot] = w;
+            p.xprune[slot] = w;
             lo = make_float4(w.x, w.y, w.z, 0.0f);
             hi = lo;
         } else if (k < nslots) {
-            perm[slot] = -1;
-            xref[slot] = pad;
-            xprune[slot] = pad;
-            xq[slot] = pad;
-            tsort[slot] = 0;
+            p.perm[slot] = -1;
+            p.xref[slot] = pad;
+            p.xprune[slot] = pad;
+            p.xq[slot] = pad;
+            p.tsort[slot] = 0;
         }
 #pragma unroll
         for (int o = 1; o < NB_CLUSTER; o <<= 1) {
@@ -225,10 +258,74 @@ __global__ void __launch_bounds__(256) k_col_sort(
             const int nreal = min(NB_CLUSTER, cnt - k);
             lo.w = __int_as_float(nreal);
             hi.w = __int_as_float(col);
-            bbox[2 * (c0 + c)] = lo;
-            bbox[2 * (c0 + c) + 1] = hi;
-            clus_sys[c0 + c] = csys;
+            p.bbox[2 * (c0 + c)] = lo;
+            p.bbox[2 * (c0 + c) + 1] = hi;
+            p.clus_sys[c0 + c] = csys;
         }
+    }
+}
+
+// cpc columns per CTA. With several (short columns on average), a column of
+// at most kWarpSortKeys atoms is sorted by one warp in registers (no block
+// barriers) and a longer one, after those, by the whole CTA with a bitonic
+// sort in shared memory. The launch takes one column per CTA when columns
+// hold more than kWarpSortKeys / 2 atoms on average; the whole CTA then
+// sorts it (one warp alone was slower: its 36 dependent shuffle stages are
+// not shared out). Shared memory: NB_MAX_COL_ATOMS keys, kWarpSortKeys of
+// them per warp for short columns.
+__global__ void __launch_bounds__(kSortWarps * 32) k_col_sort(ColSortParams p) {
+    static_assert(kSortWarps * kWarpSortKeys <= NB_MAX_COL_ATOMS, "warp regions exceed the key buffer");
+    __shared__ unsigned long long sk[NB_MAX_COL_ATOMS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col0 = blockIdx.x * p.cpc;
+    const int warp_max = p.cpc > 1 ? kWarpSortKeys : 0;  // the longest column a warp sorts alone
+    if (warp < p.cpc) {
+        const int col = col0 + warp;
+        const int cnt = col < p.ncol ? min(p.col_count[col], NB_MAX_COL_ATOMS) : 0;
+        if (col < p.ncol && cnt <= warp_max) {
+            const int a0 = p.col_atom_start[col];
+            unsigned long long v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 8 * lane + j;
+                v[j] = k < cnt ? p.keys[a0 + k] : ~0ull;
+            }
+            warp_bitonic_sort(v, lane);
+            unsigned long long *sw = sk + warp * kWarpSortKeys;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sw[8 * lane + j] = v[j];
+            __syncwarp();
+            finish_column<32>(p, sw, cnt, col, lane);
+        }
+    }
+    for (int w = 0; w < p.cpc; ++w) {  // the same decisions in every thread of the CTA
+        const int col = col0 + w;
+        if (col >= p.ncol) break;
+        const int cnt = min(p.col_count[col], NB_MAX_COL_ATOMS);  // overflow already flagged by the scan
+        if (cnt <= warp_max) continue;
+        __syncthreads();  // every earlier use of sk is over
+        const int a0 = p.col_atom_start[col];
+        int p2 = 1;
+        while (p2 < cnt) p2 <<= 1;
+        for (int k = threadIdx.x; k < p2; k += blockDim.x) sk[k] = (k < cnt) ? p.keys[a0 + k] : ~0ull;
+        __syncthreads();
+        for (int size = 2; size <= p2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int k = threadIdx.x; k < p2; k += blockDim.x) {
+                    const int partner = k ^ stride;
+                    if (partner > k) {
+                        const bool up = ((k & size) == 0);
+                        const unsigned long long u = sk[k], v = sk[partner];
+                        if ((u > v) == up) {
+                            sk[k] = v;
+                            sk[partner] = u;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        finish_column<kSortWarps * 32>(p, sk, cnt, col, threadIdx.x);
     }
 }
 
@@ -248,8 +345,25 @@ cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream
                             pl->st);
     k_col_scan<<<1, 1024, 0, s>>>(pl->ncol, pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->st);
     k_col_scatter<<<gb, bs, 0, s>>>(n, pl->xw, pl->atom_col, pl->atom_slot, pl->col_atom_start, pl->keys);
-    k_col_sort<<<pl->ncol, 256, 0, s>>>(pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->keys, pl->xw,
-                                        pl->col_sys, pl->perm, pl->pos, pl->xref, pl->xprune, pl->xq, pl->tsort,
-                                        pl->bbox, pl->clus_sys, pl->sys, pl->ztab);
+    ColSortParams cp;
+    cp.col_count = pl->col_count;
+    cp.col_atom_start = pl->col_atom_start;
+    cp.col_clus_start = pl->col_clus_start;
+    cp.keys = pl->keys;
+    cp.xw = pl->xw;
+    cp.col_sys = pl->col_sys;
+    cp.perm = pl->perm;
+    cp.pos = pl->pos;
+    cp.xref = pl->xref;
+    cp.xprune = pl->xprune;
+    cp.xq = pl->xq;
+    cp.tsort = pl->tsort;
+    cp.bbox = pl->bbox;
+    cp.clus_sys = pl->clus_sys;
+    cp.sys = pl->sys;
+    cp.ztab = pl->ztab;
+    cp.ncol = pl->ncol;
+    cp.cpc = (long long)n <= (long long)pl->ncol * (kWarpSortKeys / 2) ? kSortWarps : 1;
+    k_col_sort<<<(pl->ncol + cp.cpc - 1) / cp.cpc, kSortWarps * 32, 0, s>>>(cp);
     return cudaGetLastError();
 }
