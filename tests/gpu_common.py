@@ -121,3 +121,30 @@ def oracle_ref(box, rc, beta, coords=None):
     x = box.coords if coords is None else coords
     return oracle.energy_forces(x, box.q, box.type, box.ljparams, box.box, rc, beta, box.excl_off,
                                 box.excl_idx)
+
+
+def tiled_along_z(b, reps):
+    """The cubic box b repeated reps times along z: an orthorhombic L x L x reps L box of whole
+    molecules (each water made whole by the minimum image before it is copied and rewrapped)."""
+    L = b.box.astype(np.float64)
+    x = b.coords.astype(np.float64).reshape(-1, 3, 3)  # [molecule, atom (O, H, H), xyz]
+    d = x[:, 1:, :] - x[:, :1, :]
+    x[:, 1:, :] = x[:, :1, :] + d - L * np.rint(d / L)
+    box = np.array([L[0], L[1], reps * L[2]])
+    y = np.concatenate([x + np.array([0.0, 0.0, k * L[2]]) for k in range(reps)]).reshape(-1, 3)
+    y -= box * np.floor(y / box)
+
+    class Tiled:
+        pass
+
+    t = Tiled()
+    n = b.n_atoms
+    t.coords = y.astype(np.float32)
+    t.box = box.astype(np.float32)
+    t.n_atoms = reps * n
+    t.q = np.tile(b.q, reps)
+    t.type = np.tile(b.type, reps)
+    t.ljparams = b.ljparams
+    t.excl_off = np.concatenate([[0]] + [b.excl_off[1:] + k * b.excl_off[-1] for k in range(reps)]).astype(np.int32)
+    t.excl_idx = np.concatenate([b.excl_idx + k * n for k in range(reps)]).astype(np.int32)
+    return t

@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import synth
-from gpu_common import E_TOL, compare_forces, rel
+from gpu_common import E_TOL, compare_forces, rel, tiled_along_z
 
 pytestmark = pytest.mark.gpu
 
@@ -118,4 +118,33 @@ def test_batch_graph_replay(nb, batch):
         torch.testing.assert_close(F, F_eager, rtol=0, atol=1e-5 * F_eager.abs().max().item())
         torch.testing.assert_close(E, E_eager, rtol=1e-9, atol=0)
     assert pl.status() == 0
+    pl.close()
+
+
+def test_batch_with_long_and_short_columns(nb):
+    """Six 1,536-atom boxes (columns of about 61 atoms) and one 2.48 x 2.48 x 19.9 nm box (columns of
+    about 490 atoms): the columns average below 128 atoms, so the grid sort takes eight columns per
+    CTA, sorts the short ones in warp registers and the long ones with the whole CTA in shared
+    memory. Pair counts, forces and energies of every system against the oracle."""
+    rc, rlist = 0.9, 1.0
+    beta = synth.ewald_beta(rc)
+    boxes = [synth.water_box(512, 300 + k) for k in range(6)] + [tiled_along_z(synth.water_box(512, 1), 8)]
+    off, x, q, t, eo, ei, bx = concat(boxes)
+    lj = dev(boxes[0].ljparams)
+    pl = nb.Pairlist.batch(off, bx, count_pairs=True)
+    pl.search(dev(x), None, rlist, dev(eo), dev(ei))
+    st = pl.stats()
+    assert pl.n_atoms <= 128 * st["n_columns"]  # short columns on average
+    F, E = pl.forces(dev(x), dev(q), dev(t), lj, rc, beta)
+    assert pl.status() == 0
+    F = F.cpu().numpy()
+    E = E.cpu().numpy().reshape(-1, 2)
+    total_pairs = 0
+    for k, b in enumerate(boxes):
+        Fo, elj, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                              b.excl_idx)
+        compare_forces(F[off[k]:off[k + 1]], Fo)
+        assert rel(E[k, 0], elj) <= E_TOL and rel(E[k, 1], ec) <= E_TOL, k
+        total_pairs += oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx, count_only=True)
+    assert pl.stats()["pairs_last"] == total_pairs
     pl.close()

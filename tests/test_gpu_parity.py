@@ -11,7 +11,7 @@ import torch
 import oracle
 import synth
 from gpu_common import (E_TOL, assert_same_pairs, compare_forces, expand_counted_pairs, expand_tile_pairs, oracle_ref,
-                        pair_set, rel, to_dev)
+                        pair_set, rel, tiled_along_z, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -526,33 +526,6 @@ def test_list_sorting_does_not_change_results(nb):
     assert n1 == n2
     np.testing.assert_allclose(F1, F2, rtol=0, atol=1e-5 * np.abs(F2).max())
     assert rel(E1[0], E2[0]) <= 1e-7 and rel(E1[1], E2[1]) <= 1e-7
-
-
-def tiled_along_z(b, reps):
-    """The cubic box b repeated reps times along z: an orthorhombic L x L x reps L box of whole
-    molecules (each water made whole by the minimum image before it is copied and rewrapped)."""
-    L = b.box.astype(np.float64)
-    x = b.coords.astype(np.float64).reshape(-1, 3, 3)  # [molecule, atom (O, H, H), xyz]
-    d = x[:, 1:, :] - x[:, :1, :]
-    x[:, 1:, :] = x[:, :1, :] + d - L * np.rint(d / L)
-    box = np.array([L[0], L[1], reps * L[2]])
-    y = np.concatenate([x + np.array([0.0, 0.0, k * L[2]]) for k in range(reps)]).reshape(-1, 3)
-    y -= box * np.floor(y / box)
-
-    class Tiled:
-        pass
-
-    t = Tiled()
-    n = b.n_atoms
-    t.coords = y.astype(np.float32)
-    t.box = box.astype(np.float32)
-    t.n_atoms = reps * n
-    t.q = np.tile(b.q, reps)
-    t.type = np.tile(b.type, reps)
-    t.ljparams = b.ljparams
-    t.excl_off = np.concatenate([[0]] + [b.excl_off[1:] + k * b.excl_off[-1] for k in range(reps)]).astype(np.int32)
-    t.excl_idx = np.concatenate([b.excl_idx + k * n for k in range(reps)]).astype(np.int32)
-    return t
 
 
 def test_elongated_orthorhombic_box(nb):
