@@ -14,6 +14,7 @@ Functions:
 * ``pairs_f32`` - the set of pairs within rc under the FP32 contract that the
   GPU pair list must reproduce bit for bit.
 * ``image_f32`` - the FP32 positions that contract uses.
+* ``energy_f32`` - E_LJ and E_C at the distances that contract fixes.
 * ``force_vjp`` - adjoint of the forces: dL/dx, dL/dq, dL/dC given dL/dF.
 * ``force_matching`` - loss (1/3N) sum |F - T|^2 and its gradients.
 * ``bspline``, ``pme_spread``, ``pme_gather`` - smooth-PME cardinal
@@ -78,6 +79,8 @@ def _load():
             lib.oracle_pairs_f32.restype = I
             lib.oracle_image_f32.argtypes = [I, P, P, P, P]
             lib.oracle_image_f32.restype = None
+            lib.oracle_energy_f32.argtypes = [I, P, P, P, P, I, P, P, D, D, P, P, P, P]
+            lib.oracle_energy_f32.restype = I
             lib.oracle_force_vjp.argtypes = [I, P, P, P, I, P, P, D, D, P, P, P, P, P, P]
             lib.oracle_force_vjp.restype = I
             lib.oracle_energy_forces_coul.argtypes = [I, P, P, P, I, P, P, D, D, P, P, I, D, I, P, P, P]
@@ -210,6 +213,28 @@ def pairs_f32(x0, x, box, rc, excl_off=None, excl_idx=None, count_only=False):
         if cnt.value <= cap:
             return np.stack([pi[:cnt.value], pj[:cnt.value]], axis=1).astype(np.int64)
         cap = int(cnt.value)
+
+
+def energy_f32(x0, x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None):
+    """FP64 pair energies at the distances of the FP32 contract: ``(E_lj, E_coul, npairs)``.
+
+    The plain definitions of ``energy_forces``, summed over the ``pairs_f32``
+    set, each pair at its FP32-contract r^2. The difference from
+    ``energy_forces`` is what rounding the displacements to FP32 does to the
+    energies by itself.
+    """
+    lib = _load()
+    x0 = _f32(x0).reshape(-1, 3)
+    x = _f32(x).reshape(-1, 3)
+    lj = _f64(lj)
+    E = np.zeros(2, dtype=np.float64)
+    npairs = ctypes.c_longlong(0)
+    rcode = lib.oracle_energy_f32(x.shape[0], _p(x0), _p(x), _p(_f64(q)), _p(_i32(type_)), lj.shape[0], _p(lj),
+                                  _p(_f32(box)), float(rc), float(beta), _p(_i32(excl_off)), _p(_i32(excl_idx)),
+                                  _p(E), ctypes.byref(npairs))
+    if rcode != 0:
+        raise ValueError(f"oracle_energy_f32 failed with code {rcode}")
+    return float(E[0]), float(E[1]), int(npairs.value)
 
 
 def image_f32(x0, x, box):

@@ -22,7 +22,8 @@
  *
  * oracle_energy_forces_coul / oracle_force_vjp_coul (end of this file) add
  * the reaction-field flavour, the Ewald potential shift and the
- * excluded-pair correction.
+ * excluded-pair correction. oracle_energy_f32 (the end of this file) gives
+ * the same energies at the distances the FP32 contract fixes.
  *
  * Pins (tests, CPU only): Coulomb's law at beta = 0, tabulated erfc values,
  * the LJ force zero at 2^(1/6) sigma and energy zero at sigma, continuity at
@@ -1016,4 +1017,65 @@ int oracle_pme_gather(int n, const double *x, const double *q, const double *box
         if (psi) psi[i] = p;
     }
     return 0;
+}
+
+/*
+ * Energies at the distances the FP32 contract fixes. E_LJ and E_C are the
+ * plain FP64 definitions of pair_terms, summed over the FP32 pair set of
+ * oracle_pairs_f32, each pair evaluated at its contract value
+ * r^2 = fl(dz dz + fl(dy dy + fl(dx dx))), d = fl(fl(y_i - y_j) + S), y the
+ * contract positions. Its difference from oracle_energy_forces (FP64
+ * displacements) is the energy error that rounding the displacements to
+ * FP32 causes by itself; in water the Coulomb pair energies cancel to a few
+ * thousandths of their absolute sum, so at ~10^3 atoms that alone reaches
+ * ~1e-6 of E_C. rc is used as given for the LJ shift and as (float)rc for
+ * the contract. E[0] = E_LJ, E[1] = E_C. Returns 0, or the error code of
+ * oracle_pairs_f32 (-2: out of memory).
+ */
+int oracle_energy_f32(int n, const float *x0, const float *x, const double *q, const int *type, int ntype,
+                      const double *lj, const float *box, double rc, double beta, const int *excl_off,
+                      const int *excl_idx, double *E, long long *npairs) {
+    const float rcf = (float)rc;
+    long long cnt = 0;
+    int st = oracle_pairs_f32(n, x0, x, box, rcf, excl_off, excl_idx, NULL, NULL, 0, &cnt);
+    if (st < 0) return st;
+    int *pi = (int *)malloc(sizeof(int) * (size_t)(cnt + 1));
+    int *pj = (int *)malloc(sizeof(int) * (size_t)(cnt + 1));
+    float *y = (float *)malloc(sizeof(float) * 3 * (size_t)n + 1);
+    if (!pi || !pj || !y) {
+        free(pi);
+        free(pj);
+        free(y);
+        return -2;
+    }
+    st = oracle_pairs_f32(n, x0, x, box, rcf, excl_off, excl_idx, pi, pj, cnt, &cnt);
+    oracle_image_f32(n, x0, x, box, y);
+    const float rc2 = rcf * rcf;
+    double sum_lj = 0.0, sum_c = 0.0;
+    for (long long p = 0; st >= 0 && p < cnt; ++p) {
+        const int i = pi[p], j = pj[p];
+        float u[3];
+        for (int k = 0; k < 3; ++k) u[k] = y[3 * i + k] - y[3 * j + k];
+        for (int sx = -1; sx <= 1; ++sx)
+            for (int sy = -1; sy <= 1; ++sy)
+                for (int sz = -1; sz <= 1; ++sz) {
+                    const float dx = u[0] + (float)sx * box[0];
+                    const float dy = u[1] + (float)sy * box[1];
+                    const float dz = u[2] + (float)sz * box[2];
+                    const float r2 = r2_32(dx, dy, dz);
+                    if (!(r2 < rc2)) continue;  /* the one image within rc (the pair set checks it) */
+                    const double *c = lj + 2 * ((size_t)type[i] * ntype + type[j]);
+                    double elj, ec, s;
+                    pair_terms((double)r2, q[i], q[j], c[0], c[1], rc, beta, &elj, &ec, &s);
+                    sum_lj += elj;
+                    sum_c += ec;
+                }
+    }
+    E[0] = sum_lj;
+    E[1] = sum_c;
+    *npairs = cnt;
+    free(pi);
+    free(pj);
+    free(y);
+    return st < 0 ? st : 0;
 }

@@ -125,7 +125,10 @@ def test_batch_with_long_and_short_columns(nb):
     """Six 1,536-atom boxes (columns of about 61 atoms) and one 2.48 x 2.48 x 19.9 nm box (columns of
     about 490 atoms): the columns average below 128 atoms, so the grid sort takes eight columns per
     CTA, sorts the short ones in warp registers and the long ones with the whole CTA in shared
-    memory. Pair counts, forces and energies of every system against the oracle."""
+    memory. Pair counts, forces and energies of every system against the oracle: at 1,536 atoms the
+    FP32 rounding of the displacements alone moves E_C by up to about 1e-6 of it, so the energies are
+    held to 1e-6 of the oracle's energies at the FP32 contract's distances, and to that bar plus the
+    contract's own offset against the FP64 oracle."""
     rc, rlist = 0.9, 1.0
     beta = synth.ewald_beta(rc)
     boxes = [synth.water_box(512, 300 + k) for k in range(6)] + [tiled_along_z(synth.water_box(512, 1), 8)]
@@ -144,7 +147,11 @@ def test_batch_with_long_and_short_columns(nb):
         Fo, elj, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
                                               b.excl_idx)
         compare_forces(F[off[k]:off[k + 1]], Fo)
-        assert rel(E[k, 0], elj) <= E_TOL and rel(E[k, 1], ec) <= E_TOL, k
-        total_pairs += oracle.pairs_f32(b.coords, b.coords, b.box, rc, b.excl_off, b.excl_idx, count_only=True)
+        e32_lj, e32_c, n32 = oracle.energy_f32(b.coords, b.coords, b.q, b.type, b.ljparams, b.box, rc, beta,
+                                               b.excl_off, b.excl_idx)
+        assert rel(E[k, 0], e32_lj) <= E_TOL and rel(E[k, 1], e32_c) <= E_TOL, k
+        assert abs(E[k, 0] - elj) <= E_TOL * abs(elj) + abs(e32_lj - elj), k
+        assert abs(E[k, 1] - ec) <= E_TOL * abs(ec) + abs(e32_c - ec), k
+        total_pairs += n32
     assert pl.stats()["pairs_last"] == total_pairs
     pl.close()

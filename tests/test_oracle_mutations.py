@@ -28,6 +28,10 @@ MUTATIONS = {
     # the FP32 contract's image of a displaced position (search frame x0 != current frame x)
     "fp32_image_uses_floor": ("float k = rintf((x - w0) / L);", "float k = floorf((x - w0) / L);"),
     "fp32_image_sign_slip": ("return x - k * L;", "return x + k * L;"),
+    # the energies at the contract's distances
+    "energy_f32_drops_the_shift": ("const float dx = u[0] + (float)sx * box[0];", "const float dx = u[0];"),
+    "energy_f32_lj_parameters_swapped": ("q[i], q[j], c[0], c[1], rc, beta", "q[i], q[j], c[1], c[0], rc, beta"),
+    "energy_f32_partner_charge": ("pair_terms((double)r2, q[i], q[j],", "pair_terms((double)r2, q[i], q[i],"),
 }
 
 # mistakes in the force adjoint, caught by tests/test_oracle_adjoint.py

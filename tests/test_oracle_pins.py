@@ -404,6 +404,73 @@ def test_pairs_f32_invariant_under_whole_box_shifts(box512):
         assert np.array_equal(oracle.pairs_f32(x0s, xts, L32, 0.9, b.excl_off, b.excl_idx), p)
 
 
+def _grid_system(seed, n=128, L=4.0, step=1.0 / 16.0, dmin=0.3):
+    """n atoms at distinct points of a 1/16 nm grid in an L = 4 nm box, at least dmin apart (minimum
+    image), two LJ types. Every FP32 displacement of the contract (|d| < 2 nm, a multiple of 1/16),
+    its square and the sum of three squares (multiples of 1/256 below 12) are exact in FP32."""
+    rng = np.random.default_rng(seed)
+    m = int(round(L / step))
+    pts = []
+    while len(pts) < n:
+        p = rng.integers(0, m, 3) * step
+        if all(np.linalg.norm((p - o) - L * np.rint((p - o) / L)) >= dmin for o in pts):
+            pts.append(p)
+    x = np.array(pts, dtype=np.float32)
+    q = rng.normal(0.0, 0.5, n)
+    typ = rng.integers(0, 2, n).astype(np.int32)
+    lj = np.zeros((2, 2, 2))
+    c6, c12 = np.array([2e-3, 1e-3]), np.array([2e-6, 1e-6])
+    for a in range(2):
+        for b in range(2):
+            lj[a, b] = (math.sqrt(c6[a] * c6[b]), math.sqrt(c12[a] * c12[b]))
+    return x, q, typ, lj, np.array([L, L, L], dtype=np.float32)
+
+
+def test_energy_f32_equals_fp64_where_fp32_distances_are_exact():
+    """Where every FP32 displacement and r^2 of the contract is exact (grid coordinates), the energies
+    at the contract's distances are the FP64 energies: same pair count, E_LJ and E_C to rounding."""
+    for seed in range(3):
+        x, q, typ, lj, box = _grid_system(seed)
+        beta = synth.ewald_beta(0.9)
+        _, elj, ec, npairs = oracle.energy_forces(x, q, typ, lj, box, 0.9, beta, method="n2")
+        e32_lj, e32_c, n32 = oracle.energy_f32(x, x, q, typ, lj, box, 0.9, beta)
+        assert n32 == npairs > 200
+        assert abs(e32_lj - elj) <= 1e-12 * abs(elj) and abs(e32_c - ec) <= 1e-12 * abs(ec)
+
+
+def test_energy_f32_unchanged_by_whole_box_shifts():
+    """Adding whole box vectors to the inputs (exact on the grid) changes no contract distance, so the
+    energies at those distances are unchanged bit for bit; a displaced frame too."""
+    x, q, typ, lj, box = _grid_system(7)
+    beta = synth.ewald_beta(0.9)
+    L = box.astype(np.float64)
+    rng = np.random.default_rng(8)
+    xt = (x + rng.integers(-1, 2, x.shape) / 16.0 * (rng.random(x.shape) < 0.3)).astype(np.float32)
+    xt = (xt - L * np.floor(xt.astype(np.float64) / L)).astype(np.float32)
+    ref = oracle.energy_f32(x, xt, q, typ, lj, box, 0.9, beta)
+    for s in range(3):
+        k0 = rng.integers(-2, 3, x.shape)
+        k = rng.integers(-2, 3, x.shape)
+        got = oracle.energy_f32((x + k0 * L).astype(np.float32), (xt + k * L).astype(np.float32), q, typ, lj, box,
+                                0.9, beta)
+        assert got == ref
+
+
+def test_energy_f32_close_to_fp64_on_water(box512):
+    """On water the two differ only by FP32 rounding of the displacements: within 2e-6 of each energy
+    (the Coulomb pair energies cancel to ~1/300 of their absolute sum, which amplifies that rounding)."""
+    b = box512
+    beta = synth.ewald_beta(0.9)
+    _, elj, ec, npairs = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, 0.9, beta, b.excl_off,
+                                              b.excl_idx)
+    e32_lj, e32_c, n32 = oracle.energy_f32(b.coords, b.coords, b.q, b.type, b.ljparams, b.box, 0.9, beta,
+                                           b.excl_off, b.excl_idx)
+    assert n32 == oracle.pairs_f32(b.coords, b.coords, b.box, 0.9, b.excl_off, b.excl_idx, count_only=True)
+    assert abs(n32 - npairs) <= 2
+    assert abs(e32_lj - elj) <= 2e-6 * abs(elj) and abs(e32_c - ec) <= 2e-6 * abs(ec)
+    assert e32_c != ec  # the rounding is there
+
+
 def test_pair_count_matches_density(box512):
     """Half-pairs per atom within rc ~ rho (2/3) pi rc^3, minus one excluded pair per atom."""
     b = synth.water_box(32000, 2)
