@@ -313,10 +313,9 @@ extern "C" int nb_search(nb_pairlist *pl, const float *coords, const float *box,
         pl->ncy = ncy;
         pl->ncol = ncx * ncy;
         pl->sys_host[0] = make_sys(box, ncx, ncy, 0, 0, pl->n_atoms);
-        NB_CUDA(nb_launch_set_system(pl, pl->sys_host[0], s));
     }
-    NB_CUDA(cudaMemsetAsync(&pl->st->list_count, 0, sizeof(unsigned long long), s));
-    NB_CUDA(nb_launch_grid_sort(pl, coords, s));
+    // the grid sort's first kernel clears the list counter (and writes a single system's table)
+    NB_CUDA(nb_launch_grid_sort(pl, coords, pl->batch ? nullptr : &pl->sys_host[0], s));
 
     // The bounding-box test uses a radius inflated by a few ulps of the box
     // edge, so that every pair within rlist under the FP32 distance contract

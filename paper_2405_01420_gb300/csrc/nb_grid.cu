@@ -1,5 +1,7 @@
 // Grid sort into 8-atom clusters (first stage of the pair search, §III-A).
 //
+// 0. k_search_begin: clear the column counts and the list counter; write a
+//    single system's table.
 // 1. k_bin: wrap each atom into the box and bin it into an xy column;
 //    count atoms per column.
 // 2. k_col_scan: exclusive scans of atoms and of 8-atom clusters per column.
@@ -11,15 +13,28 @@
 //
 // Layout in HBM after the sort (slot = 8 * cluster + lane):
 //   perm[slot] (int), xref[slot] (float4), bbox[2c], bbox[2c+1] (float4).
+#include <algorithm>
+#include <cstring>
+
 #include "nb_internal.cuh"
 
 namespace {
 
-// Writes the system table of a single-system pair list (one entry and its
+// The start of a search: clears the column counts and the list counter and,
+// for a single-system pair list, writes its system table (one entry and its
 // 27 shift vectors) from kernel arguments, so that a search can be captured
-// in a CUDA graph without a host-to-device copy.
-__global__ void k_set_system(nb_sys *sys, float4 *sys_shift, nb_sys one) {
+// in a CUDA graph without a host-to-device copy. Like every kernel of the
+// grid sort and the search it may be launched with programmatic dependent
+// launch (nb_launch_if, for lists up to NB_SEARCH_PDL_MAX_CLUSTERS).
+__global__ void k_search_begin(nb_sys *sys, float4 *sys_shift, nb_sys one, int write_sys, int *col_count, int ncol,
+                               nb_dev_state *st) {
+    nb_pdl_wait();
+    nb_pdl_release();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncol; k += gridDim.x * blockDim.x) col_count[k] = 0;
+    if (blockIdx.x != 0) return;
     const int k = threadIdx.x;
+    if (k == 0) st->list_count = 0ull;
+    if (!write_sys) return;
     if (k == 0) sys[0] = one;
     if (k < 27)
         sys_shift[k] = make_float4((float)nb_shift_x(k) * one.box.x, (float)nb_shift_y(k) * one.box.y,
@@ -29,6 +44,8 @@ __global__ void k_set_system(nb_sys *sys, float4 *sys_shift, nb_sys one) {
 __global__ void k_bin(int n, const float *__restrict__ coords, const int *__restrict__ atom_sys,
                       const nb_sys *__restrict__ sys, int *__restrict__ col_count, int *__restrict__ atom_col,
                       int *__restrict__ atom_slot, float4 *__restrict__ xw, nb_dev_state *st) {
+    nb_pdl_wait();
+    nb_pdl_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int col = -1 - lane;  // lanes past the end match nobody below
@@ -65,6 +82,8 @@ __global__ void __launch_bounds__(1024) k_col_scan(int ncol, const int *__restri
                                                    int *__restrict__ col_atom_start,
                                                    int *__restrict__ col_clus_start,
                                                    nb_dev_state *st) {
+    nb_pdl_wait();
+    nb_pdl_release();
     __shared__ int warp_a[32], warp_c[32];
     int t = threadIdx.x, nt = blockDim.x;
     int chunk = (ncol + nt - 1) / nt;
@@ -129,6 +148,8 @@ __global__ void k_col_scatter(int n, const float4 *__restrict__ xw, const int *_
                               const int *__restrict__ atom_slot,
                               const int *__restrict__ col_atom_start,
                               unsigned long long *__restrict__ keys) {
+    nb_pdl_wait();
+    nb_pdl_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     // z >= 0 after wrapping, so its bit pattern orders like the value
@@ -276,6 +297,8 @@ __device__ __forceinline__ void finish_column(const ColSortParams &p, const unsi
 __global__ void __launch_bounds__(kSortWarps * 32) k_col_sort(ColSortParams p) {
     static_assert(kSortWarps * kWarpSortKeys <= NB_MAX_COL_ATOMS, "warp regions exceed the key buffer");
     __shared__ unsigned long long sk[NB_MAX_COL_ATOMS];
+    nb_pdl_wait();
+    nb_pdl_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int col0 = blockIdx.x * p.cpc;
     const int warp_max = p.cpc > 1 ? kWarpSortKeys : 0;  // the longest column a warp sorts alone
@@ -331,20 +354,25 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_col_sort(ColSortParams p) {
 
 }  // namespace
 
-cudaError_t nb_launch_set_system(nb_pairlist *pl, const nb_sys &one, cudaStream_t s) {
-    k_set_system<<<1, 32, 0, s>>>(pl->sys, pl->sys_shift, one);
-    return cudaGetLastError();
-}
-
-cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream_t s) {
-    int n = pl->n_atoms;
-    cudaError_t e = cudaMemsetAsync(pl->col_count, 0, sizeof(int) * (size_t)pl->ncol, s);
+cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, const nb_sys *one, cudaStream_t s) {
+    const int n = pl->n_atoms;
+    const bool pdl = pl->nc_max <= NB_SEARCH_PDL_MAX_CLUSTERS;
+    nb_sys none;
+    std::memset(&none, 0, sizeof(none));
+    const int bs = 256, gb = (n + bs - 1) / bs;
+    const int gc = std::max(1, std::min((pl->ncol + bs - 1) / bs, 4 * pl->num_sms));
+    cudaError_t e = nb_launch_if(pdl, k_search_begin, gc, bs, 0, s, pl->sys, pl->sys_shift, one ? *one : none,
+                                  one ? 1 : 0, pl->col_count, pl->ncol, pl->st);
     if (e != cudaSuccess) return e;
-    int bs = 256, gb = (n + bs - 1) / bs;
-    k_bin<<<gb, bs, 0, s>>>(n, coords, pl->atom_sys, pl->sys, pl->col_count, pl->atom_col, pl->atom_slot, pl->xw,
-                            pl->st);
-    k_col_scan<<<1, 1024, 0, s>>>(pl->ncol, pl->col_count, pl->col_atom_start, pl->col_clus_start, pl->st);
-    k_col_scatter<<<gb, bs, 0, s>>>(n, pl->xw, pl->atom_col, pl->atom_slot, pl->col_atom_start, pl->keys);
+    e = nb_launch_if(pdl, k_bin, gb, bs, 0, s, n, coords, (const int *)pl->atom_sys, (const nb_sys *)pl->sys,
+                      pl->col_count, pl->atom_col, pl->atom_slot, pl->xw, pl->st);
+    if (e != cudaSuccess) return e;
+    e = nb_launch_if(pdl, k_col_scan, 1, 1024, 0, s, pl->ncol, (const int *)pl->col_count, pl->col_atom_start,
+                      pl->col_clus_start, pl->st);
+    if (e != cudaSuccess) return e;
+    e = nb_launch_if(pdl, k_col_scatter, gb, bs, 0, s, n, (const float4 *)pl->xw, (const int *)pl->atom_col,
+                      (const int *)pl->atom_slot, (const int *)pl->col_atom_start, pl->keys);
+    if (e != cudaSuccess) return e;
     ColSortParams cp;
     cp.col_count = pl->col_count;
     cp.col_atom_start = pl->col_atom_start;
@@ -364,6 +392,5 @@ cudaError_t nb_launch_grid_sort(nb_pairlist *pl, const float *coords, cudaStream
     cp.ztab = pl->ztab;
     cp.ncol = pl->ncol;
     cp.cpc = (long long)n <= (long long)pl->ncol * (kWarpSortKeys / 2) ? kSortWarps : 1;
-    k_col_sort<<<(pl->ncol + cp.cpc - 1) / cp.cpc, kSortWarps * 32, 0, s>>>(cp);
-    return cudaGetLastError();
+    return nb_launch_if(pdl, k_col_sort, (pl->ncol + cp.cpc - 1) / cp.cpc, kSortWarps * 32, 0, s, cp);
 }

@@ -176,8 +176,7 @@ extern "C" int nb_forces_noalloc(int n_atoms, const float *coords, const float *
     const double ulp = (double)std::nextafter(lmax, 2.0f * lmax) - lmax;
     const double rle = rc + std::max(1e-5, 8.0 * ulp) + 1e-6 * rc;
     const float rl2 = std::nextafter((float)(rle * rle), 1e30f);
-    cudaError_t e = nb_launch_set_system(&pl, one, s);
-    if (e == cudaSuccess) e = nb_launch_grid_sort(&pl, coords, s);
+    cudaError_t e = nb_launch_grid_sort(&pl, coords, &one, s);
     if (e == cudaSuccess) e = nb_launch_search(&pl, excl_off, excl_idx, rl2, (float)(rle + 1e-3), s);
     pl.searched = 1;
     pl.has_inner = 0;

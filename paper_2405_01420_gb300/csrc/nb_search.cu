@@ -226,6 +226,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 4) k_search(SearchParams p)
     __shared__ unsigned long long s_tab_m[kSearchWarps][kExclTab];
     __shared__ WalkShared s_walk[kSearchWarps];
     __shared__ int4 s_buf[kSearchWarps][kSearchBuf];
+    nb_pdl_wait();  // with programmatic dependent launch: the grid sort has completed from here on
+    nb_pdl_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nc = p.st->nc;
 
@@ -367,6 +369,5 @@ cudaError_t nb_launch_search(nb_pairlist *pl, const int *excl_off, const int *ex
     p.cap = (unsigned long long)pl->cap;
     int blocks = (pl->nc_max + kSearchWarps - 1) / kSearchWarps;
     blocks = min(blocks, pl->num_sms * 16);
-    k_search<<<blocks, kSearchWarps * 32, 0, s>>>(p);
-    return cudaGetLastError();
+    return nb_launch_if(pl->nc_max <= NB_SEARCH_PDL_MAX_CLUSTERS, k_search, blocks, kSearchWarps * 32, 0, s, p);
 }
