@@ -383,7 +383,9 @@ int nb_set_coulomb(nb_pairlist *pl, int kind, float eps_rf, unsigned flags);
  * not depend on it, only the speed: threads per block (128 or 256), list
  * entries staged in shared memory per warp at a time (8 or 16) and CTAs per
  * SM of the persistent grid (at most what fits; 0 = as many as fit). Zero
- * for threads or chunk restores the default (256, 16).
+ * for threads or chunk restores the default: 128 threads for the kernel over
+ * gathered tiles (after a prune), 256 threads and chunks of 16 for the 8 x 8
+ * cluster-pair kernel.
  */
 int nb_set_force_shape(nb_pairlist *pl, int threads, int chunk, int blocks_per_sm);
 

@@ -116,11 +116,14 @@ __device__ __forceinline__ void stage_copies(const VtParams &p, VtStage &st, int
 // meanwhile.
 // Dynamic shared memory: the ntype x ntype LJ table, then per warp 3 float4
 // per j type (see s_lj2).
-// 768 / THREADS resident CTAs per SM leave 80 registers per thread: the 4
-// rows' forces and the j atom's data stay in registers; the rows' positions,
+// 640 / THREADS resident CTAs per SM (5 of 128 threads, the default shape)
+// leave up to 102 registers per thread (89 used, no spills): the 4 rows'
+// forces and the j atom's data stay in registers; the rows' positions,
 // charges and LJ coefficients are read from the per-warp shared tables.
+// 6 CTAs at 80 registers (and 3 of 256) were 3.5-4 us slower at 96,000
+// atoms, 4 CTAs at up to 128 registers 0.5 us slower.
 template <bool ENERGY, bool COUNT, int THREADS, int COUL>
-__global__ void __launch_bounds__(THREADS, 768 / THREADS) k_force_vt(VtParams p) {
+__global__ void __launch_bounds__(THREADS, 640 / THREADS) k_force_vt(VtParams p) {
     constexpr int kWarps = THREADS / 32;
     extern __shared__ float4 s_lj[];
     __shared__ VtStage s_st[kWarps][2];
@@ -335,7 +338,7 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     p.pad_slot = pl->nc_max * NB_CLUSTER;
     const int e = energies ? 1 : 0;
     const int c = (pl->flags & NB_FLAG_COUNT_PAIRS) ? 1 : 0;
-    const int threads = pl->force_threads == 128 ? 128 : 256;
+    const int threads = pl->force_threads == 256 ? 256 : 128;
     VtFn fn = e ? (c ? pick_vt<true, true>(threads, coul) : pick_vt<true, false>(threads, coul))
                 : (c ? pick_vt<false, true>(threads, coul) : pick_vt<false, false>(threads, coul));
     const size_t smem = sizeof(float4) * ((size_t)ntype * ntype + 3 * (size_t)ntype * (threads / 32));
