@@ -806,16 +806,18 @@ def bench_batch(dev, n_boxes: int = 256, reps: int = 30, plain_reps: int = 5):
     pl.search(xd, None, rlist, eod, eid)
     pl.forces(xd, qd, td, lj, rc, beta, F, E)
     torch.cuda.synchronize()
-    # autotune (untimed): force launch shape, then whether to prune to rc before the forces
-    shape, _ = tune_force_shape(pl, lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
+    # autotune (untimed), each step at the default launch shape: whether to prune to rc before the
+    # forces, then the tile form; last the force launch shape, on the list the batch will use (one
+    # shape serves both force kernels, and they favour different ones)
     use_prune, prune_times = tune_batch_prune(lambda: pl.search(xd, None, rlist, eod, eid),
                                               lambda: pl.prune(xd, rc),
                                               lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
     tile_form, tile_times = "cluster", None
+    pl.search(xd, None, rlist, eod, eid)
     if use_prune:  # the tile form matters only after a prune
-        pl.search(xd, None, rlist, eod, eid)
         pl.prune(xd, rc)
         tile_form, tile_times = tune_tile_form(pl, lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
+    shape, _ = tune_force_shape(pl, lambda: pl.forces(xd, qd, td, lj, rc, beta, F, E), reps=3)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
