@@ -57,7 +57,7 @@ void free_buffers(nb_pairlist *pl) {
                     pl->sys_shift, pl->atom_sys, pl->col_sys,       pl->clus_sys,       pl->len_hist,
                     pl->len_offsets, pl->len_cursor, pl->ci_order,     pl->vt_slot,        pl->vt_mask,
                     pl->half_start, pl->half_len,  pl->len_key,      pl->excl_pairs,  pl->clus_home,
-                    pl->ztab};
+                    pl->ztab,   pl->nl_list};
     for (void *b : bufs)
         if (b) cudaFree(b);
 }
@@ -147,6 +147,7 @@ int alloc_pairlist(nb_pairlist *pl, long long n, const nb_config *cfg, const cha
                 alloc(&pl->excl_pairs, pl->excl_cap, &total) &&
                 alloc(&pl->half_start, 4 * (size_t)pl->nc_max, &total) &&
                 alloc(&pl->half_len, 4 * (size_t)pl->nc_max, &total) &&
+                alloc(&pl->nl_list, 2 * (size_t)pl->nc_max, &total) &&
                 alloc(&pl->clus_home, (size_t)pl->nc_max, &total) &&
                 alloc(&pl->ztab, (size_t)pl->ncol_max * (NB_ZBINS + 1), &total);
     // gathered tiles pack a slot in 27 bits and index tiles with 32-bit ints;

@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
                 p.st->work_prune = 0u;
                 p.st->inner_count = 0ull;
                 p.st->tile_count = 0ull;
+                p.st->nl_count = 0u;
             }
         }
         if (p.energies && p.part != NB_PART_NONLOCAL)

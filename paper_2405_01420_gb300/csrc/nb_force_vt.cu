@@ -63,6 +63,7 @@ struct VtParams {
     int pad_slot;             // never holds an atom: far away, q = 0, type 0
     int reg0, nreg;           // regions of gathered tiles to compute (0 local or all, 1 non-local)
     int reg_stride;           // 2 nc_max: halves per region in half_start / half_len
+    const int *nl_list;       // with a halo: the halves with non-local tiles (the prune's list), else NULL
     int finalize;             // move the displacement maxima of this evaluation to last_*
 };
 
@@ -157,8 +158,12 @@ __global__ void __launch_bounds__(THREADS, 640 / THREADS) k_force_vt(VtParams p)
     // row pairs (0, 1) and (2, 3) at [3t], [3t + 1], minus the 4 rows' LJ
     // shifts at [3t + 2]
     float4 *s_lj2 = s_lj + nt2 + 3 * p.ntype * warp;
+    // Work items: region 0 (every pair without a halo, the local pairs with one) is every half, in
+    // the list order; region 1 (non-local) is the prune's list of the halves that have such tiles
     const unsigned nhalf = 2u * (unsigned)p.st->nc;  // halves per region
-    const unsigned nwork = nhalf * (unsigned)p.nreg;
+    const unsigned n0 = p.reg0 == 0 ? nhalf : 0u;
+    const unsigned n1 = p.reg0 + p.nreg == 2 ? (p.nl_list ? p.st->nl_count : nhalf) : 0u;
+    const unsigned nwork = n0 + n1;
     if (ENERGY && lane == 0) s_e[warp][0] = s_e[warp][1] = 0.0;
     int cur_sys = -1;
     unsigned cnt = 0;
@@ -167,8 +172,16 @@ __global__ void __launch_bounds__(THREADS, 640 / THREADS) k_force_vt(VtParams p)
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&p.st->work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        const unsigned reg = w < nwork ? w / nhalf : 0u, hw = w - reg * nhalf;
-        const int ci = (w < nwork && p.order) ? p.order[hw >> 1] : (int)(hw >> 1);
+        unsigned reg = 0u, hw = 0u;
+        int ci = 0;
+        if (w < n0) {
+            hw = w;
+            ci = p.order ? p.order[hw >> 1] : (int)(hw >> 1);
+        } else if (w < nwork) {
+            reg = 1u;
+            hw = p.nl_list ? (unsigned)p.nl_list[w - n0] : w - n0;
+            ci = (int)(hw >> 1);
+        }
         const int h = (int)(hw & 1u);
         const int csys = (w < nwork) ? p.clus_sys[ci] : -1;
         if (ENERGY && csys != cur_sys) {
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 640 / THREADS) k_force_vt(VtParams p)
             cur_sys = csys;
         }
         if (w >= nwork) break;
-        const size_t hidx = (size_t)(p.reg0 + (int)reg) * p.reg_stride + 2 * ci + h;
+        const size_t hidx = (size_t)reg * p.reg_stride + 2 * ci + h;
         const int t0 = p.half_start[hidx], t1 = t0 + p.half_len[hidx];
         if (t1 <= t0) continue;
         if (csys != shift_sys) {
@@ -314,6 +327,7 @@ cudaError_t nb_launch_force_vt(nb_pairlist *pl, int ntype, const float *ljparams
     p.reg0 = part == NB_PART_NONLOCAL ? 1 : 0;
     p.nreg = (part == NB_PART_ALL && pl->vt_parts == 2) ? 2 : 1;
     p.reg_stride = 2 * pl->nc_max;
+    p.nl_list = pl->vt_parts == 2 ? pl->nl_list : nullptr;
     p.finalize = part != NB_PART_LOCAL;
     p.xq = pl->xq;
     p.tsort = pl->tsort;

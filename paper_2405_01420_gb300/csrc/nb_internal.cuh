@@ -37,6 +37,7 @@ struct nb_dev_state {
     unsigned long long npairs;     // in-range pairs counted by the last force call
     unsigned excl_count;           // excluded pairs recorded by the last search
     unsigned long long tile_count; // gathered tiles written by the last prune
+    unsigned nl_count;             // halves with non-local tiles listed by the last prune (halo split)
 };
 
 // Per-system parameters (one entry per independent box). A single-system
@@ -123,6 +124,7 @@ struct nb_pairlist {
     unsigned *vt_mask;    // [2 cap] 4 x 8 in-range bits per gathered tile
     int *half_start;      // [2 parts][2 nc_max] first gathered tile of each half i-cluster
     int *half_len;        // [2 parts][2 nc_max]
+    int *nl_list;         // [2 nc_max] halves (2 ci + h) with non-local tiles, from the last prune with a halo
     int n_home;           // atoms [0, n_home) are home atoms (nb_set_home); n_atoms = no halo
     int vt_parts;         // regions of gathered tiles: 1, or 2 (local, non-local) with a halo
     unsigned char *clus_home;  // [nc_max] bit b: slot b of the cluster holds a home atom (with a halo)

@@ -36,6 +36,7 @@ struct PruneParams {
     unsigned *vt_mask;   // [2 parts * 2 cap] 4 x 8 in-range bits (bit a*8 + p)
     int *half_start;     // [2 parts][2 nc_max]
     int *half_len;       // [2 parts][2 nc_max]
+    int *nl_list;        // with a halo: the halves (2 ci + h) that have non-local tiles, appended
     int pad_slot;        // a slot that never holds an atom (far away, q = 0)
     int *len_key;        // [nc_max] work of each i-cluster for the force kernel
     int *len_hist;       // [NB_LEN_BINS] histogram of len_key, or NULL (no sorting)
@@ -296,6 +297,9 @@ __global__ void __launch_bounds__(kPruneThreads, kPruneCtasPerSm) k_prune(PruneP
                 const size_t hidx = (size_t)(r >> 1) * p.reg_stride + 2 * ci + (r & 1);
                 p.half_start[hidx] = 2 * NPART * k0 + r * n;
                 p.half_len[hidx] = ntile[r];
+                // the non-local force launch takes its work from this list, not from every half
+                if (NPART == 2 && (r >> 1) == 1 && ntile[r] > 0)
+                    p.nl_list[atomicAdd(&p.st->nl_count, 1u)] = 2 * ci + (r & 1);
             }
         }
         __syncwarp();
@@ -333,6 +337,7 @@ cudaError_t nb_launch_prune(nb_pairlist *pl, float r_inner2, float stale_search2
     p.vt_mask = pl->vt_mask;
     p.half_start = pl->half_start;
     p.half_len = pl->half_len;
+    p.nl_list = pl->nl_list;
     p.pad_slot = pl->nc_max * NB_CLUSTER;
     p.len_key = pl->len_key;
     p.len_hist = (pl->flags & NB_FLAG_NO_LIST_SORT) ? nullptr : pl->len_hist;
