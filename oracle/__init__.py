@@ -215,25 +215,29 @@ def pairs_f32(x0, x, box, rc, excl_off=None, excl_idx=None, count_only=False):
         cap = int(cnt.value)
 
 
-def energy_f32(x0, x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None):
-    """FP64 pair energies at the distances of the FP32 contract: ``(E_lj, E_coul, npairs)``.
+def energy_f32(x0, x, q, type_, lj, box, rc, beta, excl_off=None, excl_idx=None, abs_sums=False):
+    """FP64 pair energies of the FP32 contract: ``(E_lj, E_coul, npairs)``, with ``abs_sums``
+    also ``(sum |e_lj|, sum |e_coul|)`` over the pairs as a fourth item.
 
     The plain definitions of ``energy_forces``, summed over the ``pairs_f32``
-    set, each pair at its FP32-contract r^2. The difference from
-    ``energy_forces`` is what rounding the displacements to FP32 does to the
-    energies by itself.
+    set, each pair at its FP32-contract r^2, with the cutoff the C ABI
+    receives (``float32(rc)``) for the set and the LJ shift. The difference
+    from ``energy_forces(..., rc)`` is what rounding the displacements and
+    the cutoff to FP32 does to the energies by itself.
     """
     lib = _load()
     x0 = _f32(x0).reshape(-1, 3)
     x = _f32(x).reshape(-1, 3)
     lj = _f64(lj)
-    E = np.zeros(2, dtype=np.float64)
+    E = np.zeros(4, dtype=np.float64)
     npairs = ctypes.c_longlong(0)
     rcode = lib.oracle_energy_f32(x.shape[0], _p(x0), _p(x), _p(_f64(q)), _p(_i32(type_)), lj.shape[0], _p(lj),
                                   _p(_f32(box)), float(rc), float(beta), _p(_i32(excl_off)), _p(_i32(excl_idx)),
                                   _p(E), ctypes.byref(npairs))
     if rcode != 0:
         raise ValueError(f"oracle_energy_f32 failed with code {rcode}")
+    if abs_sums:
+        return float(E[0]), float(E[1]), int(npairs.value), (float(E[2]), float(E[3]))
     return float(E[0]), float(E[1]), int(npairs.value)
 
 

@@ -1028,8 +1028,11 @@ int oracle_pme_gather(int n, const double *x, const double *q, const double *box
  * displacements) is the energy error that rounding the displacements to
  * FP32 causes by itself; in water the Coulomb pair energies cancel to a few
  * thousandths of their absolute sum, so at ~10^3 atoms that alone reaches
- * ~1e-6 of E_C. rc is used as given for the LJ shift and as (float)rc for
- * the contract. E[0] = E_LJ, E[1] = E_C. Returns 0, or the error code of
+ * ~1e-6 of E_C. The cutoff is the contract's too: (float)rc, the value the
+ * C ABI receives, for the pair set and for the LJ potential shift (in water
+ * E_LJ cancels so far that the shift at 0.9 and at (float)0.9 give E_LJ
+ * values ~2e-6 apart). E[0] = E_LJ, E[1] = E_C, E[2] and E[3] the sums of
+ * |e_LJ| and |e_C| over the pairs. Returns 0, or the error code of
  * oracle_pairs_f32 (-2: out of memory).
  */
 int oracle_energy_f32(int n, const float *x0, const float *x, const double *q, const int *type, int ntype,
@@ -1051,7 +1054,7 @@ int oracle_energy_f32(int n, const float *x0, const float *x, const double *q, c
     st = oracle_pairs_f32(n, x0, x, box, rcf, excl_off, excl_idx, pi, pj, cnt, &cnt);
     oracle_image_f32(n, x0, x, box, y);
     const float rc2 = rcf * rcf;
-    double sum_lj = 0.0, sum_c = 0.0;
+    double sum_lj = 0.0, sum_c = 0.0, abs_lj = 0.0, abs_c = 0.0;
     for (long long p = 0; st >= 0 && p < cnt; ++p) {
         const int i = pi[p], j = pj[p];
         float u[3];
@@ -1066,13 +1069,17 @@ int oracle_energy_f32(int n, const float *x0, const float *x, const double *q, c
                     if (!(r2 < rc2)) continue;  /* the one image within rc (the pair set checks it) */
                     const double *c = lj + 2 * ((size_t)type[i] * ntype + type[j]);
                     double elj, ec, s;
-                    pair_terms((double)r2, q[i], q[j], c[0], c[1], rc, beta, &elj, &ec, &s);
+                    pair_terms((double)r2, q[i], q[j], c[0], c[1], (double)rcf, beta, &elj, &ec, &s);
                     sum_lj += elj;
                     sum_c += ec;
+                    abs_lj += fabs(elj);
+                    abs_c += fabs(ec);
                 }
     }
     E[0] = sum_lj;
     E[1] = sum_c;
+    E[2] = abs_lj;
+    E[3] = abs_c;
     *npairs = cnt;
     free(pi);
     free(pj);

@@ -4,6 +4,9 @@ Each system's forces and energies from the batch must equal the oracle's
 for that system alone (standard tolerances) and the plain single-system
 path's; the batch must replay correctly from a captured CUDA graph.
 """
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -155,3 +158,47 @@ def test_batch_with_long_and_short_columns(nb):
         total_pairs += n32
     assert pl.stats()["pairs_last"] == total_pairs
     pl.close()
+
+
+def test_full_size_batch_of_256_boxes(nb):
+    """The batched benchmark's workload at full size: 256 boxes of 1,536..24,000 atoms (3.27M atoms),
+    searched at rlist 1.0, pruned to rc 0.9 and computed on gathered tiles, as the benchmark times it.
+    Every box's pair count is the oracle's FP32 set's; its E_C is within 1e-6 of the oracle's energy at
+    the contract's distances (R28), its E_LJ within 1e-6 of max(|E_LJ|, sum |e_LJ|) of it (R18: in some
+    boxes attraction and repulsion nearly balance, E_LJ ~ 1/400 of sum |e_LJ|, and FP32 rounding of 1/r
+    at close contacts alone moves it by ~2e-6 of itself); forces of four boxes (the smallest, the
+    largest and two others) against the FP64 oracle, and their energies against it at the same bars
+    plus the contract's offset."""
+    rc, rlist = 0.9, 1.0
+    beta = synth.ewald_beta(rc)
+    boxes = synth.batch_boxes(256, 1536, 24000, seed=5)
+    off, x, q, t, eo, ei, bx = concat(boxes)
+    xd = dev(x)
+    pl = nb.Pairlist.batch(off, bx, count_pairs=True)
+    pl.search(xd, None, rlist, dev(eo), dev(ei))
+    pl.prune(xd, rc)
+    F, E = pl.forces(xd, dev(q), dev(t), dev(boxes[0].ljparams), rc, beta)
+    assert pl.status() == 0
+    total = pl.stats()["pairs_last"]
+    pl.close()
+    F = F.cpu().numpy()
+    E = E.cpu().numpy().reshape(-1, 2)
+
+    def reference(b):  # the C oracle runs without the GIL: the boxes go to threads
+        return oracle.energy_f32(b.coords, b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                 b.excl_idx, abs_sums=True)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        refs = list(ex.map(reference, boxes))
+    assert total == sum(r[2] for r in refs)
+    for k, (e32_lj, e32_c, _, (a_lj, _)) in enumerate(refs):
+        assert abs(E[k, 0] - e32_lj) <= E_TOL * max(abs(e32_lj), a_lj), k
+        assert rel(E[k, 1], e32_c) <= E_TOL, k
+    sizes = np.array([b.n_atoms for b in boxes])
+    for k in sorted({int(sizes.argmin()), int(sizes.argmax()), 7, 200}):
+        b = boxes[k]
+        Fo, elj, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
+                                              b.excl_idx)
+        compare_forces(F[off[k]:off[k + 1]], Fo)
+        assert abs(E[k, 0] - elj) <= E_TOL * max(abs(elj), refs[k][3][0]) + abs(refs[k][0] - elj), k
+        assert abs(E[k, 1] - ec) <= E_TOL * abs(ec) + abs(refs[k][1] - ec), k

@@ -30,7 +30,8 @@ MUTATIONS = {
     "fp32_image_sign_slip": ("return x - k * L;", "return x + k * L;"),
     # the energies at the contract's distances
     "energy_f32_drops_the_shift": ("const float dx = u[0] + (float)sx * box[0];", "const float dx = u[0];"),
-    "energy_f32_lj_parameters_swapped": ("q[i], q[j], c[0], c[1], rc, beta", "q[i], q[j], c[1], c[0], rc, beta"),
+    "energy_f32_lj_parameters_swapped": ("q[i], q[j], c[0], c[1], (double)rcf", "q[i], q[j], c[1], c[0], (double)rcf"),
+    "energy_f32_shift_at_the_fp64_cutoff": ("c[0], c[1], (double)rcf, beta", "c[0], c[1], rc, beta"),
     "energy_f32_partner_charge": ("pair_terms((double)r2, q[i], q[j],", "pair_terms((double)r2, q[i], q[i],"),
 }
 

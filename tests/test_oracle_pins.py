@@ -428,14 +428,18 @@ def _grid_system(seed, n=128, L=4.0, step=1.0 / 16.0, dmin=0.3):
 
 def test_energy_f32_equals_fp64_where_fp32_distances_are_exact():
     """Where every FP32 displacement and r^2 of the contract is exact (grid coordinates), the energies
-    at the contract's distances are the FP64 energies: same pair count, E_LJ and E_C to rounding."""
+    at the contract's distances are the FP64 energies at the same (FP32) cutoff: same pair count,
+    E_LJ and E_C to rounding."""
     for seed in range(3):
         x, q, typ, lj, box = _grid_system(seed)
         beta = synth.ewald_beta(0.9)
-        _, elj, ec, npairs = oracle.energy_forces(x, q, typ, lj, box, 0.9, beta, method="n2")
-        e32_lj, e32_c, n32 = oracle.energy_f32(x, x, q, typ, lj, box, 0.9, beta)
+        rc32 = float(np.float32(0.9))  # the cutoff the contract uses
+        _, elj, ec, npairs, (alj, ac) = oracle.energy_forces(x, q, typ, lj, box, rc32, beta, method="n2",
+                                                             abs_sums=True)
+        e32_lj, e32_c, n32, (a32_lj, a32_c) = oracle.energy_f32(x, x, q, typ, lj, box, 0.9, beta, abs_sums=True)
         assert n32 == npairs > 200
         assert abs(e32_lj - elj) <= 1e-12 * abs(elj) and abs(e32_c - ec) <= 1e-12 * abs(ec)
+        assert abs(a32_lj - alj) <= 1e-12 * alj and abs(a32_c - ac) <= 1e-12 * ac
 
 
 def test_energy_f32_unchanged_by_whole_box_shifts():
