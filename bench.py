@@ -391,18 +391,32 @@ def bench_small(dev, reps: int = 200, with_oracle: bool = True) -> dict:
         torch.cuda.synchronize()
         host.append(1e6 * (time.perf_counter() - t0))
     assert pl.status() == 0
+    e = E.cpu().numpy()
+    # the force call on the pruned list (gathered tiles): what each evaluation costs once the list has
+    # been pruned, as in a run that searches and prunes once for several evaluations
+    pl.prune(x, rc)
+    gp = torch.cuda.CUDAGraph()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(gp, stream=side):
+            pl.forces(x, q, t, lj, rc, beta, F, E, stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    pruned50, pruned99 = timed(gp.replay)
+    assert pl.status() == 0
     Fo, elj, ec, _ = oracle.energy_forces(b.coords, b.q, b.type, b.ljparams, b.box, rc, beta, b.excl_off,
                                           b.excl_idx)
-    e = E.cpu().numpy()
     assert abs(e[0] - elj) <= 1e-6 * abs(elj) and abs(e[1] - ec) <= 1e-6 * abs(ec)
     pl.close()
     out = {"workload": "water1.5k: 1,536-atom water box (512 waters, L 2.484 nm), rc = rlist = 0.9 nm; "
                        "one nb_search + one nb_forces (forces and energies)",
            "pairs": pairs, "plain_p50_us": plain50, "plain_p99_us": plain99, "graph_p50_us": graph50,
            "graph_p99_us": graph99, "graph_host_wall_p50_us": _percentile(host, 50),
-           "forces_only_graph_p50_us": forces50, "forces_only_graph_p99_us": forces99, "reps": reps,
+           "forces_only_graph_p50_us": forces50, "forces_only_graph_p99_us": forces99,
+           "forces_after_prune_graph_p50_us": pruned50, "forces_after_prune_graph_p99_us": pruned99, "reps": reps,
            "paper_context": "19.2 us: the paper's minimum NBNXM walltime, smallest Grappa input (about 1.5k "
-                            "atoms) on one MI250X GCD (Sec. III-A, Fig. 2); force kernel only, not a search"}
+                            "atoms) on one MI250X GCD (Sec. III-A, Fig. 2); the force kernel alone on a pruned "
+                            "list, not a search: compare forces_after_prune_graph (gather, kernel, permute-back)"}
     if with_oracle:
         ts = []
         for _ in range(5):
